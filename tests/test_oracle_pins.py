@@ -1,0 +1,426 @@
+"""Pins of the CPU oracle against facts the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: values the
+paper prints (tests/golden), closed forms, invariants, and brute force on
+tiny inputs.  None of these tests needs a GPU.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from conftest import read_golden
+
+LEVELS = (1, 3, 5)
+
+
+# ---------------------------------------------------------------------------
+# Table I (parameter sets)
+# ---------------------------------------------------------------------------
+def _table1():
+    out = {}
+    for row in read_golden("table1_params.txt"):
+        lvl = int(row[0].split("-")[1])
+        out[lvl] = dict(n=int(row[1]), w=int(row[2]), we=int(row[3]), n1=int(row[4]),
+                        k=int(row[5]), d_rs=int(row[6]), n2=int(row[7]), k_rm=int(row[8]),
+                        d_rm=int(row[9]))
+    return out
+
+
+@pytest.mark.parametrize("level", LEVELS)
+def test_params_match_table1(level):
+    t = _table1()[level]
+    P = oracle.params(level)
+    assert (P.n, P.w, P.we, P.wr, P.n1, P.k) == (t["n"], t["w"], t["we"], t["we"], t["n1"], t["k"])
+    # RS [n1, k, d] with d = 2 delta + 1 and n1 - k = 2 delta (an MDS code)
+    assert 2 * P.delta + 1 == t["d_rs"]
+    assert P.n1 - P.k == 2 * P.delta
+    # duplicated RM(1,7): length 128 * mult, dimension 8, distance 64 * mult
+    assert t["k_rm"] == 8 and P.n2 == 128 * P.mult == t["n2"] and t["d_rm"] == 64 * P.mult
+    # the concatenated codeword fits in the ring
+    assert P.n >= P.n1 * P.n2
+    assert P.W_v * 64 == P.n1 * P.n2
+
+
+def test_printed_counts():
+    rows = {r[0]: int(r[1]) for r in read_golden("printed_counts.txt")}
+    P = oracle.params(1)
+    # 2 delta syndromes, each summing n1 terms of which the j = 0 term needs
+    # no multiplication (alpha^0 = 1): Sec. III-D prints ~1,350 for HQC-1.
+    assert 2 * P.delta * (P.n1 - 1) == rows["syndrome_mults_per_codeword_hqc1"]
+    # encoder table: one byte per (generator coefficient, byte value); the
+    # monic leading coefficient needs no entry -> (n1 - k) * 256 B ~ 8 KB.
+    kb = (P.n1 - P.k) * 256 / 1024
+    assert abs(kb - rows["rs_encode_table_kb"]) < 1.0
+
+
+# ---------------------------------------------------------------------------
+# GF(2^8) (reading A3)
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def gf_table():
+    T = np.zeros((256, 256), np.uint8)
+    for a in range(256):
+        for b in range(256):
+            T[a, b] = oracle.gf_mul(a, b)
+    return T
+
+
+def test_gf_field_axioms(gf_table):
+    T = gf_table
+    a = np.arange(256)
+    assert (T == T.T).all()
+    assert (T[1] == a).all() and (T[0] == 0).all()
+    # associativity, exhaustively
+    A, B, C = np.meshgrid(a, a, a, indexing="ij")
+    assert (T[T[A, B], C] == T[A, T[B, C]]).all()
+    # distributivity over XOR (addition in characteristic 2)
+    assert (T[A, B ^ C] == (T[A, B] ^ T[A, C])).all()
+    # no zero divisors and every nonzero element has exactly one inverse
+    nz = T[1:, 1:]
+    assert (nz != 0).all()
+    assert ((nz == 1).sum(axis=1) == 1).all()
+
+
+def test_gf_modulus_and_primitive_alpha(gf_table):
+    T = gf_table
+    # alpha = x: x^8 reduces to x^4 + x^3 + x^2 + 1 = 0x1D under the modulus
+    p = 1
+    pw = []
+    for _ in range(255):
+        pw.append(p)
+        p = int(T[p, 2])
+    assert pw[8] == 0x1D
+    assert p == 1                      # alpha^255 = 1
+    assert sorted(pw) == list(range(1, 256))  # order exactly 255: primitive
+
+
+# ---------------------------------------------------------------------------
+# Ring product (Eq. 1)
+# ---------------------------------------------------------------------------
+def _schoolbook(n, a, b):
+    """Dense product mod (x^n - 1) over GF(2) through numpy's convolution."""
+    full = np.convolve(a.astype(np.int64), b.astype(np.int64)) & 1
+    out = np.zeros(n, np.int64)
+    for i, c in enumerate(full):
+        out[i % n] ^= c
+    return out.astype(np.uint8)
+
+
+@pytest.mark.parametrize("n", [7, 11, 13, 31, 67, 127, 131, 257])
+def test_eq1_matches_schoolbook(n):
+    for trial in range(6):
+        a2 = (synth.words(n, tag=100 + n, index=trial) & 1).astype(np.uint8)
+        wt = min(n, 1 + trial * 3)
+        supp = synth.support(n, wt, tag=200 + n, index=trial)
+        a1 = np.zeros(n, np.uint8)
+        a1[supp] = 1
+        got = oracle.ring_mul_sparse_bits(n, a2, supp)
+        assert (got == _schoolbook(n, a1, a2)).all()
+
+
+@pytest.mark.parametrize("n", range(2, 13))
+def test_eq1_exhaustive_small_n(n):
+    # every a2 in GF(2)^n against every single rotation and a fixed pair
+    for val in range(1 << n):
+        a2 = np.array([(val >> i) & 1 for i in range(n)], np.uint8)
+        for supp in ([0], [1 % n], [n - 1], [0, n // 2] if n > 2 else [0]):
+            a1 = np.zeros(n, np.uint8)
+            a1[supp] ^= 1
+            assert (oracle.ring_mul_sparse_bits(n, a2, supp) == _schoolbook(n, a1, a2)).all()
+
+
+def test_ring_identities():
+    n = 1031
+    s1 = synth.support(n, 9, tag=7, index=1)
+    s2 = synth.support(n, 11, tag=7, index=2)
+    s3 = synth.support(n, 5, tag=7, index=3)
+    b1 = np.zeros(n, np.uint8); b1[s1] = 1
+    b2 = np.zeros(n, np.uint8); b2[s2] = 1
+    b3 = np.zeros(n, np.uint8); b3[s3] = 1
+    # commutativity: a*b computed with either operand as the sparse one
+    assert (oracle.ring_mul_sparse_bits(n, b2, s1) == oracle.ring_mul_sparse_bits(n, b1, s2)).all()
+    # associativity
+    ab = oracle.ring_mul_sparse_bits(n, b2, s1)
+    bc = oracle.ring_mul_sparse_bits(n, b3, s2)
+    assert (oracle.ring_mul_sparse_bits(n, ab, s3) == oracle.ring_mul_sparse_bits(n, bc, s1)).all()
+    # x^n = 1: rotating by p and then by n - p is the identity
+    a = (synth.words(n, tag=8) & 1).astype(np.uint8)
+    p = 377
+    assert (oracle.ring_mul_sparse_bits(n, oracle.ring_mul_sparse_bits(n, a, [p]), [n - p]) == a).all()
+    # x^p * a is the cyclic shift towards higher degree
+    assert (oracle.ring_mul_sparse_bits(n, a, [p]) == np.roll(a, p)).all()
+    # duplicated support entries cancel, out-of-range entries contribute nothing
+    assert (oracle.ring_mul_sparse_bits(n, a, [5, 5]) == 0).all()
+    assert (oracle.ring_mul_sparse_bits(n, a, [n, n + 3]) == 0).all()
+
+
+@pytest.mark.parametrize("level", LEVELS)
+def test_ring_parity_invariant_full_n(level):
+    # evaluation at x = 1 is a ring homomorphism: wt(a*b) = wt(a) wt(b) mod 2
+    P = oracle.params(level)
+    for trial in range(2):
+        a = (synth.words(P.n, tag=300 + level, index=trial) & 1).astype(np.uint8)
+        supp = synth.support(P.n, P.w - trial, tag=310 + level, index=trial)
+        prod = oracle.ring_mul_sparse_bits(P.n, a, supp)
+        assert int(prod.sum()) % 2 == (int(a.sum()) * len(supp)) % 2
+
+
+# ---------------------------------------------------------------------------
+# Reed-Solomon (Sec. III-D; readings A4, A6, A9-A11)
+# ---------------------------------------------------------------------------
+def _alpha_pows(T):
+    pw = [1]
+    for _ in range(600):
+        pw.append(int(T[pw[-1], 2]))
+    return pw
+
+
+def _peval(T, coeffs, x):
+    acc, xp = 0, 1
+    for c in coeffs:
+        acc ^= int(T[int(c), xp])
+        xp = int(T[xp, x])
+    return acc
+
+
+@pytest.mark.parametrize("level", LEVELS)
+def test_rs_generator_roots(level, gf_table):
+    P = oracle.params(level)
+    g = oracle.rs_generator(P.n1, P.k)
+    pw = _alpha_pows(gf_table)
+    assert len(g) == 2 * P.delta + 1 and g[-1] == 1   # monic of degree 2 delta
+    for i in range(1, 2 * P.delta + 1):
+        assert _peval(gf_table, g, pw[i]) == 0
+    assert _peval(gf_table, g, pw[2 * P.delta + 1]) != 0
+    assert _peval(gf_table, g, pw[0]) != 0
+
+
+@pytest.mark.parametrize("level", LEVELS)
+def test_rs_codewords_have_zero_syndromes(level, gf_table):
+    P = oracle.params(level)
+    pw = _alpha_pows(gf_table)
+    for trial in range(4):
+        m = (synth.words(P.k, tag=400 + level, index=trial) & 0xFF).astype(np.uint8)
+        c = oracle.rs_encode(P.n1, P.k, m)
+        assert (c[P.n1 - P.k:] == m).all()            # systematic, message last
+        assert (oracle.rs_syndromes(P.n1, P.k, c) == 0).all()
+        # c(x) vanishes at alpha^1..alpha^{2 delta}, evaluated independently
+        for i in (1, P.delta, 2 * P.delta):
+            assert _peval(gf_table, c, pw[i]) == 0
+
+
+def _inject(n1, t, tag, index):
+    pos = synth.support(n1, t, tag=tag, index=index) if t else np.zeros(0, np.uint32)
+    val = (synth.below(255, max(t, 1), tag=tag + 1, index=index)[:t] + 1).astype(np.uint8)
+    e = np.zeros(n1, np.uint8)
+    e[pos] = val
+    return e, pos, val
+
+
+@pytest.mark.parametrize("level", LEVELS)
+def test_rs_decode_up_to_delta(level, gf_table):
+    P = oracle.params(level)
+    pw = _alpha_pows(gf_table)
+    for trial, t in enumerate([0, 1, 2, P.delta // 2, P.delta - 1, P.delta]):
+        m = (synth.words(P.k, tag=500 + level, index=trial) & 0xFF).astype(np.uint8)
+        c = oracle.rs_encode(P.n1, P.k, m)
+        e, pos, val = _inject(P.n1, t, tag=510 + level, index=trial)
+        d = oracle.rs_decode(P.n1, P.k, c ^ e)
+        assert (d["cw"] == c).all()
+        assert (d["errval"] == e).all()
+        assert (d["errmask"] == (e != 0)).all()
+        assert d["L"] == t and d["flag"] == 0
+        # closed form: Lambda(x) = prod over error locators X of (1 - X x)
+        lam = [1]
+        for p in pos:
+            X = pw[int(p)]
+            nxt = [0] * (len(lam) + 1)
+            for i, cf in enumerate(lam):
+                nxt[i] ^= cf
+                nxt[i + 1] ^= int(gf_table[cf, X])
+            lam = nxt
+        want = np.zeros(2 * P.delta + 1, np.uint8)
+        want[:len(lam)] = lam
+        assert (d["lam"] == want).all()
+
+
+def test_rs_brute_force_tiny_code():
+    # RS[6, 2] (delta = 2): the decoder must return the unique nearest
+    # codeword whenever one lies within distance delta.
+    n1, k = 6, 2
+    msgs = np.array(list(itertools.product(range(256), repeat=2)), np.uint8)
+    code = np.stack([oracle.rs_encode(n1, k, m[::-1].copy()) for m in msgs])
+    assert len({c.tobytes() for c in code}) == 65536
+    for trial in range(40):
+        base = code[int(synth.below(65536, 1, tag=600, index=trial)[0])]
+        t = trial % 4
+        e, _, _ = _inject(n1, t, tag=610, index=trial)
+        r = base ^ e
+        dist = (code != r).sum(axis=1)
+        d = oracle.rs_decode(n1, k, r)
+        if dist.min() <= 2:
+            nearest = code[int(dist.argmin())]
+            assert (dist == dist.min()).sum() == 1
+            assert (d["cw"] == nearest).all()
+
+
+@pytest.mark.parametrize("level", LEVELS)
+def test_rs_beyond_delta_is_deterministic(level):
+    # Reading A12: the decoder output is defined by the step list; it is not
+    # pinned externally, only checked for determinism and flagging.
+    P = oracle.params(level)
+    m = (synth.words(P.k, tag=700 + level) & 0xFF).astype(np.uint8)
+    c = oracle.rs_encode(P.n1, P.k, m)
+    e, _, _ = _inject(P.n1, P.delta + 3, tag=710 + level, index=0)
+    d1 = oracle.rs_decode(P.n1, P.k, c ^ e)
+    d2 = oracle.rs_decode(P.n1, P.k, c ^ e)
+    for key in ("S", "lam", "errmask", "errval", "cw"):
+        assert (d1[key] == d2[key]).all()
+    assert d1["L"] <= 2 * P.delta
+    assert (d1["lam"][d1["L"] + 1:] == 0).all()       # deg Lambda <= L
+    assert d1["lam"][0] == 1
+
+
+# ---------------------------------------------------------------------------
+# Reed-Muller RM(1,7), duplicated (readings A7, A8)
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def rm_code():
+    return np.stack([oracle.rm_encode_byte(b) for b in range(256)])
+
+
+def test_rm_distances(rm_code):
+    C = rm_code.astype(np.int64)
+    D = (C[:, None, :] != C[None, :, :]).sum(axis=2)
+    for a in range(256):
+        for b in range(256):
+            if a == b:
+                assert D[a, b] == 0
+            elif a ^ b == 128:
+                assert D[a, b] == 128          # complementary pair
+            else:
+                assert D[a, b] == 64           # RM(1,7) minimum distance
+    # the all-ones row is bit 7; byte 0 is the zero word
+    assert (C[0] == 0).all() and (C[128] == 1).all()
+    # the low 7 bits are the linear part: bit i of byte 2^t is bit t of i
+    for t in range(7):
+        assert (C[1 << t] == ((np.arange(128) >> t) & 1)).all()
+
+
+@pytest.mark.parametrize("mult", [3, 5])
+def test_rm_transform_peak(mult, rm_code):
+    for byte in (0, 1, 77, 128, 200, 255):
+        bits = np.tile(rm_code[byte], mult)
+        F = oracle.rm_transform(mult, bits)
+        a = byte & 127
+        sign = -1 if byte >> 7 else 1
+        assert F[a] == sign * 128 * mult
+        assert (np.delete(F, a) == 0).all()     # distinct linear parts are orthogonal
+
+
+def _brute_rm(mult, bits, rm_code):
+    dup = np.tile(rm_code, (1, mult))
+    dist = (dup != bits[None, :]).sum(axis=1)
+    best = dist.min()
+    # tie rule of reading A8: smallest linear part a first, then b = 0
+    for a in range(128):
+        for b in (0, 1):
+            if dist[a + 128 * b] == best:
+                return a + 128 * b
+
+
+@pytest.mark.parametrize("mult", [3, 5])
+def test_rm_decode_matches_brute_force(mult, rm_code):
+    for trial in range(300):
+        byte = int(synth.below(256, 1, tag=800 + mult, index=trial)[0])
+        bits = np.tile(rm_code[byte], mult).copy()
+        nflip = [0, 1, 32 * mult - 1, 64 * mult, 96 * mult][trial % 5]
+        if nflip:
+            pos = synth.support(128 * mult, nflip, tag=810 + mult, index=trial)
+            bits[pos] ^= 1
+        got = oracle.rm_decode_block(mult, bits)
+        assert got == _brute_rm(mult, bits, rm_code)
+        if nflip < 32 * mult:
+            assert got == byte                  # within the unique-decoding radius
+
+
+def test_rm_decode_tie_rule(rm_code):
+    # a word exactly between two codewords: the smaller linear part wins
+    mult = 3
+    c1, c2 = rm_code[5], rm_code[9]
+    diff = np.nonzero(c1 != c2)[0]
+    word = c1.copy()
+    word[diff[: len(diff) // 2]] = c2[diff[: len(diff) // 2]]
+    bits = np.tile(word, mult)
+    assert oracle.rm_decode_block(mult, bits) == 5 == _brute_rm(mult, bits, rm_code)
+
+
+# ---------------------------------------------------------------------------
+# PKE (Algorithms 1-3)
+# ---------------------------------------------------------------------------
+def _ring(n, dense_words, supp):
+    return oracle.ring_mul_packed(n, dense_words, supp)
+
+
+def _support_words(n, supp, nwords):
+    out = np.zeros(nwords, np.uint64)
+    for p in supp:
+        out[int(p) // 64] ^= np.uint64(1) << np.uint64(int(p) % 64)
+    return out
+
+
+@pytest.mark.parametrize("level", LEVELS)
+def test_pke_round_trip_and_decrypt_identity(level):
+    P = oracle.params(level)
+    S = synth.Shape.of(P)
+    nkeys, cnt = 3, 12
+    h, x, y = synth.keys(S, nkeys)
+    s = oracle.keygen(level, h, x, y)
+    m, r1, r2, e = synth.ciphertext_randomness(S, cnt)
+    kidx = synth.key_assignment(cnt, nkeys, tag=level)
+    u, v = oracle.encrypt(level, h, s, kidx, m, r1, r2, e)
+    assert (oracle.decrypt(level, u, v, y[kidx]) == m).all()
+    nw = (P.n + 63) // 64
+    for j in range(3):
+        kk = kidx[j]
+        # s = x + h*y (Algorithm 3) from an independent product
+        assert (s[kk][:nw] == _ring(P.n, h[kk][:nw], y[kk]) ^ _support_words(P.n, x[kk], nw)).all()
+        # u = r1 + h*r2 (Algorithm 1)
+        assert (u[j][:nw] == _ring(P.n, h[kk][:nw], r2[j]) ^ _support_words(P.n, r1[j], nw)).all()
+        # v + u*y = mG + x*r2 + r1*y + e (truncated): the h terms cancel
+        d = oracle.decrypt_dump(level, u[j], v[j], y[kk])
+        lhs = d["w"]
+        noise = (_ring(P.n, _support_words(P.n, x[kk], nw), r2[j])
+                 ^ _ring(P.n, _support_words(P.n, r1[j], nw), y[kk])
+                 ^ _support_words(P.n, e[j], nw))
+        rhs = oracle.concat_encode(level, m[j]) ^ noise[: P.W_v]
+        if (P.n1 * P.n2) % 64:
+            raise AssertionError("n1*n2 is a multiple of 64 for every level")
+        assert (lhs == rhs).all()
+        assert (d["t"] ^ v[j] == d["w"]).all()
+        assert (d["m"] == m[j]).all() and d["flag"] == 0
+        assert (d["cw"][P.n1 - P.k:] == m[j]).all()
+
+
+@pytest.mark.parametrize("level", LEVELS)
+def test_decrypt_ignores_padding_bits(level):
+    P = oracle.params(level)
+    S = synth.Shape.of(P)
+    h, x, y = synth.keys(S, 1)
+    s = oracle.keygen(level, h, x, y)
+    m, r1, r2, e = synth.ciphertext_randomness(S, 2)
+    u, v = oracle.encrypt(level, h, s, np.zeros(2, np.int32), m, r1, r2, e)
+    garbage = u.copy()
+    nb = P.n % 64
+    top = P.W_u - 1
+    g = synth.words(2 * P.W_u_pitch, tag=900 + level).reshape(2, P.W_u_pitch)
+    mask = np.uint64(((1 << 64) - 1) ^ ((1 << nb) - 1))
+    garbage[:, top] |= g[:, top] & mask
+    garbage[:, P.W_u:] = g[:, P.W_u:]
+    assert (oracle.decrypt(level, garbage, v, y[[0, 0]]) == m).all()
+    d0 = oracle.decrypt_dump(level, u[0], v[0], y[0])
+    d1 = oracle.decrypt_dump(level, garbage[0], v[0], y[0])
+    assert (d0["t"] == d1["t"]).all()
