@@ -1,0 +1,188 @@
+/*
+ * hqc_gb300.h -- C ABI of the GB300 (sm_103a) batched HQC.PKE library.
+ *
+ * The operation is HQC.PKE.Decrypt (Algorithm 2 of OptHQC, arXiv
+ * 2512.12904): for each ciphertext c = (u, v) and secret support y,
+ *     m' = C.Decode(v - u*y)
+ * where u*y is the quasi-cyclic product in GF(2)[x]/(x^n - 1) written as the
+ * XOR of rotations of u (Eq. 1, Sec. III-B), the difference is truncated to
+ * n1*n2 bits, C.Decode is duplicated RM(1,7) decoding per n2-bit block
+ * followed by Reed-Solomon decoding over GF(2^8) (Sec. II-A, Sec. III-D).
+ * The parameter sets are Table I.  (The paper prints u*s in Algorithm 2;
+ * the operand that cancels the public h is the secret y, which is what this
+ * library uses.)
+ *
+ * Conventions shared by every entry point
+ *   - Bit i of a vector is bit (i % 64) of 64-bit word i / 64.
+ *   - u rows have W_u_pitch 64-bit words (W_u = ceil(n/64) rounded up to
+ *     even); bits >= n and the pad word are ignored.  v rows have W_v words
+ *     (exactly n1*n2 bits).  m rows have k bytes.
+ *   - RS codewords are (parity bytes || message bytes); m' is the last k
+ *     bytes of the corrected codeword.
+ *   - Data pointers are DEVICE pointers owned by the caller unless stated
+ *     otherwise; u, v and arena pointers must be 16-byte aligned.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *     stream-ordered and asynchronous: argument errors are returned at once,
+ *     results are ready when the stream reaches the call.
+ *   - No entry point allocates device memory, except hqc_keys_register.
+ *   - HQC.PKE.Decrypt has no failure output, so m_out is always written.
+ *   - Every kernel has data-independent control flow and lane-replicated
+ *     GF(2^8) tables (bank-conflict-free for any secret index).
+ *   - Return value: HQC_OK or a negative HQC_E* code; hqc_last_error()
+ *     gives a message for the calling thread's last error.
+ */
+#ifndef HQC_GB300_H
+#define HQC_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HQC_OK 0
+#define HQC_EINVAL (-1)     /* bad level, count, pointer, alignment or size */
+#define HQC_ENOMEM (-2)     /* workspace too small / allocation failed */
+#define HQC_ECUDA (-3)      /* CUDA launch or runtime error (see hqc_last_error) */
+#define HQC_ETIMEOUT (-4)   /* a bounded wait gave up */
+#define HQC_EBUSY (-5)      /* admission refused (serving) */
+#define HQC_EINTERNAL (-6)  /* internal consistency check failed */
+
+/* Table I plus derived sizes.  level in {1, 3, 5}. */
+typedef struct hqc_params_s {
+  int32_t level;
+  int32_t n;          /* ring length */
+  int32_t n1, k;      /* RS [n1, k, 2 delta + 1] over GF(2^8) */
+  int32_t delta;
+  int32_t n2, mult;   /* RM(1,7) duplicated mult times: n2 = 128 mult */
+  int32_t w, wr, we;  /* weights of x, y; r1, r2; e */
+  int32_t W_u;        /* ceil(n / 64) */
+  int32_t W_u_pitch;  /* W_u rounded up to even */
+  int32_t W_v;        /* n1 * n2 / 64 */
+} hqc_params_t;
+
+/* Fill *out for `level`.  Host only, needs no GPU.  HQC_EINVAL for an
+ * unknown level or NULL out. */
+int hqc_get_params(int level, hqc_params_t* out);
+
+/* Message of the calling thread's last failed call ("" if none).  The
+ * pointer stays valid until the thread's next call into the library. */
+const char* hqc_last_error(void);
+
+/* HQC.PKE.Decrypt of `count` ciphertexts with literal supports
+ * (Algorithm 2): y is [count][w] uint32 positions of the secret y of each
+ * ciphertext.  Entries >= n contribute nothing; repeated entries cancel
+ * (the product is a XOR of rotations, Eq. 1).  u [count][W_u_pitch],
+ * v [count][W_v], m_out [count][k].  One persistent fused kernel. */
+int hqc_decrypt_batch(int level, int64_t count, const uint64_t* u, const uint64_t* v, const uint32_t* y,
+                      uint8_t* m_out, void* stream);
+
+/* Secret supports resident on the device, validated once. */
+typedef struct hqc_keyset_s hqc_keyset_t;
+
+/* Copy nkeys supports y_host [nkeys][w] (HOST memory) to the current
+ * device.  Every entry must be < n and distinct within its row, else
+ * HQC_EINVAL.  Allocates device memory; free with hqc_keys_free. */
+int hqc_keys_register(int level, int64_t nkeys, const uint32_t* y_host, hqc_keyset_t** out);
+int hqc_keys_free(hqc_keyset_t* keys);
+/* Level and count of a keyset; the device pointer of its [nkeys][w] table. */
+int hqc_keys_info(const hqc_keyset_t* keys, int* level, int64_t* nkeys, const uint32_t** device_table);
+
+/* Decrypt with registered keys: ciphertext i uses key key_idx[i]
+ * (device int32 [count]).  An index outside [0, nkeys) selects key 0.
+ * Same kernel as hqc_decrypt_batch with validated supports. */
+int hqc_decrypt_batch_keyed(int level, int64_t count, const uint64_t* u, const uint64_t* v, const hqc_keyset_t* keys,
+                            const int32_t* key_idx, uint8_t* m_out, void* stream);
+
+/* Plain one-kernel-per-stage form (product, RM decode, RS decode as three
+ * launches with intermediates in global memory): the comparison baseline
+ * of the fused kernel.  Give either y (literal) or keys + key_idx.
+ * workspace: device memory of at least hqc_staged_workspace_bytes(level,
+ * count) bytes, 16-byte aligned; its contents on return are unspecified. */
+size_t hqc_staged_workspace_bytes(int level, int64_t count);
+int hqc_decrypt_batch_staged(int level, int64_t count, const uint64_t* u, const uint64_t* v, const uint32_t* y,
+                             const hqc_keyset_t* keys, const int32_t* key_idx, void* workspace,
+                             size_t workspace_bytes, uint8_t* m_out, void* stream);
+
+/* Every intermediate of Algorithm 2, per ciphertext (device arrays):
+ *   t    [count][W_v]  u*y truncated to n1*n2 bits
+ *   w    [count][W_v]  v + t
+ *   r    [count][n1]   RM-decoded bytes
+ *   S    [count][2 delta]      syndromes S_1..S_2delta
+ *   lam  [count][2 delta + 1]  error locator Lambda_0..Lambda_2delta
+ *   L    [count]               Berlekamp-Massey length
+ *   errmask, errval, cw [count][n1]  Chien roots, Forney values, corrected word
+ *   flag [count]  1 if L > delta or #roots != L (test aid, not an HQC output) */
+typedef struct hqc_debug_dump_s {
+  uint64_t* t;
+  uint64_t* w;
+  uint8_t* r;
+  uint8_t* S;
+  uint8_t* lam;
+  int32_t* L;
+  uint8_t* errmask;
+  uint8_t* errval;
+  uint8_t* cw;
+  int32_t* flag;
+} hqc_debug_dump_t;
+
+/* Per-stage decrypt that also writes every intermediate.  dump points to
+ * HOST memory holding device pointers; all ten must be non-NULL. */
+int hqc_decrypt_debug(int level, int64_t count, const uint64_t* u, const uint64_t* v, const uint32_t* y,
+                      const hqc_debug_dump_t* dump, uint8_t* m_out, void* stream);
+
+/* Mixed-level batch in one persistent launch.  items: device array of
+ * `count` work items; u and v rows are read from `arena` (device, 64-bit
+ * words) at the given word offsets (u_off even), m is written to
+ * m_arena + m_off.  keys[0..2]: keysets for levels 1, 3, 5 (NULL if a level
+ * is absent).  An item whose level, key or offsets fall outside these
+ * arrays is skipped and its m bytes are left untouched.  workspace: at
+ * least hqc_mixed_workspace_bytes() bytes of device memory (a work
+ * counter, zeroed on the stream by this call). */
+typedef struct hqc_item_s {
+  int32_t level;
+  int32_t key;
+  int64_t u_off;
+  int64_t v_off;
+  int64_t m_off;
+} hqc_item_t;
+
+size_t hqc_mixed_workspace_bytes(void);
+int hqc_decrypt_mixed(int64_t count, const hqc_item_t* items, const uint64_t* arena, int64_t arena_words,
+                      const hqc_keyset_t* const keys[3], uint8_t* m_arena, int64_t m_bytes, void* workspace,
+                      size_t workspace_bytes, void* stream);
+
+/* Launch shape of the persistent kernels: warps per block and blocks per
+ * SM (0 = the library's default).  level 1/3/5 sets the single-level
+ * kernels, level 0 the mixed kernel.  Not thread-safe against concurrent
+ * launches. */
+typedef struct hqc_launch_cfg_s {
+  int32_t warps_per_cta;
+  int32_t ctas_per_sm;
+} hqc_launch_cfg_t;
+
+int hqc_set_launch_config(int level, const hqc_launch_cfg_t* cfg);
+/* Resolved shape on the current device: warps per block, blocks per SM and
+ * grid size of the persistent launch (keyed selects the kernel variant). */
+int hqc_get_launch_shape(int level, int keyed, int32_t* warps, int32_t* ctas_per_sm, int32_t* grid);
+
+/* Key generation core of Algorithm 3: s = x + h*y per key.
+ * h, s_out [nkeys][W_u_pitch]; x, y [nkeys][w] (device). */
+int hqc_keygen_batch(int level, int64_t nkeys, const uint64_t* h, const uint32_t* x, const uint32_t* y,
+                     uint64_t* s_out, void* stream);
+
+/* HQC.PKE.Encrypt (Algorithm 1): u = r1 + h*r2, v = first n1*n2 bits of
+ * C.Encode(m) + s*r2 + e.  h, s [nkeys][W_u_pitch]; key_idx [count] (an
+ * index outside [0, nkeys) selects key 0); m [count][k]; r1, r2
+ * [count][wr]; e [count][we]; u_out [count][W_u_pitch] (pad bits zero);
+ * v_out [count][W_v]. */
+int hqc_encrypt_batch(int level, int64_t count, const uint64_t* h, const uint64_t* s, int64_t nkeys,
+                      const int32_t* key_idx, const uint8_t* m, const uint32_t* r1, const uint32_t* r2,
+                      const uint32_t* e, uint64_t* u_out, uint64_t* v_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HQC_GB300_H */

@@ -1,0 +1,359 @@
+"""Python binding of the GB300 batched HQC.PKE library (include/hqc_gb300.h).
+
+Argument marshalling only: every function below checks tensor dtypes,
+shapes and devices, then calls the C entry point of the same name in
+``libhqc_gb300.so``.  PyTorch supplies device memory and streams; all
+arithmetic runs in the library's CUDA kernels.  There is no CPU fallback:
+without the compiled library or a CUDA device the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+__all__ = [
+    "HqcError", "Params", "Keyset", "load", "hqc_get_params", "hqc_decrypt_batch",
+    "hqc_keys_register", "hqc_decrypt_batch_keyed", "hqc_staged_workspace_bytes",
+    "hqc_decrypt_batch_staged", "hqc_decrypt_debug", "hqc_mixed_workspace_bytes",
+    "hqc_decrypt_mixed", "hqc_set_launch_config", "hqc_get_launch_shape", "hqc_keygen_batch",
+    "hqc_encrypt_batch", "LEVELS",
+]
+
+LEVELS = (1, 3, 5)
+_lock = threading.Lock()
+_lib = None
+
+
+class HqcError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("HQC error %d: %s" % (code, msg))
+        self.code = code
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in
+                ("level", "n", "n1", "k", "delta", "n2", "mult", "w", "wr", "we", "W_u", "W_u_pitch", "W_v")]
+
+
+class _Dump(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in
+                ("t", "w", "r", "S", "lam", "L", "errmask", "errval", "cw", "flag")]
+
+
+class _LaunchCfg(ctypes.Structure):
+    _fields_ = [("warps_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+
+
+ITEM_DTYPE = np.dtype([("level", "<i4"), ("key", "<i4"), ("u_off", "<i8"), ("v_off", "<i8"), ("m_off", "<i8")])
+
+
+def load(build_if_missing: bool = True):
+    """Load libhqc_gb300.so (building it with nvcc first if needed)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError("libhqc_gb300.so is not built; run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        P, i32, i64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
+        sig = {
+            "hqc_get_params": (i32, [i32, P]),
+            "hqc_last_error": (ctypes.c_char_p, []),
+            "hqc_decrypt_batch": (i32, [i32, i64, P, P, P, P, P]),
+            "hqc_keys_register": (i32, [i32, i64, P, P]),
+            "hqc_keys_free": (i32, [P]),
+            "hqc_keys_info": (i32, [P, P, P, P]),
+            "hqc_decrypt_batch_keyed": (i32, [i32, i64, P, P, P, P, P, P]),
+            "hqc_staged_workspace_bytes": (sz, [i32, i64]),
+            "hqc_decrypt_batch_staged": (i32, [i32, i64, P, P, P, P, P, P, sz, P, P]),
+            "hqc_decrypt_debug": (i32, [i32, i64, P, P, P, P, P, P]),
+            "hqc_mixed_workspace_bytes": (sz, []),
+            "hqc_decrypt_mixed": (i32, [i64, P, P, i64, P, P, i64, P, sz, P]),
+            "hqc_set_launch_config": (i32, [i32, P]),
+            "hqc_get_launch_shape": (i32, [i32, i32, P, P, P]),
+            "hqc_keygen_batch": (i32, [i32, i64, P, P, P, P, P]),
+            "hqc_encrypt_batch": (i32, [i32, i64, P, P, i64, P, P, P, P, P, P, P, P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise HqcError(rc, load().hqc_last_error().decode(errors="replace"))
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers (torch is imported lazily so the CPU tests can load
+# the library without touching CUDA)
+# ---------------------------------------------------------------------------
+def _torch():
+    import torch
+    return torch
+
+
+def _dev_ptr(t, dtype, shape=None, name="tensor"):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch.Tensor" % name)
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must have dtype %s (got %s)" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError("%s must have shape %s (got %s)" % (name, tuple(shape), tuple(t.shape)))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+@dataclass(frozen=True)
+class Params:
+    level: int
+    n: int
+    n1: int
+    k: int
+    delta: int
+    n2: int
+    mult: int
+    w: int
+    wr: int
+    we: int
+    W_u: int
+    W_u_pitch: int
+    W_v: int
+
+
+def hqc_get_params(level: int) -> Params:
+    p = _Params()
+    _check(load().hqc_get_params(level, ctypes.byref(p)))
+    return Params(*(int(getattr(p, f)) for f, _ in _Params._fields_))
+
+
+def _as_u64(t):
+    """View a uint64 tensor as int64 (torch's 64-bit integer type of choice)."""
+    torch = _torch()
+    return t.view(torch.int64) if t.dtype == torch.uint64 else t
+
+
+def hqc_decrypt_batch(level, u, v, y, m_out=None, stream=None):
+    """Fused decryption with literal supports y [count][w] (int32/uint32 view)."""
+    torch = _torch()
+    P = hqc_get_params(level)
+    u, v = _as_u64(u), _as_u64(v)
+    cnt = u.shape[0]
+    if m_out is None:
+        m_out = torch.empty((cnt, P.k), dtype=torch.uint8, device=u.device)
+    y = y.view(torch.int32) if y.dtype == torch.uint32 else y
+    _check(load().hqc_decrypt_batch(level, cnt, _dev_ptr(u, torch.int64, (cnt, P.W_u_pitch), "u"),
+                                    _dev_ptr(v, torch.int64, (cnt, P.W_v), "v"),
+                                    _dev_ptr(y, torch.int32, (cnt, P.w), "y"),
+                                    _dev_ptr(m_out, torch.uint8, (cnt, P.k), "m_out"), _stream(stream)))
+    return m_out
+
+
+class Keyset:
+    """Secret supports registered on the current device (hqc_keys_register)."""
+
+    def __init__(self, level: int, y_host):
+        y = np.ascontiguousarray(np.asarray(y_host, dtype=np.uint32))
+        P = hqc_get_params(level)
+        if y.ndim != 2 or y.shape[1] != P.w:
+            raise ValueError("y_host must be [nkeys][%d]" % P.w)
+        self.level = level
+        self.nkeys = y.shape[0]
+        self._h = ctypes.c_void_p()
+        _check(load().hqc_keys_register(level, self.nkeys, y.ctypes.data_as(ctypes.c_void_p), ctypes.byref(self._h)))
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("keyset was freed")
+        return self._h
+
+    def free(self):
+        if self._h:
+            _check(load().hqc_keys_free(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def hqc_keys_register(level, y_host) -> Keyset:
+    return Keyset(level, y_host)
+
+
+def hqc_decrypt_batch_keyed(level, u, v, keys: Keyset, key_idx, m_out=None, stream=None):
+    torch = _torch()
+    P = hqc_get_params(level)
+    u, v = _as_u64(u), _as_u64(v)
+    cnt = u.shape[0]
+    if m_out is None:
+        m_out = torch.empty((cnt, P.k), dtype=torch.uint8, device=u.device)
+    _check(load().hqc_decrypt_batch_keyed(level, cnt, _dev_ptr(u, torch.int64, (cnt, P.W_u_pitch), "u"),
+                                          _dev_ptr(v, torch.int64, (cnt, P.W_v), "v"), keys.handle,
+                                          _dev_ptr(key_idx, torch.int32, (cnt,), "key_idx"),
+                                          _dev_ptr(m_out, torch.uint8, (cnt, P.k), "m_out"), _stream(stream)))
+    return m_out
+
+
+def hqc_staged_workspace_bytes(level: int, count: int) -> int:
+    return int(load().hqc_staged_workspace_bytes(level, count))
+
+
+def hqc_decrypt_batch_staged(level, u, v, y=None, keys: Keyset = None, key_idx=None, workspace=None,
+                             m_out=None, stream=None):
+    """Plain per-stage form (three kernels, intermediates in `workspace`)."""
+    torch = _torch()
+    P = hqc_get_params(level)
+    u, v = _as_u64(u), _as_u64(v)
+    cnt = u.shape[0]
+    if m_out is None:
+        m_out = torch.empty((cnt, P.k), dtype=torch.uint8, device=u.device)
+    need = hqc_staged_workspace_bytes(level, cnt)
+    if workspace is None:
+        workspace = torch.empty(max(need, 16), dtype=torch.uint8, device=u.device)
+    yp = ctypes.c_void_p()
+    kp = ctypes.c_void_p()
+    ip = ctypes.c_void_p()
+    if keys is not None:
+        kp = keys.handle
+        ip = _dev_ptr(key_idx, torch.int32, (cnt,), "key_idx")
+    else:
+        y = y.view(torch.int32) if y.dtype == torch.uint32 else y
+        yp = _dev_ptr(y, torch.int32, (cnt, P.w), "y")
+    _check(load().hqc_decrypt_batch_staged(level, cnt, _dev_ptr(u, torch.int64, (cnt, P.W_u_pitch), "u"),
+                                           _dev_ptr(v, torch.int64, (cnt, P.W_v), "v"), yp, kp, ip,
+                                           _dev_ptr(workspace, torch.uint8, None, "workspace"),
+                                           workspace.numel(), _dev_ptr(m_out, torch.uint8, (cnt, P.k), "m_out"),
+                                           _stream(stream)))
+    return m_out
+
+
+def hqc_decrypt_debug(level, u, v, y, stream=None):
+    """Per-stage decryption returning every intermediate of Algorithm 2."""
+    torch = _torch()
+    P = hqc_get_params(level)
+    u, v = _as_u64(u), _as_u64(v)
+    y = y.view(torch.int32) if y.dtype == torch.uint32 else y
+    cnt = u.shape[0]
+    dev = u.device
+    nr = 2 * P.delta
+    out = dict(t=torch.zeros((cnt, P.W_v), dtype=torch.int64, device=dev),
+               w=torch.zeros((cnt, P.W_v), dtype=torch.int64, device=dev),
+               r=torch.zeros((cnt, P.n1), dtype=torch.uint8, device=dev),
+               S=torch.zeros((cnt, nr), dtype=torch.uint8, device=dev),
+               lam=torch.zeros((cnt, nr + 1), dtype=torch.uint8, device=dev),
+               L=torch.zeros((cnt,), dtype=torch.int32, device=dev),
+               errmask=torch.zeros((cnt, P.n1), dtype=torch.uint8, device=dev),
+               errval=torch.zeros((cnt, P.n1), dtype=torch.uint8, device=dev),
+               cw=torch.zeros((cnt, P.n1), dtype=torch.uint8, device=dev),
+               flag=torch.zeros((cnt,), dtype=torch.int32, device=dev),
+               m=torch.zeros((cnt, P.k), dtype=torch.uint8, device=dev))
+    d = _Dump(*[ctypes.c_void_p(out[f].data_ptr()) for f, _ in _Dump._fields_])
+    _check(load().hqc_decrypt_debug(level, cnt, _dev_ptr(u, torch.int64, (cnt, P.W_u_pitch), "u"),
+                                    _dev_ptr(v, torch.int64, (cnt, P.W_v), "v"),
+                                    _dev_ptr(y, torch.int32, (cnt, P.w), "y"), ctypes.byref(d),
+                                    _dev_ptr(out["m"], torch.uint8, (cnt, P.k), "m"), _stream(stream)))
+    return out
+
+
+def hqc_mixed_workspace_bytes() -> int:
+    return int(load().hqc_mixed_workspace_bytes())
+
+
+def hqc_decrypt_mixed(items, arena, keys, m_arena, workspace=None, stream=None):
+    """One persistent launch over mixed-level items.
+
+    items: uint8 CUDA tensor viewing an array of ITEM_DTYPE records;
+    arena: int64 CUDA tensor of u/v words; keys: (Keyset|None) x 3 for
+    levels 1, 3, 5; m_arena: uint8 CUDA tensor."""
+    torch = _torch()
+    if items.dtype != torch.uint8 or items.numel() % ITEM_DTYPE.itemsize:
+        raise TypeError("items must be a uint8 tensor of packed ITEM_DTYPE records")
+    cnt = items.numel() // ITEM_DTYPE.itemsize
+    arena = _as_u64(arena)
+    if workspace is None:
+        workspace = torch.zeros(hqc_mixed_workspace_bytes(), dtype=torch.uint8, device=arena.device)
+    karr = (ctypes.c_void_p * 3)(*[(k.handle if k is not None else None) for k in keys])
+    _check(load().hqc_decrypt_mixed(cnt, _dev_ptr(items, torch.uint8, None, "items"),
+                                    _dev_ptr(arena, torch.int64, None, "arena"), arena.numel(), karr,
+                                    _dev_ptr(m_arena, torch.uint8, None, "m_arena"), m_arena.numel(),
+                                    _dev_ptr(workspace, torch.uint8, None, "workspace"), workspace.numel(),
+                                    _stream(stream)))
+    return m_arena
+
+
+def hqc_set_launch_config(level: int, warps_per_cta: int = 0, ctas_per_sm: int = 0):
+    cfg = _LaunchCfg(warps_per_cta, ctas_per_sm)
+    _check(load().hqc_set_launch_config(level, ctypes.byref(cfg)))
+
+
+def hqc_get_launch_shape(level: int, keyed: bool = True):
+    w, c, g = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().hqc_get_launch_shape(level, int(keyed), ctypes.byref(w), ctypes.byref(c), ctypes.byref(g)))
+    return dict(warps_per_cta=w.value, ctas_per_sm=c.value, grid=g.value)
+
+
+def hqc_keygen_batch(level, h, x, y, s_out=None, stream=None):
+    torch = _torch()
+    P = hqc_get_params(level)
+    h = _as_u64(h)
+    nk = h.shape[0]
+    if s_out is None:
+        s_out = torch.empty((nk, P.W_u_pitch), dtype=torch.int64, device=h.device)
+    x = x.view(torch.int32) if x.dtype == torch.uint32 else x
+    y = y.view(torch.int32) if y.dtype == torch.uint32 else y
+    _check(load().hqc_keygen_batch(level, nk, _dev_ptr(h, torch.int64, (nk, P.W_u_pitch), "h"),
+                                   _dev_ptr(x, torch.int32, (nk, P.w), "x"), _dev_ptr(y, torch.int32, (nk, P.w), "y"),
+                                   _dev_ptr(s_out, torch.int64, (nk, P.W_u_pitch), "s_out"), _stream(stream)))
+    return s_out
+
+
+def hqc_encrypt_batch(level, h, s, key_idx, m, r1, r2, e, u_out=None, v_out=None, stream=None):
+    torch = _torch()
+    P = hqc_get_params(level)
+    h, s = _as_u64(h), _as_u64(s)
+    nk = h.shape[0]
+    cnt = m.shape[0]
+    dev = m.device
+    if u_out is None:
+        u_out = torch.empty((cnt, P.W_u_pitch), dtype=torch.int64, device=dev)
+    if v_out is None:
+        v_out = torch.empty((cnt, P.W_v), dtype=torch.int64, device=dev)
+    r1, r2, e = [t.view(torch.int32) if t.dtype == torch.uint32 else t for t in (r1, r2, e)]
+    _check(load().hqc_encrypt_batch(level, cnt, _dev_ptr(h, torch.int64, (nk, P.W_u_pitch), "h"),
+                                    _dev_ptr(s, torch.int64, (nk, P.W_u_pitch), "s"), nk,
+                                    _dev_ptr(key_idx, torch.int32, (cnt,), "key_idx"),
+                                    _dev_ptr(m, torch.uint8, (cnt, P.k), "m"),
+                                    _dev_ptr(r1, torch.int32, (cnt, P.wr), "r1"),
+                                    _dev_ptr(r2, torch.int32, (cnt, P.wr), "r2"),
+                                    _dev_ptr(e, torch.int32, (cnt, P.we), "e"),
+                                    _dev_ptr(u_out, torch.int64, (cnt, P.W_u_pitch), "u_out"),
+                                    _dev_ptr(v_out, torch.int64, (cnt, P.W_v), "v_out"), _stream(stream)))
+    return u_out, v_out

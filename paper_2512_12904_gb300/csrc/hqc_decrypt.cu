@@ -1,0 +1,320 @@
+// Decryption kernels for sm_103a:
+//   * k_decrypt_fused  -- persistent kernel, one warp per ciphertext at a
+//     time, S1-S9 fused with every intermediate in shared memory/registers;
+//   * k_decrypt_mixed  -- the same for a shuffled HQC-1/3/5 item list with a
+//     dynamic work counter;
+//   * k_stage_*        -- the plain one-kernel-per-stage form (product, RM,
+//     RS) with intermediates in global memory, also used by the debug path
+//     that dumps every intermediate.
+#include <cuda_runtime.h>
+
+#include "hqc_device.cuh"
+#include "hqc_internal.h"
+
+namespace hqc {
+
+int level_index(int level) { return level == 1 ? 0 : level == 3 ? 1 : level == 5 ? 2 : -1; }
+
+constexpr int FUSED_MAX_THREADS = 512;
+
+// ---------------------------------------------------------------------------
+// Fused persistent kernel, one level.
+// ---------------------------------------------------------------------------
+template <int LEVEL, bool KEYED>
+__global__ void __launch_bounds__(FUSED_MAX_THREADS, 1) k_decrypt_fused(DecArgs a) {
+  using LV = Level<LEVEL>;
+  extern __shared__ __align__(16) uint8_t smem[];
+  gf_tables_init(smem, threadIdx.x, blockDim.x);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const GF gf(smem, lane);
+  uint32_t* ws = reinterpret_cast<uint32_t*>(smem + GF_TABLE_BYTES) + warp * LV::WARP_WORDS;
+  for (int64_t it = (int64_t)blockIdx.x * nw + warp; it < a.count; it += (int64_t)gridDim.x * nw) {
+    const uint32_t* yrow;
+    if (KEYED) {
+      const uint32_t ki = (uint32_t)__ldg(a.key_idx + it);
+      yrow = a.y + (ki < (uint64_t)a.nkeys ? (int64_t)ki : 0) * LV::w;  // out-of-range index -> key 0
+    } else {
+      yrow = a.y + it * LV::w;
+    }
+    decrypt_one<LV, !KEYED>(gf, ws, lane, a.u + it * LV::W_u_pitch, a.v + it * LV::W_v, yrow, a.m + it * LV::k);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fused persistent kernel over a mixed-level item list.  Each warp claims
+// the next item from a.counter (or walks a static stride when no counter is
+// given); shared memory per warp is sized for HQC-5.  Items whose level,
+// key or offsets fall outside the given arrays are skipped.
+// ---------------------------------------------------------------------------
+constexpr int MIXED_WARP_WORDS = cmax(Level<1>::WARP_WORDS, cmax(Level<3>::WARP_WORDS, Level<5>::WARP_WORDS));
+
+template <class LV>
+__device__ __forceinline__ void mixed_item(const GF& gf, uint32_t* ws, int lane, const MixedArgs& a,
+                                           const MixedItem& it) {
+  const int li = LV::level == 1 ? 0 : LV::level == 3 ? 1 : 2;
+  const bool ok = (uint32_t)it.key < (uint64_t)a.nkeys[li] && it.u_off >= 0 && (it.u_off & 1) == 0 &&
+                  it.u_off + LV::W_u_pitch <= a.arena_words && it.v_off >= 0 &&
+                  it.v_off + LV::W_v <= a.arena_words && it.m_off >= 0 && it.m_off + LV::k <= a.m_bytes;
+  if (!ok) return;
+  decrypt_one<LV, false>(gf, ws, lane, a.arena + it.u_off, a.arena + it.v_off, a.keys[li] + (int64_t)it.key * LV::w,
+                         a.m + it.m_off);
+}
+
+__global__ void __launch_bounds__(FUSED_MAX_THREADS, 1) k_decrypt_mixed(MixedArgs a) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  gf_tables_init(smem, threadIdx.x, blockDim.x);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const GF gf(smem, lane);
+  uint32_t* ws = reinterpret_cast<uint32_t*>(smem + GF_TABLE_BYTES) + warp * MIXED_WARP_WORDS;
+  const int64_t stride = (int64_t)gridDim.x * nw;
+  int64_t it = (int64_t)blockIdx.x * nw + warp;
+  if (a.counter) {
+    uint32_t c = 0;
+    if (lane == 0) c = atomicAdd(a.counter, 1u);
+    it = (int64_t)__shfl_sync(FULL_MASK, c, 0);
+  }
+  while (it < a.count) {
+    const MixedItem item = a.items[it];
+    if (item.level == 1) mixed_item<Level<1>>(gf, ws, lane, a, item);
+    else if (item.level == 3) mixed_item<Level<3>>(gf, ws, lane, a, item);
+    else if (item.level == 5) mixed_item<Level<5>>(gf, ws, lane, a, item);
+    if (a.counter) {
+      uint32_t c = 0;
+      if (lane == 0) c = atomicAdd(a.counter, 1u);
+      it = (int64_t)__shfl_sync(FULL_MASK, c, 0);
+    } else {
+      it += stride;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Plain per-stage form.
+// K1: product + XOR with v (warp per ciphertext), w (and t) to global.
+// ---------------------------------------------------------------------------
+constexpr int STAGE_THREADS = 256;
+
+template <int LEVEL, bool KEYED, bool WITH_T>
+__global__ void __launch_bounds__(STAGE_THREADS) k_stage_product(DecArgs a, uint64_t* w_out, uint64_t* t_out) {
+  using LV = Level<LEVEL>;
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t it = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (it >= a.count) return;
+  uint32_t* ws = reinterpret_cast<uint32_t*>(smem) + warp * LV::WARP_WORDS;
+  const uint32_t* yrow;
+  if (KEYED) {
+    const uint32_t ki = (uint32_t)__ldg(a.key_idx + it);
+    yrow = a.y + (ki < (uint64_t)a.nkeys ? (int64_t)ki : 0) * LV::w;
+  } else {
+    yrow = a.y + it * LV::w;
+  }
+  load_supports<LV::n, LV::w>(ws + LV::U2W, yrow, lane);
+  build_doubled<LV::n, LV::W_u_pitch, LV::U2W>(ws, a.u + it * LV::W_u_pitch, lane);
+  uint32_t acc[LV::WPT];
+  rot_xor_product<LV::WPT, LV::w, !KEYED>(ws, ws + LV::U2W, lane, acc);
+  const uint32_t* v32 = reinterpret_cast<const uint32_t*>(a.v + it * LV::W_v);
+  uint32_t* w32 = reinterpret_cast<uint32_t*>(w_out + it * LV::W_v);
+  uint32_t* t32 = WITH_T ? reinterpret_cast<uint32_t*>(t_out + it * LV::W_v) : nullptr;
+#pragma unroll
+  for (int k = 0; k < LV::WPT; k++) {
+    const int i = lane * LV::WPT + k;
+    if (i < LV::W_v32) {
+      if (WITH_T) t32[i] = acc[k];
+      w32[i] = acc[k] ^ v32[i];
+    }
+  }
+}
+
+// K2: one thread per (ciphertext, RS symbol): duplicated RM decode.
+template <int LEVEL>
+__global__ void __launch_bounds__(STAGE_THREADS) k_stage_rm(int64_t count, const uint64_t* __restrict__ w,
+                                                           uint8_t* __restrict__ r_out) {
+  using LV = Level<LEVEL>;
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t it = g / LV::n1;
+  const int j = (int)(g - it * LV::n1);
+  if (it >= count) return;
+  const uint32_t* blk = reinterpret_cast<const uint32_t*>(w + it * LV::W_v) + j * (LV::n2 / 32);
+  r_out[it * LV::n1 + j] = (uint8_t)rm_decode_block<LV::mult>(blk);
+}
+
+// K3: one warp per ciphertext: Reed-Solomon decode (and the debug dump).
+constexpr int RS_SCRATCH_WORDS = 192;
+
+template <int LEVEL, bool DEBUG>
+__global__ void __launch_bounds__(STAGE_THREADS) k_stage_rs(int64_t count, const uint8_t* __restrict__ r_in,
+                                                           uint8_t* __restrict__ m_out, DebugArgs d) {
+  using LV = Level<LEVEL>;
+  static_assert(LV::RS_END - LV::RS_R <= RS_SCRATCH_WORDS, "RS scratch");
+  extern __shared__ __align__(16) uint8_t smem[];
+  gf_tables_init(smem, threadIdx.x, blockDim.x);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t it = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (it >= count) return;
+  const GF gf(smem, lane);
+  uint32_t* rs = reinterpret_cast<uint32_t*>(smem + GF_TABLE_BYTES) + warp * RS_SCRATCH_WORDS;
+  uint8_t* rb = reinterpret_cast<uint8_t*>(rs);
+  for (int j = lane; j < LV::n1; j += 32) rb[j] = r_in[it * LV::n1 + j];
+  __syncwarp();
+  if (DEBUG) {
+    RSDebugRow row{d.S + it * LV::NR, d.lam + it * LV::CAP, d.L + it,  d.errmask + it * LV::n1,
+                   d.errval + it * LV::n1, d.cw + it * LV::n1, d.flag + it};
+    rs_decode_warp<LV, true>(gf, rs, lane, m_out + it * LV::k, &row);
+  } else {
+    rs_decode_warp<LV, false>(gf, rs, lane, m_out + it * LV::k, nullptr);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launch helpers
+// ---------------------------------------------------------------------------
+template <int LEVEL>
+static size_t fused_smem(int warps) {
+  return (size_t)GF_TABLE_BYTES + (size_t)warps * Level<LEVEL>::WARP_WORDS * 4;
+}
+
+static int device_props(int* sms, int* smem_optin) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return dev;
+}
+
+template <class KernelT>
+static cudaError_t shape_for(KernelT kern, size_t per_warp, const LaunchCfg& cfg, int* warps, int* ctas,
+                             int* grid, size_t* smem_bytes) {
+  int sms = 0, optin = 0;
+  device_props(&sms, &optin);
+  int nw = cfg.warps_per_cta;
+  if (nw <= 0) {
+    nw = (int)((optin - GF_TABLE_BYTES) / per_warp);
+    if (nw > FUSED_MAX_THREADS / 32) nw = FUSED_MAX_THREADS / 32;
+  }
+  if (nw < 1) nw = 1;
+  if (nw > FUSED_MAX_THREADS / 32) return cudaErrorInvalidValue;
+  const size_t sm = GF_TABLE_BYTES + (size_t)nw * per_warp;
+  if (sm > (size_t)optin) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, nw * 32, sm);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  int c = cfg.ctas_per_sm > 0 ? cfg.ctas_per_sm : occ;
+  if (c > occ) c = occ;
+  *warps = nw;
+  *ctas = c;
+  *grid = sms * c;
+  *smem_bytes = sm;
+  return cudaSuccess;
+}
+
+template <int LEVEL, bool KEYED>
+static cudaError_t fused_level(const DecArgs& a, cudaStream_t st, const LaunchCfg& cfg, bool launch, int* warps,
+                               int* ctas, int* grid) {
+  int nw = 0, c = 0, g = 0;
+  size_t sm = 0;
+  cudaError_t e = shape_for(k_decrypt_fused<LEVEL, KEYED>, (size_t)Level<LEVEL>::WARP_WORDS * 4, cfg, &nw, &c, &g, &sm);
+  if (e != cudaSuccess) return e;
+  if (warps) *warps = nw;
+  if (ctas) *ctas = c;
+  if (grid) *grid = g;
+  if (!launch || a.count == 0) return cudaSuccess;
+  const int64_t need = (a.count + nw - 1) / nw;
+  if (need < g) g = (int)need;
+  k_decrypt_fused<LEVEL, KEYED><<<g, nw * 32, sm, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fused(int level, bool keyed, const DecArgs& a, cudaStream_t st, const LaunchCfg& cfg) {
+  switch (level) {
+    case 1: return keyed ? fused_level<1, true>(a, st, cfg, true, 0, 0, 0) : fused_level<1, false>(a, st, cfg, true, 0, 0, 0);
+    case 3: return keyed ? fused_level<3, true>(a, st, cfg, true, 0, 0, 0) : fused_level<3, false>(a, st, cfg, true, 0, 0, 0);
+    case 5: return keyed ? fused_level<5, true>(a, st, cfg, true, 0, 0, 0) : fused_level<5, false>(a, st, cfg, true, 0, 0, 0);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t fused_occupancy(int level, bool keyed, const LaunchCfg& cfg, int* warps, int* ctas, int* grid) {
+  DecArgs none;
+  switch (level) {
+    case 1: return keyed ? fused_level<1, true>(none, 0, cfg, false, warps, ctas, grid) : fused_level<1, false>(none, 0, cfg, false, warps, ctas, grid);
+    case 3: return keyed ? fused_level<3, true>(none, 0, cfg, false, warps, ctas, grid) : fused_level<3, false>(none, 0, cfg, false, warps, ctas, grid);
+    case 5: return keyed ? fused_level<5, true>(none, 0, cfg, false, warps, ctas, grid) : fused_level<5, false>(none, 0, cfg, false, warps, ctas, grid);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_mixed(const MixedArgs& a, cudaStream_t st, const LaunchCfg& cfg) {
+  int nw = 0, c = 0, g = 0;
+  size_t sm = 0;
+  cudaError_t e = shape_for(k_decrypt_mixed, (size_t)MIXED_WARP_WORDS * 4, cfg, &nw, &c, &g, &sm);
+  if (e != cudaSuccess) return e;
+  if (a.count == 0) return cudaSuccess;
+  const int64_t need = (a.count + nw - 1) / nw;
+  if (need < g) g = (int)need;
+  k_decrypt_mixed<<<g, nw * 32, sm, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int LEVEL, bool KEYED, bool DEBUG>
+static cudaError_t staged_level(const DecArgs& a, uint64_t* w, uint8_t* r, const DebugArgs* d, cudaStream_t st) {
+  using LV = Level<LEVEL>;
+  if (a.count == 0) return cudaSuccess;
+  const int wpb = STAGE_THREADS / 32;
+  // K1
+  {
+    auto kern = k_stage_product<LEVEL, KEYED, DEBUG>;
+    const size_t sm = (size_t)wpb * LV::WARP_WORDS * 4;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = (a.count + wpb - 1) / wpb;
+    kern<<<(unsigned)blocks, STAGE_THREADS, sm, st>>>(a, w, DEBUG ? d->t : nullptr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  // K2
+  {
+    const int64_t threads = a.count * LV::n1;
+    const int64_t blocks = (threads + STAGE_THREADS - 1) / STAGE_THREADS;
+    k_stage_rm<LEVEL><<<(unsigned)blocks, STAGE_THREADS, 0, st>>>(a.count, w, r);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  // K3
+  {
+    auto kern = k_stage_rs<LEVEL, DEBUG>;
+    const size_t sm = GF_TABLE_BYTES + (size_t)wpb * RS_SCRATCH_WORDS * 4;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = (a.count + wpb - 1) / wpb;
+    DebugArgs dd{};
+    if (DEBUG) dd = *d;
+    kern<<<(unsigned)blocks, STAGE_THREADS, sm, st>>>(a.count, r, a.m, dd);
+    return cudaGetLastError();
+  }
+}
+
+cudaError_t launch_staged(int level, bool keyed, const DecArgs& a, uint64_t* w, uint8_t* r, cudaStream_t st) {
+  switch (level) {
+    case 1: return keyed ? staged_level<1, true, false>(a, w, r, nullptr, st) : staged_level<1, false, false>(a, w, r, nullptr, st);
+    case 3: return keyed ? staged_level<3, true, false>(a, w, r, nullptr, st) : staged_level<3, false, false>(a, w, r, nullptr, st);
+    case 5: return keyed ? staged_level<5, true, false>(a, w, r, nullptr, st) : staged_level<5, false, false>(a, w, r, nullptr, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_debug(int level, const DecArgs& a, const DebugArgs& d, cudaStream_t st) {
+  switch (level) {
+    case 1: return staged_level<1, false, true>(a, d.w, d.r, &d, st);
+    case 3: return staged_level<3, false, true>(a, d.w, d.r, &d, st);
+    case 5: return staged_level<5, false, true>(a, d.w, d.r, &d, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace hqc

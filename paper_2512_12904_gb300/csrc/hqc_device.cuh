@@ -1,0 +1,476 @@
+// Device building blocks of batched HQC.PKE decryption on sm_103a.
+//
+// Every routine is warp- or thread-level, has a fixed trip count that
+// depends only on the (public) level, and selects with masks instead of
+// branching on ciphertext or key data, so the control flow of a
+// decryption does not depend on secrets (HQC's constant-time requirement,
+// Sec. III-B and III-D of the paper).
+#pragma once
+#include <cstdint>
+#include "hqc_params.cuh"
+
+namespace hqc {
+
+constexpr unsigned FULL_MASK = 0xFFFFFFFFu;
+
+// ---------------------------------------------------------------------------
+// GF(2^8) = GF(2)[x]/(x^8+x^4+x^3+x^2+1), alpha = x.
+// Log/antilog tables live in shared memory, replicated once per lane so a
+// warp's 32 lookups always hit 32 different banks: the access time does not
+// depend on the (secret) indices.
+//   exp: entries e in [0, 512): alpha^(e mod 255) for e < 511, exp[511] = 0
+//   log: entries a in [0, 256): log_alpha(a), log[0] = 511
+// With log 0 = 511, a*b = exp[min(log a + log b, 511)] for all a, b.
+// ---------------------------------------------------------------------------
+constexpr int GF_EXP_BYTES = 512 * 32;
+constexpr int GF_LOG_BYTES = 256 * 32 * 2;
+constexpr int GF_TABLE_BYTES = GF_EXP_BYTES + GF_LOG_BYTES;
+constexpr uint32_t GF_LOG_ZERO = 511;
+
+__device__ __forceinline__ uint32_t sel(bool c, uint32_t a, uint32_t b) {
+  uint32_t m = 0u - (uint32_t)c;
+  return (a & m) | (b & ~m);
+}
+
+__device__ __forceinline__ uint32_t gf_xtime(uint32_t a) {
+  return ((a << 1) ^ (0x11Du & (0u - (a >> 7)))) & 0xFFu;
+}
+
+// Fill both tables; called by every thread of the block, then __syncthreads.
+__device__ inline void gf_tables_init(uint8_t* smem, int tid, int nthreads) {
+  uint8_t* ex = smem;
+  uint16_t* lg = reinterpret_cast<uint16_t*>(smem + GF_EXP_BYTES);
+  for (int e = tid; e < 512; e += nthreads) {
+    uint32_t v = 0;
+    if (e < 511) {
+      v = 1;
+      const int ee = e % 255;
+      for (int i = 0; i < ee; i++) v = gf_xtime(v);
+    }
+    for (int l = 0; l < 32; l++) ex[((e & ~3) << 5) + (l << 2) + (e & 3)] = (uint8_t)v;
+    if (e < 255)
+      for (int l = 0; l < 32; l++) lg[((v & ~1u) << 5) + (l << 1) + (v & 1u)] = (uint16_t)e;
+  }
+  if (tid < 32) lg[(tid << 1)] = (uint16_t)GF_LOG_ZERO;  // log 0 in every replica
+}
+
+struct GF {
+  const uint8_t* ex;
+  const uint16_t* lg;
+  uint32_t lane;
+  __device__ __forceinline__ GF(const uint8_t* smem, uint32_t lane_)
+      : ex(smem), lg(reinterpret_cast<const uint16_t*>(smem + GF_EXP_BYTES)), lane(lane_) {}
+  // e in [0, 511]
+  __device__ __forceinline__ uint32_t exp(uint32_t e) const {
+    return ex[((e & ~3u) << 5) + (lane << 2) + (e & 3u)];
+  }
+  // a in [0, 255]
+  __device__ __forceinline__ uint32_t log(uint32_t a) const {
+    return lg[((a & ~1u) << 5) + (lane << 1) + (a & 1u)];
+  }
+  // product of two elements given by their logs (511 = zero)
+  __device__ __forceinline__ uint32_t mul_l(uint32_t la, uint32_t lb) const {
+    return exp(min(la + lb, GF_LOG_ZERO));
+  }
+  __device__ __forceinline__ uint32_t mul(uint32_t a, uint32_t b) const { return mul_l(log(a), log(b)); }
+  // a / b from logs, with x / 0 := 0 and 0 / x = 0
+  __device__ __forceinline__ uint32_t div_l(uint32_t la, uint32_t lb) const {
+    const uint32_t e = la + 255u - lb;
+    return exp(sel(max(la, lb) >= GF_LOG_ZERO, GF_LOG_ZERO, e));
+  }
+};
+
+// ---------------------------------------------------------------------------
+// S1/S2: stage u in shared memory as the doubled 2n-bit string u || u.
+// Bits of u at positions >= n (the padding of the last word and the pad
+// word) are cleared, so garbage there never reaches the product.
+// PITCH64 = 64-bit words per HBM row (even, 16-byte aligned rows).
+// ---------------------------------------------------------------------------
+template <int N, int PITCH64, int U2W>
+__device__ __forceinline__ void build_doubled(uint32_t* u2, const uint64_t* __restrict__ urow, int lane) {
+  constexpr int N32 = (N + 31) / 32, R = N & 31, F = N >> 5;
+  const uint4* src = reinterpret_cast<const uint4*>(urow);
+  uint4* dst = reinterpret_cast<uint4*>(u2);
+#pragma unroll 2
+  for (int i = lane; i < PITCH64 / 2; i += 32) {
+    uint4 x = __ldcs(src + i);
+    uint32_t wv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      const int idx = 4 * i + c;
+      uint32_t keep = idx < F ? 0xFFFFFFFFu : 0u;
+      if (R) keep = idx == F ? ((1u << R) - 1u) : keep;
+      wv[c] &= keep;
+    }
+    dst[i] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+  }
+  __syncwarp();
+  // second copy: word a >= N32 holds bits [32a - N, 32a - N + 32) of u
+#pragma unroll 2
+  for (int a = N32 + lane; a < U2W; a += 32) {
+    const int o = 32 * a - N;
+    const int kw = o >> 5, sh = o & 31;
+    const uint32_t lo = kw < N32 ? u2[kw] : 0u;
+    const uint32_t hi = kw + 1 < N32 ? u2[kw + 1] : 0u;
+    u2[a] = __funnelshift_r(lo, hi, sh);
+  }
+  __syncwarp();
+  // straddle word: the first bits of the second copy start at bit R of word F
+  if (R && lane == 0) u2[F] |= u2[0] << R;
+  __syncwarp();
+}
+
+// Support entry p -> packed word: q0 = n - p (so the rotation by p reads
+// u2 from bit 32 i + q0), bit 31 = "p < n".  An entry p >= n packs to 0 and
+// its contribution is masked off.
+template <int N, int W>
+__device__ __forceinline__ void load_supports(uint32_t* sup, const uint32_t* __restrict__ yrow, int lane) {
+  for (int t = lane; t < W; t += 32) {
+    const uint32_t p = __ldg(yrow + t);
+    const uint32_t q0 = (uint32_t)N - p;
+    sup[t] = sel(p < (uint32_t)N, q0 | 0x80000000u, 0u);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// S3 (Eq. 1): t = XOR over p in Supp(y) of x^p u, truncated to the first
+// 32*32*WPT bits.  Lane l owns output words [l*WPT, l*WPT + WPT).
+// Word i of x^p u is the 32-bit window of u2 at bit 32 i + n - p: two
+// neighbouring u2 words joined by one funnel shift.  The lane's strip of
+// WPT + 1 u2 words is read once per support entry; WPT odd keeps the
+// warp's reads on 32 distinct banks for every rotation.
+// ---------------------------------------------------------------------------
+template <int WPT, int W, bool MASKED>
+__device__ __forceinline__ void rot_xor_product(const uint32_t* u2, const uint32_t* sup, int lane,
+                                                uint32_t (&acc)[WPT]) {
+#pragma unroll
+  for (int k = 0; k < WPT; k++) acc[k] = 0;
+  const uint32_t* base = u2 + lane * WPT;
+  if (MASKED) {
+#pragma unroll 1
+    for (int t = 0; t < W; t++) {
+      const uint32_t e = sup[t];
+      const uint32_t s = e & 31u;
+      const uint32_t msk = (uint32_t)((int32_t)e >> 31);
+      const uint32_t* src = base + ((e & 0x7FFFFFFFu) >> 5);
+      uint32_t lo = src[0];
+#pragma unroll
+      for (int k = 0; k < WPT; k++) {
+        const uint32_t hi = src[k + 1];
+        acc[k] ^= __funnelshift_r(lo, hi, s) & msk;
+        lo = hi;
+      }
+    }
+  } else {
+    // validated supports: two entries per pass so each accumulator update
+    // is a single three-input XOR
+#pragma unroll 1
+    for (int t = 0; t + 1 < W; t += 2) {
+      const uint2 e = *reinterpret_cast<const uint2*>(sup + t);
+      const uint32_t s0 = e.x & 31u, s1 = e.y & 31u;
+      const uint32_t* a0 = base + ((e.x & 0x7FFFFFFFu) >> 5);
+      const uint32_t* a1 = base + ((e.y & 0x7FFFFFFFu) >> 5);
+      uint32_t lo0 = a0[0], lo1 = a1[0];
+#pragma unroll
+      for (int k = 0; k < WPT; k++) {
+        const uint32_t hi0 = a0[k + 1], hi1 = a1[k + 1];
+        acc[k] ^= __funnelshift_r(lo0, hi0, s0) ^ __funnelshift_r(lo1, hi1, s1);
+        lo0 = hi0;
+        lo1 = hi1;
+      }
+    }
+    if (W & 1) {
+      const uint32_t e = sup[W - 1];
+      const uint32_t s = e & 31u;
+      const uint32_t* src = base + ((e & 0x7FFFFFFFu) >> 5);
+      uint32_t lo = src[0];
+#pragma unroll
+      for (int k = 0; k < WPT; k++) {
+        const uint32_t hi = src[k + 1];
+        acc[k] ^= __funnelshift_r(lo, hi, s);
+        lo = hi;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// S5-S7: decode one duplicated RM(1,7) block (mult copies of 128 bits at
+// blk, 16-byte aligned) to one byte.
+//   s_i = mult - 2 * #(copies with bit i set)           (S5)
+//   F(a) = sum_i s_i (-1)^{popcount(a & i)}, 7 butterfly stages (S6)
+//   byte = a* + 128 [F(a*) < 0], a* = argmax |F|, ties -> smallest a (S7)
+// The 128 values are held as 64 packed pairs of 16-bit halves with a bias
+// of 2^15 per half (|F| <= 640), so one 32-bit add/sub does two
+// butterflies.  Register r = 16 t + q holds element indices 32 t + q (low
+// half) and 32 t + q + 16 (high half); the stage on index bit 4 (the two
+// halves) is folded into the argmax.
+// ---------------------------------------------------------------------------
+template <int MULT>
+__device__ __forceinline__ uint32_t rm_decode_block(const uint32_t* blk) {
+  constexpr uint32_t BIAS = 0x8000u;
+  constexpr uint32_t BP = BIAS * 0x10001u;
+  constexpr uint32_t K = (BIAS + MULT) * 0x10001u;
+  uint32_t p0[4], p1[4], p2[4];
+  {
+    uint4 cp[MULT];
+#pragma unroll
+    for (int c = 0; c < MULT; c++) cp[c] = *reinterpret_cast<const uint4*>(blk + 4 * c);
+#pragma unroll
+    for (int t = 0; t < 4; t++) {
+      uint32_t b[MULT];
+#pragma unroll
+      for (int c = 0; c < MULT; c++)
+        b[c] = t == 0 ? cp[c].x : t == 1 ? cp[c].y : t == 2 ? cp[c].z : cp[c].w;
+      // bit-sliced population count of the copies
+      const uint32_t s1 = b[0] ^ b[1] ^ b[2];
+      const uint32_t k1 = (b[0] & b[1]) | (b[2] & (b[0] ^ b[1]));
+      if (MULT == 3) {
+        p0[t] = s1;
+        p1[t] = k1;
+        p2[t] = 0;
+      } else {
+        const uint32_t d = b[MULT > 3 ? 3 : 0], e = b[MULT > 4 ? 4 : 0];
+        const uint32_t k2 = (s1 & d) | (e & (s1 ^ d));
+        p0[t] = s1 ^ d ^ e;
+        p1[t] = k1 ^ k2;
+        p2[t] = k1 & k2;
+      }
+    }
+  }
+  uint32_t R[64];
+#pragma unroll
+  for (int t = 0; t < 4; t++) {
+#pragma unroll
+    for (int q = 0; q < 16; q++) {
+      uint32_t cnt = ((p0[t] >> q) & 0x10001u) + (((p1[t] >> q) & 0x10001u) << 1);
+      if (MULT == 5) cnt += ((p2[t] >> q) & 0x10001u) << 2;
+      R[16 * t + q] = K - 2u * cnt;
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < 6; b++) {
+#pragma unroll
+    for (int r = 0; r < 64; r++) {
+      if (!(r & (1 << b))) {
+        const uint32_t X = R[r], Y = R[r | (1 << b)];
+        R[r] = X + Y - BP;
+        R[r | (1 << b)] = X - Y + BP;
+      }
+    }
+  }
+  uint32_t best = 0;
+#pragma unroll
+  for (int r = 0; r < 64; r++) {
+    const int lo = (int)(R[r] & 0xFFFFu) - (int)BIAS;
+    const int hi = (int)(R[r] >> 16) - (int)BIAS;
+    const int f0 = lo + hi, f1 = lo - hi;
+    const uint32_t idx0 = (uint32_t)((r & 15) | ((r >> 4) << 5));
+    const uint32_t key0 = ((uint32_t)abs(f0) << 8) | ((127u - idx0) << 1) | ((uint32_t)f0 >> 31);
+    const uint32_t key1 = ((uint32_t)abs(f1) << 8) | ((127u - (idx0 | 16u)) << 1) | ((uint32_t)f1 >> 31);
+    best = max(best, max(key0, key1));
+  }
+  const uint32_t a = 127u - ((best >> 1) & 127u);
+  return a | ((best & 1u) << 7);
+}
+
+// ---------------------------------------------------------------------------
+// S8-S9: Reed-Solomon decoding of one received word by one warp.
+//   syndromes S_i = sum_j r_j alpha^{i j}, i = 1..2 delta    (Sec. III-D)
+//   Berlekamp-Massey, exactly 2 delta iterations, Lambda and x^m B kept
+//   with 2 delta + 1 coefficients spread over the lanes
+//   Chien: position j in error iff Lambda(alpha^{-j}) = 0
+//   Forney: e_j = Omega(alpha^{-j}) / Lambda'(alpha^{-j}), Omega = S Lambda
+//   mod x^{2 delta}
+// The received bytes r[0, n1) are the first bytes of the scratch rs (at
+// least RS_END - RS_R words of shared memory).  With
+// ALL_POS false only the k message positions are evaluated (m is all the
+// decryption returns); with ALL_POS true every position is evaluated and
+// the intermediates are written to dbg.
+// ---------------------------------------------------------------------------
+struct RSDebugRow {
+  uint8_t* S;        // 2 delta
+  uint8_t* lam;      // 2 delta + 1
+  int32_t* L;        // 1
+  uint8_t* errmask;  // n1
+  uint8_t* errval;   // n1
+  uint8_t* cw;       // n1
+  int32_t* flag;     // 1
+};
+
+template <class LV, bool ALL_POS>
+__device__ __forceinline__ void rs_decode_warp(const GF& gf, uint32_t* rs, int lane, uint8_t* __restrict__ m_out,
+                                               const RSDebugRow* dbg) {
+  constexpr int n1 = LV::n1, k = LV::k, NR = LV::NR, CAP = LV::CAP, delta = LV::delta;
+  const uint8_t* r = reinterpret_cast<const uint8_t*>(rs);
+  uint16_t* logr = reinterpret_cast<uint16_t*>(rs + (LV::RS_LOGR - LV::RS_R));
+  uint16_t* logS = reinterpret_cast<uint16_t*>(rs + (LV::RS_LOGS - LV::RS_R));
+  uint16_t* logLam = reinterpret_cast<uint16_t*>(rs + (LV::RS_LOGLAM - LV::RS_R));
+  uint16_t* logOm = reinterpret_cast<uint16_t*>(rs + (LV::RS_LOGOM - LV::RS_R));
+
+  for (int j = lane; j < n1; j += 32) logr[j] = (uint16_t)gf.log(r[j]);
+  __syncwarp();
+
+  // syndromes: lane owns i = lane + 1 + 32 s
+  constexpr int NS = cdiv(NR, 32);
+#pragma unroll
+  for (int s = 0; s < NS; s++) {
+    const uint32_t i = (uint32_t)(lane + 1 + 32 * s);
+    uint32_t acc = 0, e = 0;
+#pragma unroll 2
+    for (int j = 0; j < n1; j++) {
+      acc ^= gf.exp(min((uint32_t)logr[j] + e, GF_LOG_ZERO));
+      e += i;
+      e = e >= 255u ? e - 255u : e;
+    }
+    if (i <= (uint32_t)NR) {
+      logS[i - 1] = (uint16_t)gf.log(acc);
+      if (ALL_POS) dbg->S[i - 1] = (uint8_t)acc;
+    }
+  }
+  __syncwarp();
+
+  // Berlekamp-Massey; lane owns coefficient c = lane + 32 x
+  constexpr int NC = cdiv(CAP, 32);
+  uint32_t lam[NC], bp[NC];
+#pragma unroll
+  for (int x = 0; x < NC; x++) {
+    const int c = lane + 32 * x;
+    lam[x] = c == 0;
+    bp[x] = c == 1;  // x^m B with m = 1, B = 1
+  }
+  uint32_t lb = 0, L = 0;  // log b (b = 1), LFSR length
+#pragma unroll 1
+  for (int rr = 0; rr < NR; rr++) {
+    uint32_t part = 0;
+#pragma unroll
+    for (int x = 0; x < NC; x++) {
+      const int c = lane + 32 * x;
+      const bool in = c <= rr;
+      const uint32_t ls = logS[in ? rr - c : 0];
+      part ^= sel(in, gf.mul_l(gf.log(lam[x]), ls), 0u);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part ^= __shfl_xor_sync(FULL_MASK, part, o);
+    const uint32_t d = part;
+    const uint32_t ld = gf.log(d);
+    const uint32_t lcoef = sel(d == 0, GF_LOG_ZERO, sel(ld >= lb, ld - lb, ld + 255u - lb));
+    const bool cond = (d != 0) & (2 * L <= (uint32_t)rr);
+    uint32_t src[NC];
+#pragma unroll
+    for (int x = 0; x < NC; x++) {
+      const uint32_t T = lam[x];
+      lam[x] = T ^ gf.mul_l(lcoef, gf.log(bp[x]));
+      src[x] = sel(cond, T, bp[x]);
+    }
+#pragma unroll
+    for (int x = 0; x < NC; x++) {
+      const uint32_t up = __shfl_up_sync(FULL_MASK, src[x], 1);
+      const uint32_t carry = x > 0 ? __shfl_sync(FULL_MASK, src[x > 0 ? x - 1 : 0], 31) : 0u;
+      const uint32_t nb = lane == 0 ? carry : up;
+      bp[x] = (lane + 32 * x) < CAP ? nb : 0u;
+    }
+    lb = sel(cond, ld, lb);
+    L = sel(cond, (uint32_t)rr + 1u - L, L);
+  }
+#pragma unroll
+  for (int x = 0; x < NC; x++) {
+    const int c = lane + 32 * x;
+    if (c < CAP) {
+      logLam[c] = (uint16_t)gf.log(lam[x]);
+      if (ALL_POS) dbg->lam[c] = (uint8_t)lam[x];
+    }
+  }
+  if (ALL_POS && lane == 0) *dbg->L = (int32_t)L;
+  __syncwarp();
+
+  // Omega_k = sum_{c <= k} Lambda_c S_{k+1-c}, k < 2 delta
+#pragma unroll
+  for (int x = 0; x < NS; x++) {
+    const int kk = lane + 32 * x;
+    uint32_t om = 0;
+#pragma unroll 4
+    for (int c = 0; c < NR; c++) {
+      const bool in = c <= kk;
+      const uint32_t t = gf.mul_l(logLam[c], logS[in ? kk - c : 0]);
+      om ^= sel(in, t, 0u);
+    }
+    if (kk < NR) logOm[kk] = (uint16_t)gf.log(om);
+  }
+  __syncwarp();
+
+  // Chien + Forney at position j: powers of alpha^{-j}
+  constexpr int NPOS = ALL_POS ? cdiv(n1, 32) : 1;
+  uint32_t roots = 0;
+#pragma unroll
+  for (int y = 0; y < NPOS; y++) {
+    const int j = ALL_POS ? lane + 32 * y : (n1 - k) + lane;
+    const bool valid = ALL_POS ? j < n1 : lane < k;
+    const uint32_t jj = valid ? (uint32_t)j : 0u;
+    const uint32_t step = jj == 0 ? 0u : 255u - jj;
+    uint32_t ec = 0, ecp = 0, lamv = 0, omv = 0, dlv = 0;
+#pragma unroll
+    for (int c = 0; c < CAP; c++) {
+      const uint32_t llc = logLam[c];
+      lamv ^= gf.exp(min(llc + ec, GF_LOG_ZERO));
+      if (c & 1) dlv ^= gf.exp(min(llc + ecp, GF_LOG_ZERO));
+      if (c < NR) omv ^= gf.exp(min((uint32_t)logOm[c] + ec, GF_LOG_ZERO));
+      ecp = ec;
+      ec += step;
+      ec = ec >= 255u ? ec - 255u : ec;
+    }
+    const bool root = lamv == 0;
+    const uint32_t ev = sel(root, gf.div_l(gf.log(omv), gf.log(dlv)), 0u);
+    const uint32_t cwj = (uint32_t)r[jj] ^ ev;
+    if (ALL_POS) {
+      roots += __popc(__ballot_sync(FULL_MASK, root && valid));
+      if (valid) {
+        dbg->errmask[j] = (uint8_t)root;
+        dbg->errval[j] = (uint8_t)ev;
+        dbg->cw[j] = (uint8_t)cwj;
+        if (j >= n1 - k) m_out[j - (n1 - k)] = (uint8_t)cwj;
+      }
+    } else if (valid) {
+      m_out[lane] = (uint8_t)cwj;
+    }
+  }
+  if (ALL_POS && lane == 0) *dbg->flag = (int32_t)((L > (uint32_t)delta) || (roots != L));
+}
+
+// ---------------------------------------------------------------------------
+// Whole decryption of one ciphertext by one warp (S1-S9).
+// ws: WARP_WORDS of shared memory owned by this warp.
+// ---------------------------------------------------------------------------
+template <class LV, bool MASKED>
+__device__ __forceinline__ void decrypt_one(const GF& gf, uint32_t* ws, int lane, const uint64_t* __restrict__ urow,
+                                            const uint64_t* __restrict__ vrow, const uint32_t* __restrict__ yrow,
+                                            uint8_t* __restrict__ mrow) {
+  constexpr int WPT = LV::WPT, W_v32 = LV::W_v32;
+  uint32_t* u2 = ws;
+  uint32_t* sup = ws + LV::U2W;
+  load_supports<LV::n, LV::w>(sup, yrow, lane);
+  build_doubled<LV::n, LV::W_u_pitch, LV::U2W>(u2, urow, lane);
+  uint32_t acc[WPT];
+  rot_xor_product<WPT, LV::w, MASKED>(u2, sup, lane, acc);
+  // S4: w = v + t, truncated (only the first n1*n2 bits were computed)
+  const uint32_t* v32 = reinterpret_cast<const uint32_t*>(vrow);
+#pragma unroll
+  for (int k = 0; k < WPT; k++) {
+    const int i = lane * WPT + k;
+    if (i < W_v32) acc[k] ^= __ldcs(v32 + i);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < WPT; k++) {
+    const int i = lane * WPT + k;
+    if (i < W_v32) u2[i] = acc[k];
+  }
+  __syncwarp();
+  uint8_t* r = reinterpret_cast<uint8_t*>(ws + LV::RS_R);
+  for (int j = lane; j < LV::n1; j += 32) r[j] = (uint8_t)rm_decode_block<LV::mult>(u2 + j * (LV::n2 / 32));
+  __syncwarp();
+  rs_decode_warp<LV, false>(gf, ws + LV::RS_R, lane, mrow, nullptr);
+  __syncwarp();
+}
+
+}  // namespace hqc

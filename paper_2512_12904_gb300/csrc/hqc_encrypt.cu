@@ -1,0 +1,227 @@
+// Batched HQC.PKE key generation core (Algorithm 3: s = x + h*y) and
+// encryption (Algorithm 1: u = r1 + h*r2, v = first n1*n2 bits of
+// mG + s*r2 + e) on the same rotate-XOR product as decryption.  One warp
+// per item; used to build synthetic ciphertexts on the device.
+#include <cuda_runtime.h>
+
+#include "hqc_device.cuh"
+#include "hqc_internal.h"
+
+namespace hqc {
+
+constexpr int ENC_THREADS = 256;
+
+// Product of the dense row `dense` by the support `supp` (w entries, may
+// be invalid -> masked) over the full n bits, left in u2[0, N32) with the
+// bits >= n of the last word cleared.
+template <class LV, int W, int WPT, int U2W>
+__device__ __forceinline__ void full_product_to_smem(uint32_t* u2, uint32_t* sup, const uint64_t* dense,
+                                                     const uint32_t* supp, int lane) {
+  constexpr int N32 = LV::N32, R = LV::n & 31;
+  load_supports<LV::n, W>(sup, supp, lane);
+  build_doubled<LV::n, LV::W_u_pitch, U2W>(u2, dense, lane);
+  uint32_t acc[WPT];
+  rot_xor_product<WPT, W, true>(u2, sup, lane, acc);
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < WPT; k++) {
+    const int i = lane * WPT + k;
+    if (i < N32) u2[i] = (R && i == N32 - 1) ? (acc[k] & ((1u << R) - 1u)) : acc[k];
+  }
+  __syncwarp();
+}
+
+template <int W, int NBITS>
+__device__ __forceinline__ void xor_support_bits(uint32_t* out, const uint32_t* supp, int lane) {
+  for (int t = lane; t < W; t += 32) {
+    const uint32_t p = __ldg(supp + t);
+    if (p < (uint32_t)NBITS) atomicXor(out + (p >> 5), 1u << (p & 31));
+  }
+  __syncwarp();
+}
+
+template <int PITCH64, int NWORDS32>
+__device__ __forceinline__ void store_row(uint64_t* dst, const uint32_t* src, int lane) {
+  uint32_t* d32 = reinterpret_cast<uint32_t*>(dst);
+  for (int i = lane; i < 2 * PITCH64; i += 32) d32[i] = i < NWORDS32 ? src[i] : 0u;
+}
+
+template <int LEVEL>
+__global__ void __launch_bounds__(ENC_THREADS) k_keygen(int64_t nkeys, const uint64_t* __restrict__ h,
+                                                       const uint32_t* __restrict__ x, const uint32_t* __restrict__ y,
+                                                       uint64_t* __restrict__ s) {
+  using LV = Level<LEVEL>;
+  constexpr int WARP_W = LV::U2W_FULL + LV::WP;
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t it = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (it >= nkeys) return;
+  uint32_t* u2 = reinterpret_cast<uint32_t*>(smem) + warp * WARP_W;
+  uint32_t* sup = u2 + LV::U2W_FULL;
+  full_product_to_smem<LV, LV::w, LV::WPT_FULL, LV::U2W_FULL>(u2, sup, h + it * LV::W_u_pitch, y + it * LV::w, lane);
+  xor_support_bits<LV::w, LV::n>(u2, x + it * LV::w, lane);
+  store_row<LV::W_u_pitch, LV::N32>(s + it * LV::W_u_pitch, u2, lane);
+}
+
+// Codeword bits of one byte B = a + 128 b, word t of 4: bit q is
+// b ^ parity(a & (32 t + q)).
+__device__ __forceinline__ uint32_t rm_codeword_word(uint32_t B, int t) {
+  const uint32_t a = B & 127u;
+  uint32_t w = 0;
+  w ^= 0xAAAAAAAAu & (0u - (a & 1u));
+  w ^= 0xCCCCCCCCu & (0u - ((a >> 1) & 1u));
+  w ^= 0xF0F0F0F0u & (0u - ((a >> 2) & 1u));
+  w ^= 0xFF00FF00u & (0u - ((a >> 3) & 1u));
+  w ^= 0xFFFF0000u & (0u - ((a >> 4) & 1u));
+  w ^= 0u - ((a >> 5) & 1u & (uint32_t)t);
+  w ^= 0u - ((a >> 6) & 1u & ((uint32_t)t >> 1));
+  w ^= 0u - (B >> 7);
+  return w;
+}
+
+template <int LEVEL>
+__global__ void __launch_bounds__(ENC_THREADS) k_encrypt(int64_t count, const uint64_t* __restrict__ h,
+                                                        const uint64_t* __restrict__ s, int64_t nkeys,
+                                                        const int32_t* __restrict__ key_idx,
+                                                        const uint8_t* __restrict__ m, const uint32_t* __restrict__ r1,
+                                                        const uint32_t* __restrict__ r2, const uint32_t* __restrict__ e,
+                                                        uint64_t* __restrict__ u, uint64_t* __restrict__ v) {
+  using LV = Level<LEVEL>;
+  constexpr int NR = LV::NR, n1 = LV::n1, k = LV::k;
+  constexpr int WARP_W = LV::U2W_FULL + LV::WP_R;
+  extern __shared__ __align__(16) uint8_t smem[];
+  gf_tables_init(smem, threadIdx.x, blockDim.x);
+  uint8_t* g = smem + GF_TABLE_BYTES;  // generator, NR + 1 coefficients (64 bytes reserved)
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const GF gf0(smem, 0);
+    for (int d = 0; d <= NR; d++) g[d] = d == 0;
+    for (int i = 1; i <= NR; i++) {
+      const uint32_t root = gf0.exp((uint32_t)i);
+      for (int d = i; d >= 0; d--) g[d] = (uint8_t)((d > 0 ? g[d - 1] : 0u) ^ gf0.mul(g[d], root));
+    }
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t it = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (it >= count) return;
+  const GF gf(smem, lane);
+  uint32_t* u2 = reinterpret_cast<uint32_t*>(smem + GF_TABLE_BYTES + 64) + warp * WARP_W;
+  uint32_t* sup = u2 + LV::U2W_FULL;
+  const uint32_t ki = (uint32_t)key_idx[it];
+  const int64_t key = ki < (uint64_t)nkeys ? (int64_t)ki : 0;
+
+  // u = r1 + h * r2
+  full_product_to_smem<LV, LV::wr, LV::WPT_FULL, LV::U2W_FULL>(u2, sup, h + key * LV::W_u_pitch, r2 + it * LV::wr, lane);
+  xor_support_bits<LV::wr, LV::n>(u2, r1 + it * LV::wr, lane);
+  store_row<LV::W_u_pitch, LV::N32>(u + it * LV::W_u_pitch, u2, lane);
+  __syncwarp();
+
+  // s * r2, truncated to n1*n2 bits, plus e
+  build_doubled<LV::n, LV::W_u_pitch, LV::U2W_FULL>(u2, s + key * LV::W_u_pitch, lane);
+  {
+    uint32_t acc[LV::WPT];
+    rot_xor_product<LV::WPT, LV::wr, true>(u2, sup, lane, acc);
+    __syncwarp();
+#pragma unroll
+    for (int kk = 0; kk < LV::WPT; kk++) {
+      const int i = lane * LV::WPT + kk;
+      if (i < LV::W_v32) u2[i] = acc[kk];
+    }
+    __syncwarp();
+  }
+  xor_support_bits<LV::we, LV::n1 * LV::n2>(u2, e + it * LV::we, lane);
+
+  // RS systematic encoding by the division register; lane owns parity
+  // coefficient c = lane + 32 x
+  constexpr int NX = cdiv(NR, 32);
+  uint32_t par[NX];
+#pragma unroll
+  for (int x = 0; x < NX; x++) par[x] = 0;
+  const uint8_t* mrow = m + it * k;
+  for (int i = k - 1; i >= 0; i--) {
+    const uint32_t top = __shfl_sync(FULL_MASK, par[(NR - 1) / 32], (NR - 1) % 32);
+    const uint32_t fb = (uint32_t)mrow[i] ^ top;
+    uint32_t nxt[NX];
+#pragma unroll
+    for (int x = 0; x < NX; x++) {
+      const uint32_t up = __shfl_up_sync(FULL_MASK, par[x], 1);
+      const uint32_t carry = x > 0 ? __shfl_sync(FULL_MASK, par[x > 0 ? x - 1 : 0], 31) : 0u;
+      const int c = lane + 32 * x;
+      const uint32_t prev = lane == 0 ? carry : up;
+      nxt[x] = c < NR ? (prev ^ gf.mul(g[c], fb)) : 0u;
+    }
+#pragma unroll
+    for (int x = 0; x < NX; x++) par[x] = nxt[x];
+  }
+  uint8_t* cw = reinterpret_cast<uint8_t*>(u2 + LV::W_v32);
+#pragma unroll
+  for (int x = 0; x < NX; x++) {
+    const int c = lane + 32 * x;
+    if (c < NR) cw[c] = (uint8_t)par[x];
+  }
+  for (int i = lane; i < k; i += 32) cw[NR + i] = mrow[i];
+  __syncwarp();
+  // duplicated RM(1,7) encoding of every symbol, added into the product
+  for (int j = lane; j < n1; j += 32) {
+    const uint32_t B = cw[j];
+#pragma unroll
+    for (int t = 0; t < 4; t++) {
+      const uint32_t cwt = rm_codeword_word(B, t);
+#pragma unroll
+      for (int rcp = 0; rcp < LV::mult; rcp++) u2[j * (LV::n2 / 32) + 4 * rcp + t] ^= cwt;
+    }
+  }
+  __syncwarp();
+  store_row<LV::W_v, LV::W_v32>(v + it * LV::W_v, u2, lane);
+}
+
+template <int LEVEL>
+static cudaError_t keygen_level(int64_t nkeys, const uint64_t* h, const uint32_t* x, const uint32_t* y, uint64_t* s,
+                                cudaStream_t st) {
+  using LV = Level<LEVEL>;
+  if (nkeys == 0) return cudaSuccess;
+  const int wpb = ENC_THREADS / 32;
+  const size_t sm = (size_t)wpb * (LV::U2W_FULL + LV::WP) * 4;
+  cudaError_t e = cudaFuncSetAttribute(k_keygen<LEVEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_keygen<LEVEL><<<(unsigned)((nkeys + wpb - 1) / wpb), ENC_THREADS, sm, st>>>(nkeys, h, x, y, s);
+  return cudaGetLastError();
+}
+
+template <int LEVEL>
+static cudaError_t encrypt_level(int64_t count, const uint64_t* h, const uint64_t* s, int64_t nkeys, const int32_t* ki,
+                                 const uint8_t* m, const uint32_t* r1, const uint32_t* r2, const uint32_t* e,
+                                 uint64_t* u, uint64_t* v, cudaStream_t st) {
+  using LV = Level<LEVEL>;
+  if (count == 0) return cudaSuccess;
+  const int wpb = 4;
+  const size_t sm = GF_TABLE_BYTES + 64 + (size_t)wpb * (LV::U2W_FULL + LV::WP_R) * 4;
+  cudaError_t err = cudaFuncSetAttribute(k_encrypt<LEVEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (err != cudaSuccess) return err;
+  k_encrypt<LEVEL><<<(unsigned)((count + wpb - 1) / wpb), wpb * 32, sm, st>>>(count, h, s, nkeys, ki, m, r1, r2, e, u, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_keygen(int level, int64_t nkeys, const uint64_t* h, const uint32_t* x, const uint32_t* y,
+                          uint64_t* s, cudaStream_t st) {
+  switch (level) {
+    case 1: return keygen_level<1>(nkeys, h, x, y, s, st);
+    case 3: return keygen_level<3>(nkeys, h, x, y, s, st);
+    case 5: return keygen_level<5>(nkeys, h, x, y, s, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_encrypt(int level, int64_t count, const uint64_t* h, const uint64_t* s, int64_t nkeys,
+                           const int32_t* key_idx, const uint8_t* m, const uint32_t* r1, const uint32_t* r2,
+                           const uint32_t* e, uint64_t* u, uint64_t* v, cudaStream_t st) {
+  switch (level) {
+    case 1: return encrypt_level<1>(count, h, s, nkeys, key_idx, m, r1, r2, e, u, v, st);
+    case 3: return encrypt_level<3>(count, h, s, nkeys, key_idx, m, r1, r2, e, u, v, st);
+    case 5: return encrypt_level<5>(count, h, s, nkeys, key_idx, m, r1, r2, e, u, v, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace hqc

@@ -1,0 +1,75 @@
+// Internal launch interface between the C ABI (hqc_abi.cu) and the kernel
+// translation units.  Not installed; the public interface is
+// include/hqc_gb300.h.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hqc {
+
+// Launch shape of the persistent fused kernel: warps per block and blocks
+// per SM (0 = the library's choice for the level).
+struct LaunchCfg {
+  int warps_per_cta = 0;
+  int ctas_per_sm = 0;
+};
+
+struct DecArgs {
+  int64_t count = 0;
+  const uint64_t* u = nullptr;      // [count][W_u_pitch]
+  const uint64_t* v = nullptr;      // [count][W_v]
+  const uint32_t* y = nullptr;      // literal: [count][w]; keyed: [nkeys][w]
+  const int32_t* key_idx = nullptr; // keyed: [count]
+  int64_t nkeys = 0;
+  uint8_t* m = nullptr;             // [count][k]
+};
+
+struct DebugArgs {
+  uint64_t* t;        // [count][W_v]
+  uint64_t* w;        // [count][W_v]
+  uint8_t* r;         // [count][n1]
+  uint8_t* S;         // [count][2 delta]
+  uint8_t* lam;       // [count][2 delta + 1]
+  int32_t* L;         // [count]
+  uint8_t* errmask;   // [count][n1]
+  uint8_t* errval;    // [count][n1]
+  uint8_t* cw;        // [count][n1]
+  int32_t* flag;      // [count]
+};
+
+// Mixed-level work item (see hqc_item_t in the public header).
+struct MixedItem {
+  int32_t level;
+  int32_t key;
+  int64_t u_off;
+  int64_t v_off;
+  int64_t m_off;
+};
+
+struct MixedArgs {
+  int64_t count = 0;
+  const MixedItem* items = nullptr;
+  const uint64_t* arena = nullptr;  // u and v rows
+  int64_t arena_words = 0;
+  const uint32_t* keys[3] = {nullptr, nullptr, nullptr};  // levels 1, 3, 5: [nkeys][w]
+  int64_t nkeys[3] = {0, 0, 0};
+  uint8_t* m = nullptr;
+  int64_t m_bytes = 0;
+  uint32_t* counter = nullptr;      // dynamic scheduling counter (zeroed before launch)
+};
+
+int level_index(int level);  // 1 -> 0, 3 -> 1, 5 -> 2, else -1
+
+cudaError_t launch_fused(int level, bool keyed, const DecArgs& a, cudaStream_t st, const LaunchCfg& cfg);
+cudaError_t launch_staged(int level, bool keyed, const DecArgs& a, uint64_t* w_ws, uint8_t* r_ws, cudaStream_t st);
+cudaError_t launch_debug(int level, const DecArgs& a, const DebugArgs& d, cudaStream_t st);
+cudaError_t launch_mixed(const MixedArgs& a, cudaStream_t st, const LaunchCfg& cfg);
+cudaError_t fused_occupancy(int level, bool keyed, const LaunchCfg& cfg, int* warps, int* ctas_per_sm, int* grid);
+
+cudaError_t launch_keygen(int level, int64_t nkeys, const uint64_t* h, const uint32_t* x, const uint32_t* y,
+                          uint64_t* s, cudaStream_t st);
+cudaError_t launch_encrypt(int level, int64_t count, const uint64_t* h, const uint64_t* s, int64_t nkeys,
+                           const int32_t* key_idx, const uint8_t* m, const uint32_t* r1, const uint32_t* r2,
+                           const uint32_t* e, uint64_t* u, uint64_t* v, cudaStream_t st);
+
+}  // namespace hqc

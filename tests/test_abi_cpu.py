@@ -1,0 +1,90 @@
+"""Host-side checks of the C-ABI library that need no GPU: it builds for
+sm_103a, loads, exports every entry point the public header declares, and
+its host logic (parameters, argument checks, workspace sizes) is right."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2512_12904_gb300 as hqc
+from conftest import ROOT, read_golden
+
+HEADER = os.path.join(ROOT, "include", "hqc_gb300.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hqc_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = hqc.load()
+    names = declared_functions()
+    assert len(names) >= 16
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+@pytest.mark.parametrize("level", [1, 3, 5])
+def test_params_match_table1_and_oracle(level):
+    rows = {int(r[0].split("-")[1]): r for r in read_golden("table1_params.txt")}
+    r = rows[level]
+    p = hqc.hqc_get_params(level)
+    assert (p.n, p.w, p.we, p.wr, p.n1, p.k) == tuple(int(x) for x in (r[1], r[2], r[3], r[3], r[4], r[5]))
+    assert 2 * p.delta + 1 == int(r[6]) and p.n2 == int(r[7]) and 64 * p.mult == int(r[9])
+    o = oracle.params(level)
+    assert (p.W_u, p.W_u_pitch, p.W_v, p.delta, p.mult) == (o.W_u, o.W_u_pitch, o.W_v, o.delta, o.mult)
+
+
+def test_argument_errors_are_reported_without_a_gpu():
+    lib = hqc.load()
+    p = hqc._Params()
+    assert lib.hqc_get_params(2, ctypes.byref(p)) == -1
+    assert b"level" in lib.hqc_last_error()
+    assert lib.hqc_get_params(1, None) == -1
+    # count 0 is a no-op; bad level and negative count are rejected first
+    assert lib.hqc_decrypt_batch(1, 0, None, None, None, None, None) == 0
+    assert lib.hqc_decrypt_batch(4, 1, None, None, None, None, None) == -1
+    assert lib.hqc_decrypt_batch(1, -5, None, None, None, None, None) == -1
+    assert lib.hqc_decrypt_batch(1, 3, None, None, None, None, None) == -1
+    # misaligned u
+    assert lib.hqc_decrypt_batch(1, 1, ctypes.c_void_p(8), ctypes.c_void_p(16), ctypes.c_void_p(16),
+                                 ctypes.c_void_p(16), None) == -1
+    assert b"aligned" in lib.hqc_last_error()
+    cfg = hqc._LaunchCfg(99, 0)
+    assert lib.hqc_set_launch_config(1, ctypes.byref(cfg)) == -1
+    assert lib.hqc_set_launch_config(7, None) == -1
+    assert lib.hqc_set_launch_config(1, None) == 0
+
+
+def test_keyset_validation_rejects_bad_supports_before_any_copy():
+    lib = hqc.load()
+    P = hqc.hqc_get_params(1)
+    h = ctypes.c_void_p()
+    bad = np.arange(P.w, dtype=np.uint32).reshape(1, P.w).copy()
+    bad[0, 3] = P.n
+    assert lib.hqc_keys_register(1, 1, bad.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)) == -1
+    assert b">= n" in lib.hqc_last_error()
+    dup = np.arange(P.w, dtype=np.uint32).reshape(1, P.w).copy()
+    dup[0, 7] = dup[0, 2]
+    assert lib.hqc_keys_register(1, 1, dup.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)) == -1
+    assert b"repeats" in lib.hqc_last_error()
+    assert lib.hqc_keys_register(1, 0, bad.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)) == -1
+
+
+@pytest.mark.parametrize("level", [1, 3, 5])
+def test_workspace_sizes(level):
+    p = hqc.hqc_get_params(level)
+    for cnt in (1, 7, 4096):
+        b = hqc.hqc_staged_workspace_bytes(level, cnt)
+        assert b >= cnt * p.W_v * 8 + cnt * p.n1 and b % 16 == 0
+    assert hqc.hqc_staged_workspace_bytes(level, 0) == 0
+    assert hqc.hqc_mixed_workspace_bytes() >= 4
+
+
+def test_item_record_layout():
+    assert hqc.ITEM_DTYPE.itemsize == 32

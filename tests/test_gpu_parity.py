@@ -1,0 +1,196 @@
+"""GPU parity: every CUDA entry point against the CPU oracle, bit-exact.
+
+Inputs come from the seeded generator and the oracle's own key generation
+and encryption; expected values come only from the oracle.  Integer and
+GF arithmetic, so the bar is exact equality of every word and byte.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from workloads import adversarial, honest, with_garbage_padding
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+LEVELS = (1, 3, 5)
+
+
+@pytest.fixture(scope="module")
+def hqc():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import paper_2512_12904_gb300 as lib
+    lib.load()
+    return lib
+
+
+def dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.view(dtype)
+    return t.cuda()
+
+
+def u64(a):
+    return dev(np.ascontiguousarray(a, np.uint64).view(np.int64))
+
+
+def i32(a):
+    return dev(np.ascontiguousarray(a).astype(np.uint32).view(np.int32))
+
+
+def host(t):
+    return t.cpu().numpy()
+
+
+def oracle_dumps(level, u, v, y):
+    keys = ["t", "w", "r", "S", "lam", "L", "errmask", "errval", "cw", "m", "flag"]
+    out = {k: [] for k in keys}
+    for i in range(u.shape[0]):
+        d = oracle.decrypt_dump(level, u[i], v[i], y[i])
+        for k in keys:
+            out[k].append(d[k])
+    return {k: np.array(vv) for k, vv in out.items()}
+
+
+@pytest.mark.parametrize("level", LEVELS)
+def test_debug_path_every_intermediate(hqc, level):
+    P, u, v, y = adversarial(level, tag=level)
+    wl = honest(level, 4, 20, first_ct=500, tag=3)
+    u = np.concatenate([u, wl.u]); v = np.concatenate([v, wl.v]); y = np.concatenate([y, wl.y_rows])
+    want = oracle_dumps(level, u, v, y)
+    got = hqc.hqc_decrypt_debug(level, u64(u), u64(v), i32(y))
+    torch.cuda.synchronize()
+    assert (host(got["t"]).view(np.uint64) == want["t"]).all()
+    assert (host(got["w"]).view(np.uint64) == want["w"]).all()
+    for k in ("r", "S", "lam", "errmask", "errval", "cw", "m"):
+        g = host(got[k])
+        bad = np.argwhere(g != want[k])
+        assert bad.size == 0, (k, bad[:5], g[tuple(bad[0])], want[k][tuple(bad[0])])
+    assert (host(got["L"]) == want["L"]).all()
+    assert (host(got["flag"]) == want["flag"]).all()
+    # the honest tail decrypts to its messages
+    assert (host(got["m"])[-20:] == wl.m).all()
+
+
+@pytest.mark.parametrize("level", LEVELS)
+def test_fused_literal_matches_oracle(hqc, level):
+    P, u, v, y = adversarial(level, tag=10 + level)
+    wl = honest(level, 5, 37, first_ct=900, tag=4)
+    u = np.concatenate([u, with_garbage_padding(P, wl.u, tag=5)]); v = np.concatenate([v, wl.v])
+    y = np.concatenate([y, wl.y_rows])
+    want = oracle.decrypt(level, u, v, y)
+    got = host(hqc.hqc_decrypt_batch(level, u64(u), u64(v), i32(y)))
+    assert (got == want).all()
+    assert (got[-37:] == wl.m).all()
+
+
+@pytest.mark.parametrize("level", LEVELS)
+def test_fused_keyed_and_staged_match_oracle(hqc, level):
+    wl = honest(level, 16, 256 if level == 1 else 96, tag=5)
+    keys = hqc.Keyset(level, wl.y)
+    kidx = dev(wl.key_idx.astype(np.int32))
+    want = oracle.decrypt(level, wl.u, wl.v, wl.y_rows)
+    assert (want == wl.m).all()
+    got = host(hqc.hqc_decrypt_batch_keyed(level, u64(wl.u), u64(wl.v), keys, kidx))
+    assert (got == want).all()
+    got2 = host(hqc.hqc_decrypt_batch_staged(level, u64(wl.u), u64(wl.v), keys=keys, key_idx=kidx))
+    assert (got2 == want).all()
+    got3 = host(hqc.hqc_decrypt_batch_staged(level, u64(wl.u), u64(wl.v), y=i32(wl.y_rows)))
+    assert (got3 == want).all()
+    keys.free()
+
+
+@pytest.mark.parametrize("level", LEVELS)
+def test_ragged_counts(hqc, level):
+    wl = honest(level, 3, 41, first_ct=3000, tag=6)
+    for cnt in (1, 2, 31, 33, 41):
+        got = host(hqc.hqc_decrypt_batch(level, u64(wl.u[:cnt]), u64(wl.v[:cnt]), i32(wl.y_rows[:cnt])))
+        assert (got == wl.m[:cnt]).all(), cnt
+    empty = hqc.hqc_decrypt_batch(level, u64(wl.u[:0]), u64(wl.v[:0]), i32(wl.y_rows[:0]))
+    assert empty.shape == (0, wl.P.k)
+
+
+@pytest.mark.parametrize("level", LEVELS)
+def test_launch_shapes_agree(hqc, level):
+    wl = honest(level, 4, 200, first_ct=7000, tag=7)
+    keys = hqc.Keyset(level, wl.y)
+    kidx = dev(wl.key_idx.astype(np.int32))
+    ref = None
+    for wpc, cps in ((0, 0), (1, 1), (3, 1), (8, 0), (16, 0)):
+        try:
+            hqc.hqc_set_launch_config(level, wpc, cps)
+            got = host(hqc.hqc_decrypt_batch_keyed(level, u64(wl.u), u64(wl.v), keys, kidx))
+        except hqc.HqcError:
+            continue  # shape does not fit on this device
+        finally:
+            hqc.hqc_set_launch_config(level, 0, 0)
+        ref = got if ref is None else ref
+        assert (got == wl.m).all()
+    assert ref is not None
+
+
+@pytest.mark.parametrize("level", LEVELS)
+def test_keygen_and_encrypt_match_oracle(hqc, level):
+    P = oracle.params(level)
+    S = synth.Shape.of(P)
+    h, x, y = synth.keys(S, 6, first=40)
+    want_s = oracle.keygen(level, h, x, y)
+    got_s = host(hqc.hqc_keygen_batch(level, u64(h), i32(x), i32(y))).view(np.uint64)
+    assert (got_s == want_s).all()
+    m, r1, r2, e = synth.ciphertext_randomness(S, 50, first=50)
+    kidx = synth.key_assignment(50, 6, tag=9)
+    want_u, want_v = oracle.encrypt(level, h, want_s, kidx, m, r1, r2, e)
+    gu, gv = hqc.hqc_encrypt_batch(level, u64(h), u64(want_s), dev(kidx.astype(np.int32)), dev(m), i32(r1), i32(r2),
+                                   i32(e))
+    assert (host(gu).view(np.uint64) == want_u).all()
+    assert (host(gv).view(np.uint64) == want_v).all()
+
+
+def test_mixed_levels_one_launch(hqc):
+    parts = {}
+    for lvl, cnt in ((1, 40), (3, 35), (5, 25)):
+        parts[lvl] = honest(lvl, 8, cnt, first_ct=20000, tag=11)
+    order = synth.shuffle(np.arange(100, dtype=np.int32), tag=12)
+    seq = [(1, i) for i in range(40)] + [(3, i) for i in range(35)] + [(5, i) for i in range(25)]
+    seq = [seq[j] for j in order]
+    items = np.zeros(len(seq), dtype=__import__("paper_2512_12904_gb300").ITEM_DTYPE)
+    arena, m_off, words = [], 0, 0
+    for idx, (lvl, i) in enumerate(seq):
+        wl = parts[lvl]
+        items[idx] = (lvl, wl.key_idx[i], words, words + wl.P.W_u_pitch, m_off)
+        arena.append(wl.u[i]); arena.append(wl.v[i])
+        words += wl.P.W_u_pitch + wl.P.W_v
+        m_off += wl.P.k
+    arena = np.concatenate(arena)
+    keys = [hqc.Keyset(l, parts[l].y) for l in (1, 3, 5)]
+    m_arena = torch.full((m_off,), 0xAA, dtype=torch.uint8, device="cuda")
+    hqc.hqc_decrypt_mixed(dev(items.view(np.uint8)), u64(arena), keys, m_arena)
+    got = host(m_arena)
+    pos = 0
+    for lvl, i in seq:
+        k = parts[lvl].P.k
+        assert (got[pos: pos + k] == parts[lvl].m[i]).all()
+        pos += k
+    # an item with an out-of-range key is skipped, the rest still decrypt
+    items2 = items.copy()
+    items2[0]["key"] = 10 ** 6
+    m2 = torch.full((m_off,), 0x55, dtype=torch.uint8, device="cuda")
+    hqc.hqc_decrypt_mixed(dev(items2.view(np.uint8)), u64(arena), keys, m2)
+    g2 = host(m2)
+    k0 = parts[seq[0][0]].P.k
+    assert (g2[:k0] == 0x55).all() and (g2[k0:] == got[k0:]).all()
+
+
+def test_full_size_hqc1_bulk_sampled(hqc):
+    # 65,536 HQC-1 ciphertexts under 256 keys in one keyed launch: every m
+    # must round-trip, and a sample is compared with the oracle's decryption
+    wl = honest(1, 256, 65536, tag=13)
+    keys = hqc.Keyset(1, wl.y)
+    got = host(hqc.hqc_decrypt_batch_keyed(1, u64(wl.u), u64(wl.v), keys, dev(wl.key_idx.astype(np.int32))))
+    assert (got == wl.m).all()
+    sample = synth.below(65536, 128, tag=14)
+    want = oracle.decrypt(1, wl.u[sample], wl.v[sample], wl.y_rows[sample])
+    assert (got[sample] == want).all()
