@@ -1,0 +1,436 @@
+#!/usr/bin/env python3
+"""Throughput of batched HQC.PKE decryption on GB300.
+
+One step = one pass of the whole decryption path (product, XOR/truncate,
+duplicated RM decode, RS decode) over one batch of synthetic ciphertexts
+that are already resident in HBM.  Default workload: HQC-1 bulk, 65,536
+ciphertexts under 256 registered keys, one fused keyed launch per step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+    python bench.py --impl reference ...     # the CPU oracle on host cores
+
+Prints one JSON line (rank 0).  Under torchrun each rank decrypts its own
+batch (weak scaling, no collective on the data path); the reported time is
+the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "HQC-1/3/5 decryptions/sec per GB300 (batched vs plain) and p99 latency"
+UNIT = "decryptions/s"
+L2_BYTES = 129 * 2 ** 20
+
+WORKLOADS = {
+    # name: (level, count, nkeys, description)
+    "hqc1-bulk": (1, 65536, 256, "HQC-1 bulk: 65536 ciphertexts under 256 keypairs, one batched keyed launch"),
+    "hqc3": (3, 32768, 128, "HQC-3 batch: 32768 ciphertexts under 128 keypairs, one batched keyed launch"),
+    "hqc5": (5, 32768, 128, "HQC-5 batch: 32768 ciphertexts under 128 keypairs, one batched keyed launch"),
+    "hqc1-plain": (1, 256, 16, "HQC-1 plain path: 256 ciphertexts under 16 keypairs"),
+}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="hqc1-bulk")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU-baseline duration")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (one process per GPU, launched by torchrun)
+# ---------------------------------------------------------------------------
+class Dist:
+    def __init__(self, want_gpus: int):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            import torch
+            torch.cuda.set_device(self.local)
+            dist.init_process_group(backend="nccl", device_id=torch.device("cuda", self.local))
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.QUERY,
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, r[5:9]):
+                if val.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# workload construction (on the device, with the library's own keygen and
+# encryption kernels; randomness from the seeded generator)
+# ---------------------------------------------------------------------------
+def make_workload(hqc, level, count, nkeys, rank, device):
+    import torch
+    import synth
+    P = hqc.hqc_get_params(level)
+    S = synth.Shape.of(P)
+    h, x, y = synth.keys(S, nkeys, first=rank * nkeys)
+    m, r1, r2, e = synth.ciphertext_randomness(S, count, first=rank * count)
+    kidx = synth.key_assignment(count, nkeys, tag=100 + level)
+    dev = lambda a, dt=None: torch.from_numpy(np.ascontiguousarray(a if dt is None else a.view(dt))).to(device)
+    h_d = dev(h, np.int64)
+    s_d = hqc.hqc_keygen_batch(level, h_d, dev(x, np.int32), dev(y, np.int32))
+    m_d = dev(m)
+    k_d = dev(kidx.astype(np.int32))
+    u_d, v_d = hqc.hqc_encrypt_batch(level, h_d, s_d, k_d, m_d, dev(r1, np.int32), dev(r2, np.int32),
+                                     dev(e, np.int32))
+    torch.cuda.synchronize()
+    keys = hqc.Keyset(level, y)
+    return P, keys, u_d, v_d, k_d, m_d, y, kidx
+
+
+def timed_steps(fn, steps, stream, dist, clocks_idx=None):
+    """Run fn() `steps` times between barriers; return (total_ms, per-step ms list, clocks)."""
+    import torch
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    dist.barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(clocks_idx) if clocks_idx is not None else None
+    with torch.cuda.stream(stream):
+        evs[0].record(stream)
+        for i in range(steps):
+            fn()
+            evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clocks = clk.stop() if clk else None
+    per = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
+    return evs[0].elapsed_time(evs[-1]), per, clocks
+
+
+def pct(xs, q):
+    s = sorted(xs)
+    return s[min(len(s) - 1, int(round(q / 100.0 * (len(s) - 1))))]
+
+
+def load_peaks():
+    from paper_2512_12904_gb300 import _build
+    lib = ctypes.CDLL(_build.PEAKS_LIB)
+    lib.hqc_peak_smem_read_bytes_per_s.restype = ctypes.c_double
+    lib.hqc_peak_int_ops_per_s.restype = ctypes.c_double
+    return lib.hqc_peak_smem_read_bytes_per_s(), lib.hqc_peak_int_ops_per_s()
+
+
+def measured_peaks_file():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def per_decryption_work(P):
+    """Algorithmic work of one decryption (the per-unit figures of the roofline)."""
+    W_v32 = P.n1 * P.n2 // 32
+    nr, cap = 2 * P.delta, 2 * P.delta + 1
+    smem = P.w * P.n1 * P.n2 // 8                  # rotated operand read once per support entry
+    hbm = P.W_u_pitch * 8 + P.W_v * 8 + P.k + 4     # u row, v row, m row, key index
+    gf_mults = nr * P.n1 + 2 * nr * cap + nr * nr // 2 + P.k * (2 * cap + nr)
+    int_ops = 2 * P.w * W_v32 + P.n1 * (128 * P.mult + 896 + 256) + 4 * gf_mults
+    return smem, hbm, int_ops
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(level, nkeys, count):
+    import oracle
+    import synth
+    P = oracle.params(level)
+    S = synth.Shape.of(P)
+    h, x, y = synth.keys(S, nkeys)
+    s = oracle.keygen(level, h, x, y)
+    m, r1, r2, e = synth.ciphertext_randomness(S, count)
+    kidx = synth.key_assignment(count, nkeys, tag=100 + level) % nkeys
+    u, v = oracle.encrypt(level, h, s, kidx.astype(np.int32), m, r1, r2, e)
+    return u, v, y[kidx], m
+
+
+def oracle_rate(level, nkeys, target_s, cores):
+    import oracle
+    probe = max(2 * cores, 16)
+    u, v, y, m = oracle_sample(level, nkeys, probe)
+    t = time.perf_counter()
+    oracle.decrypt(level, u, v, y, nthreads=cores)
+    rate = probe / max(time.perf_counter() - t, 1e-6)
+    n = int(max(probe, min(200000, rate * target_s)))
+    u, v, y, m = oracle_sample(level, nkeys, n)
+    t = time.perf_counter()
+    got = oracle.decrypt(level, u, v, y, nthreads=cores)
+    dt = time.perf_counter() - t
+    assert (got == m).all(), "oracle sample failed to decrypt"
+    return n / dt, n, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    level, count, nkeys, desc = WORKLOADS[args.workload]
+    cores = os.cpu_count() or 1
+    # calibrate, then size each step so the whole run takes ~2 minutes
+    probe = max(2 * cores, 16)
+    u, v, y, m = oracle_sample(level, nkeys, probe)
+    t = time.perf_counter()
+    oracle.decrypt(level, u, v, y, nthreads=cores)
+    rate = probe / max(time.perf_counter() - t, 1e-6)
+    per_step = int(max(cores, min(count, 120.0 * rate / max(1, args.steps + args.warmup))))
+    u, v, y, m = oracle_sample(level, nkeys, per_step)
+    for _ in range(args.warmup):
+        oracle.decrypt(level, u, v, y, nthreads=cores)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        got = oracle.decrypt(level, u, v, y, nthreads=cores)
+    dt = time.perf_counter() - t
+    assert (got == m).all()
+    value = per_step * args.steps / dt
+    sample = "%d of the workload's ciphertexts per step (oracle-encrypted, same seeds), %d threads" % (per_step, cores)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic", "config": {"workload": desc, "level": level, "count": count, "nkeys": nkeys},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import paper_2512_12904_gb300 as hqc
+
+    dist = Dist(args.gpus)
+    device = torch.device("cuda", dist.local)
+    torch.cuda.set_device(device)
+    hqc.load()
+    level, count, nkeys, desc = WORKLOADS[args.workload]
+    smem_peak, int_peak = load_peaks()
+    P, keys, u_d, v_d, k_d, m_ref, y_host, kidx = make_workload(hqc, level, count, nkeys, dist.rank, device)
+    m_out = torch.empty_like(m_ref)
+    stream = torch.cuda.Stream(device=device)
+    shape = hqc.hqc_get_launch_shape(level, True)
+
+    def step():
+        hqc.hqc_decrypt_batch_keyed(level, u_d, v_d, keys, k_d, m_out, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+    total_ms, per, clocks = timed_steps(step, args.steps, stream, dist, clocks_idx=dist.local)
+    max_ms = dist.max(total_ms)
+    correct = bool((m_out == m_ref).all().item())
+    wrong = int((m_out != m_ref).any(dim=1).sum().item())
+
+    # plain one-kernel-per-stage form on the same inputs
+    ws = torch.empty(hqc.hqc_staged_workspace_bytes(level, count), dtype=torch.uint8, device=device)
+    m_plain = torch.empty_like(m_ref)
+
+    def plain_step():
+        hqc.hqc_decrypt_batch_staged(level, u_d, v_d, keys=keys, key_idx=k_d, workspace=ws, m_out=m_plain,
+                                     stream=stream)
+
+    plain_steps = max(5, min(args.steps, 200))
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            plain_step()
+    plain_ms, plain_per, _ = timed_steps(plain_step, plain_steps, stream, dist)
+    plain_ms = dist.max(plain_ms)
+    plain_ok = bool((m_plain == m_ref).all().item())
+
+    # end to end through the public API with pinned host buffers
+    u_h = u_d.cpu().pin_memory()
+    v_h = v_d.cpu().pin_memory()
+    k_h = k_d.cpu().pin_memory()
+    m_h = torch.empty(m_ref.shape, dtype=torch.uint8).pin_memory()
+    u_e, v_e, k_e, m_e = torch.empty_like(u_d), torch.empty_like(v_d), torch.empty_like(k_d), torch.empty_like(m_ref)
+
+    def e2e_step():
+        u_e.copy_(u_h, non_blocking=True)
+        v_e.copy_(v_h, non_blocking=True)
+        k_e.copy_(k_h, non_blocking=True)
+        hqc.hqc_decrypt_batch_keyed(level, u_e, v_e, keys, k_e, m_e, stream=stream)
+        m_h.copy_(m_e, non_blocking=True)
+
+    e2e_steps = max(5, min(args.steps, 100))
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            e2e_step()
+    e2e_ms, _, _ = timed_steps(e2e_step, e2e_steps, stream, dist)
+    e2e_ms = dist.max(e2e_ms)
+    e2e_ok = bool((m_h == m_ref.cpu()).all().item())
+    h2d = u_h.numel() * 8 + v_h.numel() * 8 + k_h.numel() * 4
+    d2h = m_h.numel()
+
+    total_dec = dist.sum(float(count)) * args.steps
+    value = total_dec / (max_ms * 1e-3)
+    smem_b, hbm_b, int_ops = per_decryption_work(P)
+    launch_s = (total_ms / args.steps) * 1e-3  # one launch of the fused kernel per step
+    peaks = measured_peaks_file()
+    hbm_peak = peaks.get("hbm_gbs")
+    smem_ach = smem_b * count / launch_s / 1e9
+    int_ach = int_ops * count / launch_s / 1e9
+    hbm_ach = hbm_b * count / launch_s / 1e9
+    blocks = {
+        "smem": {"bound": "smem", "achieved": smem_ach, "peak": smem_peak / 1e9, "unit": "GB/s",
+                 "frac": smem_ach / (smem_peak / 1e9) if smem_peak else None, "traffic": None,
+                 "peak_source": "measured in this run: conflict-free 32-bit shared-memory loads, all SMs"},
+        "alu": {"bound": "alu", "achieved": int_ach, "peak": int_peak / 1e9, "unit": "Gop/s",
+                "frac": int_ach / (int_peak / 1e9) if int_peak else None,
+                "peak_source": "measured in this run: 32-bit funnel-shift + XOR issue rate, all SMs"},
+        "hbm": {"bound": "hbm", "achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": hbm_ach / hbm_peak if hbm_peak else None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if hbm_peak else "absent"},
+    }
+    primary = max(("smem", "alu"), key=lambda k: blocks[k]["frac"] or 0)
+    roofline = dict(blocks[primary])
+    roofline["kernel"] = "k_decrypt_fused<%d,keyed>" % level
+    roofline["traffic"] = traffic_from_profile(level)
+    roofline["others"] = {k: v for k, v in blocks.items() if k != primary}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": desc, "level": level, "count_per_gpu": count, "nkeys": nkeys,
+                   "inputs_bytes_per_gpu": int(u_d.numel() * 8 + v_d.numel() * 8),
+                   "l2": "inputs (%d MB) larger than L2 (129 MB); no flush" % ((u_d.numel() + v_d.numel()) * 8 // 2 ** 20)
+                   if (u_d.numel() + v_d.numel()) * 8 > L2_BYTES else "inputs smaller than L2",
+                   "launch": shape, "parallelism": "replicas" if dist.world > 1 else "single GPU"},
+        "correct": correct and plain_ok and e2e_ok, "wrong_messages": wrong,
+        "latency_ms": {"p50": pct(per, 50), "p99": pct(per, 99), "max": max(per),
+                       "what": "one batch of %d decryptions (launch to completion, device events)" % count},
+        "plain_per_stage": {"value": dist.sum(float(count)) * plain_steps / (plain_ms * 1e-3), "unit": UNIT,
+                            "ms_per_step": plain_ms / plain_steps, "launches_per_step": 3, "correct": plain_ok},
+        "roofline": roofline,
+        "e2e": {"value": dist.sum(float(count)) * e2e_steps / (e2e_ms * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps,
+                "api": "hqc_decrypt_batch_keyed with pinned host u, v, key_idx copied in and m copied out"},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        rate, n, dt = oracle_rate(level, nkeys, args.cpu_seconds, cores)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": "%d ciphertexts of the same workload recipe (oracle-encrypted), %.1f s" % (n, dt)}
+    keys.free()
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+    dist.close()
+    return 0
+
+
+def traffic_from_profile(level):
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary, if current."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except OSError:
+        return None
+    from paper_2512_12904_gb300 import _build
+    ent = rec.get("hqc%d" % level)
+    if not ent or ent.get("source_digest") != _build._digest():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

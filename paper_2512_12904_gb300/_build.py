@@ -15,7 +15,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libhqc_gb300.so")
+PEAKS_LIB = os.path.join(BUILD, "libhqc_peaks.so")
 SOURCES = ["hqc_decrypt.cu", "hqc_encrypt.cu", "hqc_abi.cu"]
+PEAKS_SOURCES = ["hqc_peaks.cu"]
 HEADERS = ["hqc_params.cuh", "hqc_device.cuh", "hqc_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]
@@ -28,7 +30,7 @@ def _nvcc() -> str:
 
 def _digest() -> str:
     h = hashlib.sha256()
-    files = [os.path.join(CSRC, f) for f in SOURCES + HEADERS]
+    files = [os.path.join(CSRC, f) for f in SOURCES + PEAKS_SOURCES + HEADERS]
     files.append(os.path.join(ROOT, "include", "hqc_gb300.h"))
     for f in files:
         with open(f, "rb") as fh:
@@ -42,7 +44,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     stamp = os.path.join(BUILD, "stamp")
     dig = _digest()
-    if not force and os.path.exists(LIB) and os.path.exists(stamp):
+    if not force and os.path.exists(LIB) and os.path.exists(PEAKS_LIB) and os.path.exists(stamp):
         with open(stamp) as f:
             if f.read().strip() == dig:
                 return LIB
@@ -58,17 +60,18 @@ def build(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError("nvcc failed for %s:\n%s%s" % (src, res.stdout, res.stderr))
         return obj, res.stderr
 
-    with ThreadPoolExecutor(len(SOURCES)) as ex:
-        results = list(ex.map(compile_one, SOURCES))
+    with ThreadPoolExecutor(len(SOURCES) + len(PEAKS_SOURCES)) as ex:
+        results = list(ex.map(compile_one, SOURCES + PEAKS_SOURCES))
     if verbose:
         for _, log in results:
             print(log)
-    tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp] + [o for o, _ in results]
-    res = subprocess.run(cmd, capture_output=True, text=True)
-    if res.returncode != 0:
-        raise RuntimeError("link failed:\n%s%s" % (res.stdout, res.stderr))
-    os.replace(tmp, LIB)
+    for lib, objs in ((LIB, results[:len(SOURCES)]), (PEAKS_LIB, results[len(SOURCES):])):
+        tmp = lib + ".tmp%d" % os.getpid()
+        cmd = [nvcc, *ARCH, "-shared", "-o", tmp] + [o for o, _ in objs]
+        res = subprocess.run(cmd, capture_output=True, text=True)
+        if res.returncode != 0:
+            raise RuntimeError("link failed:\n%s%s" % (res.stdout, res.stderr))
+        os.replace(tmp, lib)
     with open(stamp, "w") as f:
         f.write(dig)
     return LIB

@@ -283,8 +283,8 @@ int hqc_set_launch_config(int level, const hqc_launch_cfg_t* cfg) {
     g_cfg[idx] = hqc::LaunchCfg{};
     return HQC_OK;
   }
-  if (cfg->warps_per_cta < 0 || cfg->warps_per_cta > 16 || cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 32)
-    return fail(HQC_EINVAL, "warps_per_cta in [0, 16], ctas_per_sm in [0, 32]");
+  if (cfg->warps_per_cta < 0 || cfg->warps_per_cta > 32 || cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 32)
+    return fail(HQC_EINVAL, "warps_per_cta in [0, 32], ctas_per_sm in [0, 32]");
   g_cfg[idx].warps_per_cta = cfg->warps_per_cta;
   g_cfg[idx].ctas_per_sm = cfg->ctas_per_sm;
   return HQC_OK;

@@ -15,13 +15,20 @@ namespace hqc {
 
 int level_index(int level) { return level == 1 ? 0 : level == 3 ? 1 : level == 5 ? 2 : -1; }
 
-constexpr int FUSED_MAX_THREADS = 512;
+// Largest block of the persistent kernels per level.  Shared memory caps
+// the warps per SM at about 40 / 20 / 13 for HQC-1 / 3 / 5; the bound lets
+// the compiler spend the rest of the register file on each warp.
+template <int LEVEL> struct FusedBound;
+template <> struct FusedBound<1> { static constexpr int threads = 1024; };
+template <> struct FusedBound<3> { static constexpr int threads = 640; };
+template <> struct FusedBound<5> { static constexpr int threads = 416; };
+constexpr int MIXED_MAX_THREADS = 416;
 
 // ---------------------------------------------------------------------------
 // Fused persistent kernel, one level.
 // ---------------------------------------------------------------------------
 template <int LEVEL, bool KEYED>
-__global__ void __launch_bounds__(FUSED_MAX_THREADS, 1) k_decrypt_fused(DecArgs a) {
+__global__ void __launch_bounds__(FusedBound<LEVEL>::threads, 1) k_decrypt_fused(DecArgs a) {
   using LV = Level<LEVEL>;
   extern __shared__ __align__(16) uint8_t smem[];
   gf_tables_init(smem, threadIdx.x, blockDim.x);
@@ -61,7 +68,7 @@ __device__ __forceinline__ void mixed_item(const GF& gf, uint32_t* ws, int lane,
                          a.m + it.m_off);
 }
 
-__global__ void __launch_bounds__(FUSED_MAX_THREADS, 1) k_decrypt_mixed(MixedArgs a) {
+__global__ void __launch_bounds__(MIXED_MAX_THREADS, 1) k_decrypt_mixed(MixedArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   gf_tables_init(smem, threadIdx.x, blockDim.x);
   __syncthreads();
@@ -128,17 +135,19 @@ __global__ void __launch_bounds__(STAGE_THREADS) k_stage_product(DecArgs a, uint
   }
 }
 
-// K2: one thread per (ciphertext, RS symbol): duplicated RM decode.
+// K2: one lane pair per (ciphertext, RS symbol): duplicated RM decode.
 template <int LEVEL>
 __global__ void __launch_bounds__(STAGE_THREADS) k_stage_rm(int64_t count, const uint64_t* __restrict__ w,
                                                            uint8_t* __restrict__ r_out) {
   using LV = Level<LEVEL>;
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t it = g / LV::n1;
-  const int j = (int)(g - it * LV::n1);
-  if (it >= count) return;
+  const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 1;  // pair index
+  const int64_t total = count * LV::n1;
+  const int64_t gg = g < total ? g : total - 1;  // both lanes of every pair stay active
+  const int64_t it = gg / LV::n1;
+  const int j = (int)(gg - it * LV::n1);
   const uint32_t* blk = reinterpret_cast<const uint32_t*>(w + it * LV::W_v) + j * (LV::n2 / 32);
-  r_out[it * LV::n1 + j] = (uint8_t)rm_decode_block<LV::mult>(blk);
+  const uint32_t byte = rm_decode_pair<LV::mult>(blk, threadIdx.x & 1);
+  if (g < total && (threadIdx.x & 1) == 0) r_out[it * LV::n1 + j] = (uint8_t)byte;
 }
 
 // K3: one warp per ciphertext: Reed-Solomon decode (and the debug dump).
@@ -186,17 +195,17 @@ static int device_props(int* sms, int* smem_optin) {
 }
 
 template <class KernelT>
-static cudaError_t shape_for(KernelT kern, size_t per_warp, const LaunchCfg& cfg, int* warps, int* ctas,
-                             int* grid, size_t* smem_bytes) {
+static cudaError_t shape_for(KernelT kern, int max_threads, size_t per_warp, const LaunchCfg& cfg, int* warps,
+                             int* ctas, int* grid, size_t* smem_bytes) {
   int sms = 0, optin = 0;
   device_props(&sms, &optin);
   int nw = cfg.warps_per_cta;
   if (nw <= 0) {
     nw = (int)((optin - GF_TABLE_BYTES) / per_warp);
-    if (nw > FUSED_MAX_THREADS / 32) nw = FUSED_MAX_THREADS / 32;
+    if (nw > max_threads / 32) nw = max_threads / 32;
   }
   if (nw < 1) nw = 1;
-  if (nw > FUSED_MAX_THREADS / 32) return cudaErrorInvalidValue;
+  if (nw > max_threads / 32) return cudaErrorInvalidValue;
   const size_t sm = GF_TABLE_BYTES + (size_t)nw * per_warp;
   if (sm > (size_t)optin) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -219,7 +228,8 @@ static cudaError_t fused_level(const DecArgs& a, cudaStream_t st, const LaunchCf
                                int* ctas, int* grid) {
   int nw = 0, c = 0, g = 0;
   size_t sm = 0;
-  cudaError_t e = shape_for(k_decrypt_fused<LEVEL, KEYED>, (size_t)Level<LEVEL>::WARP_WORDS * 4, cfg, &nw, &c, &g, &sm);
+  cudaError_t e = shape_for(k_decrypt_fused<LEVEL, KEYED>, FusedBound<LEVEL>::threads,
+                            (size_t)Level<LEVEL>::WARP_WORDS * 4, cfg, &nw, &c, &g, &sm);
   if (e != cudaSuccess) return e;
   if (warps) *warps = nw;
   if (ctas) *ctas = c;
@@ -253,7 +263,7 @@ cudaError_t fused_occupancy(int level, bool keyed, const LaunchCfg& cfg, int* wa
 cudaError_t launch_mixed(const MixedArgs& a, cudaStream_t st, const LaunchCfg& cfg) {
   int nw = 0, c = 0, g = 0;
   size_t sm = 0;
-  cudaError_t e = shape_for(k_decrypt_mixed, (size_t)MIXED_WARP_WORDS * 4, cfg, &nw, &c, &g, &sm);
+  cudaError_t e = shape_for(k_decrypt_mixed, MIXED_MAX_THREADS, (size_t)MIXED_WARP_WORDS * 4, cfg, &nw, &c, &g, &sm);
   if (e != cudaSuccess) return e;
   if (a.count == 0) return cudaSuccess;
   const int64_t need = (a.count + nw - 1) / nw;
@@ -279,7 +289,7 @@ static cudaError_t staged_level(const DecArgs& a, uint64_t* w, uint8_t* r, const
   }
   // K2
   {
-    const int64_t threads = a.count * LV::n1;
+    const int64_t threads = 2 * a.count * LV::n1;
     const int64_t blocks = (threads + STAGE_THREADS - 1) / STAGE_THREADS;
     k_stage_rm<LEVEL><<<(unsigned)blocks, STAGE_THREADS, 0, st>>>(a.count, w, r);
     cudaError_t e = cudaGetLastError();

@@ -196,62 +196,73 @@ __device__ __forceinline__ void rot_xor_product(const uint32_t* u2, const uint32
 
 // ---------------------------------------------------------------------------
 // S5-S7: decode one duplicated RM(1,7) block (mult copies of 128 bits at
-// blk, 16-byte aligned) to one byte.
+// blk, 16-byte aligned) to one byte, with a PAIR of lanes per block.
 //   s_i = mult - 2 * #(copies with bit i set)           (S5)
 //   F(a) = sum_i s_i (-1)^{popcount(a & i)}, 7 butterfly stages (S6)
 //   byte = a* + 128 [F(a*) < 0], a* = argmax |F|, ties -> smallest a (S7)
-// The 128 values are held as 64 packed pairs of 16-bit halves with a bias
-// of 2^15 per half (|F| <= 640), so one 32-bit add/sub does two
-// butterflies.  Register r = 16 t + q holds element indices 32 t + q (low
-// half) and 32 t + q + 16 (high half); the stage on index bit 4 (the two
-// halves) is folded into the argmax.
+// Lane hb (= lane & 1) of the pair holds the 64 elements with index bit 6
+// equal to hb, as 32 registers of two 16-bit halves biased by 640 (|F| <=
+// 640, and F is even: a sum of 128 odd s_i).  Register r = 16 tt + q holds
+// indices q | tt << 5 | hb << 6 (low half) and the same | 16 (high half).
+// Stages on index bits 0-3 and 5 are packed adds inside a lane, bit 6 is
+// one shuffle with the partner lane, bit 4 (the halves) is the last stage.
+// The argmax runs on 16-bit keys (F + 640) / 2 * 64 + (63 - r6) -- score,
+// then smaller index -- with packed unsigned max, once for +F (b = 0) and
+// once for -F (b = 1); the half bit and b stay implicit in where the key
+// sits.  Both lanes of the pair return the byte.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t vmax_u16x2(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("max.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+
 template <int MULT>
-__device__ __forceinline__ uint32_t rm_decode_block(const uint32_t* blk) {
-  constexpr uint32_t BIAS = 0x8000u;
+__device__ __forceinline__ uint32_t rm_decode_pair(const uint32_t* blk, uint32_t hb) {
+  constexpr uint32_t BIAS = 640u;
   constexpr uint32_t BP = BIAS * 0x10001u;
   constexpr uint32_t K = (BIAS + MULT) * 0x10001u;
-  uint32_t p0[4], p1[4], p2[4];
+  constexpr uint32_t KN = 2u * BP * 32u;  // (1280 per half) * 32
+  uint32_t p0[2], p1[2], p2[2];
   {
-    uint4 cp[MULT];
+    uint2 cp[MULT];
 #pragma unroll
-    for (int c = 0; c < MULT; c++) cp[c] = *reinterpret_cast<const uint4*>(blk + 4 * c);
+    for (int c = 0; c < MULT; c++) cp[c] = *reinterpret_cast<const uint2*>(blk + 4 * c + 2 * hb);
 #pragma unroll
-    for (int t = 0; t < 4; t++) {
+    for (int tt = 0; tt < 2; tt++) {
       uint32_t b[MULT];
 #pragma unroll
-      for (int c = 0; c < MULT; c++)
-        b[c] = t == 0 ? cp[c].x : t == 1 ? cp[c].y : t == 2 ? cp[c].z : cp[c].w;
+      for (int c = 0; c < MULT; c++) b[c] = tt == 0 ? cp[c].x : cp[c].y;
       // bit-sliced population count of the copies
       const uint32_t s1 = b[0] ^ b[1] ^ b[2];
       const uint32_t k1 = (b[0] & b[1]) | (b[2] & (b[0] ^ b[1]));
       if (MULT == 3) {
-        p0[t] = s1;
-        p1[t] = k1;
-        p2[t] = 0;
+        p0[tt] = s1;
+        p1[tt] = k1;
+        p2[tt] = 0;
       } else {
         const uint32_t d = b[MULT > 3 ? 3 : 0], e = b[MULT > 4 ? 4 : 0];
         const uint32_t k2 = (s1 & d) | (e & (s1 ^ d));
-        p0[t] = s1 ^ d ^ e;
-        p1[t] = k1 ^ k2;
-        p2[t] = k1 & k2;
+        p0[tt] = s1 ^ d ^ e;
+        p1[tt] = k1 ^ k2;
+        p2[tt] = k1 & k2;
       }
     }
   }
-  uint32_t R[64];
+  uint32_t R[32];
 #pragma unroll
-  for (int t = 0; t < 4; t++) {
+  for (int tt = 0; tt < 2; tt++) {
 #pragma unroll
     for (int q = 0; q < 16; q++) {
-      uint32_t cnt = ((p0[t] >> q) & 0x10001u) + (((p1[t] >> q) & 0x10001u) << 1);
-      if (MULT == 5) cnt += ((p2[t] >> q) & 0x10001u) << 2;
-      R[16 * t + q] = K - 2u * cnt;
+      uint32_t cnt = ((p0[tt] >> q) & 0x10001u) + (((p1[tt] >> q) & 0x10001u) << 1);
+      if (MULT == 5) cnt += ((p2[tt] >> q) & 0x10001u) << 2;
+      R[16 * tt + q] = K - 2u * cnt;
     }
   }
 #pragma unroll
-  for (int b = 0; b < 6; b++) {
+  for (int b = 0; b < 5; b++) {
 #pragma unroll
-    for (int r = 0; r < 64; r++) {
+    for (int r = 0; r < 32; r++) {
       if (!(r & (1 << b))) {
         const uint32_t X = R[r], Y = R[r | (1 << b)];
         R[r] = X + Y - BP;
@@ -259,19 +270,55 @@ __device__ __forceinline__ uint32_t rm_decode_block(const uint32_t* blk) {
       }
     }
   }
+  // index bit 6: lane 0 keeps x + y, lane 1 keeps x - y (x = lane 0's value)
+#pragma unroll
+  for (int r = 0; r < 32; r++) {
+    const uint32_t Y = __shfl_xor_sync(FULL_MASK, R[r], 1);
+    R[r] = hb ? (Y - R[r] + BP) : (R[r] + Y - BP);
+  }
+  uint32_t mp[4] = {0, 0, 0, 0}, mn[4] = {0, 0, 0, 0};
+  const uint32_t cbase = (63u - 32u * hb) * 0x10001u;
+#pragma unroll
+  for (int r = 0; r < 32; r++) {
+    // index bit 4: low half -> lo + hi, high half -> lo - hi
+    const uint32_t X = R[r];
+    const uint32_t Xs = __byte_perm(X, 0, 0x1032);
+    const uint32_t A = X + Xs - BP, D = Xs - X + BP;
+    const uint32_t P = __byte_perm(A, D, 0x7610);
+    const uint32_t C = cbase - (uint32_t)r * 0x10001u;
+    mp[r & 3] = vmax_u16x2(mp[r & 3], P * 32u + C);
+    mn[r & 3] = vmax_u16x2(mn[r & 3], (KN + C) - P * 32u);
+  }
+  uint32_t MP = vmax_u16x2(vmax_u16x2(mp[0], mp[1]), vmax_u16x2(mp[2], mp[3]));
+  uint32_t MN = vmax_u16x2(vmax_u16x2(mn[0], mn[1]), vmax_u16x2(mn[2], mn[3]));
+  MP = vmax_u16x2(MP, __shfl_xor_sync(FULL_MASK, MP, 1));
+  MN = vmax_u16x2(MN, __shfl_xor_sync(FULL_MASK, MN, 1));
   uint32_t best = 0;
 #pragma unroll
-  for (int r = 0; r < 64; r++) {
-    const int lo = (int)(R[r] & 0xFFFFu) - (int)BIAS;
-    const int hi = (int)(R[r] >> 16) - (int)BIAS;
-    const int f0 = lo + hi, f1 = lo - hi;
-    const uint32_t idx0 = (uint32_t)((r & 15) | ((r >> 4) << 5));
-    const uint32_t key0 = ((uint32_t)abs(f0) << 8) | ((127u - idx0) << 1) | ((uint32_t)f0 >> 31);
-    const uint32_t key1 = ((uint32_t)abs(f1) << 8) | ((127u - (idx0 | 16u)) << 1) | ((uint32_t)f1 >> 31);
-    best = max(best, max(key0, key1));
+  for (int c = 0; c < 4; c++) {
+    const uint32_t M = c < 2 ? MP : MN;
+    const uint32_t h = c & 1, b = c >> 1;
+    const uint32_t key = h ? (M >> 16) : (M & 0xFFFFu);
+    const uint32_t s = key >> 6, r6 = 63u - (key & 63u);
+    const uint32_t a = (r6 & 15u) | (h << 4) | ((r6 >> 4) << 5);
+    best = max(best, (s << 8) | ((127u - a) << 1) | (1u - b));
   }
   const uint32_t a = 127u - ((best >> 1) & 127u);
-  return a | ((best & 1u) << 7);
+  return a | ((1u - (best & 1u)) << 7);
+}
+
+// All n1 blocks of one ciphertext by one warp: 16 lane pairs per round.
+// w: the n1*n2-bit word vector (shared or global, 16-byte aligned).
+template <class LV>
+__device__ __forceinline__ void rm_decode_warp(const uint32_t* w, uint8_t* r, int lane) {
+  const uint32_t hb = lane & 1;
+#pragma unroll 1
+  for (int j0 = 0; j0 < LV::n1; j0 += 16) {
+    const int j = j0 + (lane >> 1);
+    const int jj = j < LV::n1 ? j : LV::n1 - 1;
+    const uint32_t byte = rm_decode_pair<LV::mult>(w + jj * (LV::n2 / 32), hb);
+    if (j < LV::n1 && hb == 0) r[j] = (uint8_t)byte;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -467,7 +514,7 @@ __device__ __forceinline__ void decrypt_one(const GF& gf, uint32_t* ws, int lane
   }
   __syncwarp();
   uint8_t* r = reinterpret_cast<uint8_t*>(ws + LV::RS_R);
-  for (int j = lane; j < LV::n1; j += 32) r[j] = (uint8_t)rm_decode_block<LV::mult>(u2 + j * (LV::n2 / 32));
+  rm_decode_warp<LV>(u2, r, lane);
   __syncwarp();
   rs_decode_warp<LV, false>(gf, ws + LV::RS_R, lane, mrow, nullptr);
   __syncwarp();
