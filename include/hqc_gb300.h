@@ -105,6 +105,33 @@ int hqc_decrypt_batch_staged(int level, int64_t count, const uint64_t* u, const 
                              const hqc_keyset_t* keys, const int32_t* key_idx, void* workspace,
                              size_t workspace_bytes, uint8_t* m_out, void* stream);
 
+/* Same per-stage decryption, for callers that cannot allocate device memory
+ * at all (a framework that owns every device byte through its own
+ * allocator, a latency-critical path where cudaMalloc could block or fail
+ * under memory pressure, a service that reserves all of its memory at
+ * load).  The paper has no counterpart to this entry point.
+ *   - No allocation: the intermediates live in one array of
+ *     HQC_NOALLOC_SCRATCH_BYTES compiled into the library, which every GPU
+ *     that loads the library holds until the process exits.
+ *   - Size limit: count may be at most (HQC_NOALLOC_SCRATCH_BYTES - 16) /
+ *     (8 W_v + n1): 7443 (HQC-1), 3698 (HQC-3), 2301 (HQC-5) per call.  A
+ *     larger count returns HQC_EINVAL (message in hqc_last_error) and
+ *     launches nothing.
+ *   - First call on a device: it looks up the array's device address with
+ *     cudaGetSymbolAddress once (per device, that device current), so make
+ *     that first call outside any stream capture.
+ *   - Sharing: every call on a device uses the same array, and each call
+ *     overwrites all of the part it reads before reading it (nothing needs
+ *     to start at zero).  Calls whose work overlaps on the GPU -- two
+ *     streams, or two host threads -- race on the array; order them on one
+ *     stream or synchronize between them.
+ * Arguments and errors are those of hqc_decrypt_batch_staged minus the
+ * workspace. */
+#define HQC_NOALLOC_SCRATCH_BYTES (16u << 20)
+int hqc_decrypt_batch_staged_noalloc(int level, int64_t count, const uint64_t* u, const uint64_t* v,
+                                     const uint32_t* y, const hqc_keyset_t* keys, const int32_t* key_idx,
+                                     uint8_t* m_out, void* stream);
+
 /* Every intermediate of Algorithm 2, per ciphertext (device arrays):
  *   t    [count][W_v]  u*y truncated to n1*n2 bits
  *   w    [count][W_v]  v + t

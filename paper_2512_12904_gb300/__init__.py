@@ -20,7 +20,7 @@ from . import _build
 __all__ = [
     "HqcError", "Params", "Keyset", "load", "hqc_get_params", "hqc_decrypt_batch",
     "hqc_keys_register", "hqc_decrypt_batch_keyed", "hqc_staged_workspace_bytes",
-    "hqc_decrypt_batch_staged", "hqc_decrypt_debug", "hqc_mixed_workspace_bytes",
+    "hqc_decrypt_batch_staged", "hqc_decrypt_batch_staged_noalloc", "hqc_decrypt_debug", "hqc_mixed_workspace_bytes",
     "hqc_decrypt_mixed", "hqc_set_launch_config", "hqc_get_launch_shape", "hqc_keygen_batch",
     "hqc_encrypt_batch", "LEVELS",
 ]
@@ -76,6 +76,7 @@ def load(build_if_missing: bool = True):
             "hqc_decrypt_batch_keyed": (i32, [i32, i64, P, P, P, P, P, P]),
             "hqc_staged_workspace_bytes": (sz, [i32, i64]),
             "hqc_decrypt_batch_staged": (i32, [i32, i64, P, P, P, P, P, P, sz, P, P]),
+            "hqc_decrypt_batch_staged_noalloc": (i32, [i32, i64, P, P, P, P, P, P, P]),
             "hqc_decrypt_debug": (i32, [i32, i64, P, P, P, P, P, P]),
             "hqc_mixed_workspace_bytes": (sz, []),
             "hqc_decrypt_mixed": (i32, [i64, P, P, i64, P, P, i64, P, sz, P]),
@@ -252,6 +253,32 @@ def hqc_decrypt_batch_staged(level, u, v, y=None, keys: Keyset = None, key_idx=N
                                            _dev_ptr(workspace, torch.uint8, None, "workspace"),
                                            workspace.numel(), _dev_ptr(m_out, torch.uint8, (cnt, P.k), "m_out"),
                                            _stream(stream)))
+    return m_out
+
+
+def hqc_decrypt_batch_staged_noalloc(level, u, v, y=None, keys: Keyset = None, key_idx=None, m_out=None,
+                                     stream=None):
+    """Per-stage decryption whose scratch is the library's compiled-in array
+    (no device allocation by the library; m_out may be passed in by a caller
+    that allocates nothing either).  Calls overlapping on the GPU race on
+    that array."""
+    torch = _torch()
+    P = hqc_get_params(level)
+    u, v = _as_u64(u), _as_u64(v)
+    cnt = u.shape[0]
+    if m_out is None:
+        m_out = torch.empty((cnt, P.k), dtype=torch.uint8, device=u.device)
+    yp, kp, ip = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    if keys is not None:
+        kp = keys.handle
+        ip = _dev_ptr(key_idx, torch.int32, (cnt,), "key_idx")
+    else:
+        y = y.view(torch.int32) if y.dtype == torch.uint32 else y
+        yp = _dev_ptr(y, torch.int32, (cnt, P.w), "y")
+    _check(load().hqc_decrypt_batch_staged_noalloc(level, cnt, _dev_ptr(u, torch.int64, (cnt, P.W_u_pitch), "u"),
+                                                   _dev_ptr(v, torch.int64, (cnt, P.W_v), "v"), yp, kp, ip,
+                                                   _dev_ptr(m_out, torch.uint8, (cnt, P.k), "m_out"),
+                                                   _stream(stream)))
     return m_out
 
 

@@ -85,6 +85,8 @@ int launch_result(cudaError_t e, const char* what) { return e == cudaSuccess ? H
 
 }  // namespace
 
+void hqc::set_last_error(const char* msg) { g_err = msg; }
+
 extern "C" {
 
 int hqc_get_params(int level, hqc_params_t* out) {

@@ -59,6 +59,7 @@ struct MixedArgs {
 };
 
 int level_index(int level);  // 1 -> 0, 3 -> 1, 5 -> 2, else -1
+void set_last_error(const char* msg);  // message returned by hqc_last_error() on this thread
 
 cudaError_t launch_fused(int level, bool keyed, const DecArgs& a, cudaStream_t st, const LaunchCfg& cfg);
 cudaError_t launch_staged(int level, bool keyed, const DecArgs& a, uint64_t* w_ws, uint8_t* r_ws, cudaStream_t st);
