@@ -40,7 +40,10 @@ WORKLOADS = {
     "hqc3": (3, 32768, 128, "HQC-3 batch: 32768 ciphertexts under 128 keypairs, one batched keyed launch"),
     "hqc5": (5, 32768, 128, "HQC-5 batch: 32768 ciphertexts under 128 keypairs, one batched keyed launch"),
     "hqc1-plain": (1, 256, 16, "HQC-1 plain path: 256 ciphertexts under 16 keypairs"),
+    "mixed": (0, 100000, 384, "Mixed levels: 100000 ciphertexts, 40% HQC-1 / 35% HQC-3 / 25% HQC-5 shuffled, "
+                              "384 keypairs (128 per level), one CUDA-graph plan with autotuned launch shapes"),
 }
+MIXED_SPLIT = ((1, 40000), (3, 35000), (5, 25000))
 
 
 def parse_args():
@@ -251,6 +254,8 @@ def run_reference(args):
         return 0
     import oracle
     level, count, nkeys, desc = WORKLOADS[args.workload]
+    if level == 0:
+        level, nkeys = 1, nkeys // 3  # the mixed workload's reference arm times its HQC-1 share
     cores = os.cpu_count() or 1
     # calibrate, then size each step so the whole run takes ~2 minutes
     probe = max(2 * cores, 16)
@@ -284,9 +289,190 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # the GPU arm
 # ---------------------------------------------------------------------------
+def run_mixed(args):
+    """Mixed-level batch: autotuned CUDA-graph plan vs the single mixed kernel,
+    per-level fused launches and the plain per-stage form."""
+    import torch
+    import synth
+    import paper_2512_12904_gb300 as hqc
+
+    dist = Dist(args.gpus)
+    device = torch.device("cuda", dist.local)
+    torch.cuda.set_device(device)
+    hqc.load()
+    _, count, nkeys_total, desc = WORKLOADS["mixed"]
+    nk = nkeys_total // 3
+    per = {}
+    for lvl, cnt in MIXED_SPLIT:
+        per[lvl] = make_workload(hqc, lvl, cnt, nk, dist.rank, device)
+    # shuffled item order and arena layout (u row then v row per item)
+    seq_lvl = np.concatenate([np.full(cnt, lvl, np.int32) for lvl, cnt in MIXED_SPLIT])
+    seq_idx = np.concatenate([np.arange(cnt, dtype=np.int64) for _, cnt in MIXED_SPLIT])
+    order = synth.shuffle(np.arange(count, dtype=np.int32), tag=77)
+    seq_lvl, seq_idx = seq_lvl[order], seq_idx[order]
+    P = {lvl: per[lvl][0] for lvl, _ in MIXED_SPLIT}
+    wu = np.array([0, P[1].W_u_pitch, 0, P[3].W_u_pitch, 0, P[5].W_u_pitch])[seq_lvl]
+    wv = np.array([0, P[1].W_v, 0, P[3].W_v, 0, P[5].W_v])[seq_lvl]
+    kk = np.array([0, P[1].k, 0, P[3].k, 0, P[5].k])[seq_lvl]
+    u_off = np.concatenate([[0], np.cumsum(wu + wv)[:-1]])
+    v_off = u_off + wu
+    m_off = np.concatenate([[0], np.cumsum(kk)[:-1]])
+    words = int((wu + wv).sum())
+    m_bytes = int(kk.sum())
+    arena = torch.empty(words, dtype=torch.int64, device=device)
+    m_expect = torch.empty(m_bytes, dtype=torch.uint8, device=device)
+    items = np.zeros(count, dtype=hqc.ITEM_DTYPE)
+    items["level"] = seq_lvl
+    items["u_off"] = u_off
+    items["v_off"] = v_off
+    items["m_off"] = m_off
+    for lvl, cnt in MIXED_SPLIT:
+        Pl, keys, u_d, v_d, k_d, m_ref, y_host, kidx = per[lvl]
+        sel = np.nonzero(seq_lvl == lvl)[0]
+        src = torch.from_numpy(seq_idx[sel]).to(device)
+        items["key"][sel] = kidx[seq_idx[sel]]
+        ui = torch.from_numpy(u_off[sel]).to(device)[:, None] + torch.arange(Pl.W_u_pitch, device=device)
+        vi = torch.from_numpy(v_off[sel]).to(device)[:, None] + torch.arange(Pl.W_v, device=device)
+        mi = torch.from_numpy(m_off[sel]).to(device)[:, None] + torch.arange(Pl.k, device=device)
+        arena[ui.reshape(-1)] = u_d[src].reshape(-1)
+        arena[vi.reshape(-1)] = v_d[src].reshape(-1)
+        m_expect[mi.reshape(-1)] = m_ref[src].reshape(-1)
+    items_d = torch.from_numpy(items.view(np.uint8)).to(device)
+    keys3 = [per[l][1] for l in (1, 3, 5)]
+    m_out = torch.zeros(m_bytes, dtype=torch.uint8, device=device)
+    stream = torch.cuda.Stream(device=device)
+    torch.cuda.synchronize()
+
+    t0 = time.perf_counter()
+    plan = hqc.hqc_plan_create_mixed(items_d, arena, keys3, m_out, autotune=True, stream=stream)
+    torch.cuda.synchronize()
+    tune_s = time.perf_counter() - t0
+    info = plan.info()
+
+    def step():
+        plan.launch(stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+    total_ms, per_ms, clocks = timed_steps(step, args.steps, stream, dist, clocks_idx=dist.local)
+    max_ms = dist.max(total_ms)
+    correct = bool((m_out == m_expect).all().item())
+
+    def arm(fn, steps):
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                fn()
+        ms, _, _ = timed_steps(fn, steps, stream, dist)
+        return dist.max(ms) / steps
+
+    ws_mixed = torch.zeros(hqc.hqc_mixed_workspace_bytes(), dtype=torch.uint8, device=device)
+    m_single = torch.zeros_like(m_out)
+    single_ms = arm(lambda: hqc.hqc_decrypt_mixed(items_d, arena, keys3, m_single, workspace=ws_mixed, stream=stream),
+                    max(5, min(args.steps, 200)))
+    single_ok = bool((m_single == m_expect).all().item())
+    outs = {lvl: torch.empty_like(per[lvl][5]) for lvl, _ in MIXED_SPLIT}
+
+    def fused_levels():
+        for lvl, _ in MIXED_SPLIT:
+            Pl, keys, u_d, v_d, k_d, m_ref, _, _ = per[lvl]
+            hqc.hqc_decrypt_batch_keyed(lvl, u_d, v_d, keys, k_d, outs[lvl], stream=stream)
+
+    levels_ms = arm(fused_levels, max(5, min(args.steps, 200)))
+    wss = {lvl: torch.empty(hqc.hqc_staged_workspace_bytes(lvl, cnt), dtype=torch.uint8, device=device)
+           for lvl, cnt in MIXED_SPLIT}
+    outs2 = {lvl: torch.empty_like(per[lvl][5]) for lvl, _ in MIXED_SPLIT}
+
+    def staged_levels():
+        for lvl, _ in MIXED_SPLIT:
+            Pl, keys, u_d, v_d, k_d, m_ref, _, _ = per[lvl]
+            hqc.hqc_decrypt_batch_staged(lvl, u_d, v_d, keys=keys, key_idx=k_d, workspace=wss[lvl], m_out=outs2[lvl],
+                                         stream=stream)
+
+    staged_ms = arm(staged_levels, max(5, min(args.steps, 100)))
+    staged_ok = all(bool((outs2[l] == per[l][5]).all().item()) for l, _ in MIXED_SPLIT)
+
+    # end to end: the arena and item list from pinned host memory, m back
+    arena_h = arena.cpu().pin_memory()
+    items_h = items_d.cpu().pin_memory()
+    m_h = torch.empty(m_bytes, dtype=torch.uint8).pin_memory()
+    arena_e, items_e, m_e = torch.empty_like(arena), torch.empty_like(items_d), torch.zeros_like(m_out)
+    ws_e = torch.zeros(hqc.hqc_mixed_workspace_bytes(), dtype=torch.uint8, device=device)
+
+    def e2e_step():
+        arena_e.copy_(arena_h, non_blocking=True)
+        items_e.copy_(items_h, non_blocking=True)
+        hqc.hqc_decrypt_mixed(items_e, arena_e, keys3, m_e, workspace=ws_e, stream=stream)
+        m_h.copy_(m_e, non_blocking=True)
+
+    e2e_steps = max(5, min(args.steps, 50))
+    e2e_ms = arm(e2e_step, e2e_steps)
+    e2e_ok = bool((m_h == m_expect.cpu()).all().item())
+
+    total = dist.sum(float(count))
+    value = total * args.steps / (max_ms * 1e-3)
+    smem_b = sum(cnt * per_decryption_work(P[l])[0] for l, cnt in MIXED_SPLIT)
+    int_ops = sum(cnt * per_decryption_work(P[l])[2] for l, cnt in MIXED_SPLIT)
+    hbm_b = sum(cnt * per_decryption_work(P[l])[1] for l, cnt in MIXED_SPLIT)
+    smem_peak, int_peak = load_peaks()
+    step_s = (total_ms / args.steps) * 1e-3
+    peaks = measured_peaks_file()
+    blocks = {
+        "smem": {"bound": "smem", "achieved": smem_b / step_s / 1e9, "peak": smem_peak / 1e9, "unit": "GB/s"},
+        "alu": {"bound": "alu", "achieved": int_ops / step_s / 1e9, "peak": int_peak / 1e9, "unit": "Gop/s"},
+        "hbm": {"bound": "hbm", "achieved": hbm_b / step_s / 1e9, "peak": peaks.get("hbm_gbs"), "unit": "GB/s"},
+    }
+    for b in blocks.values():
+        b["frac"] = b["achieved"] / b["peak"] if b["peak"] else None
+    primary = max(("smem", "alu"), key=lambda k: blocks[k]["frac"] or 0)
+    roofline = dict(blocks[primary], traffic=None, kernel="mixed plan (%s)" % info["form"],
+                    others={k: v for k, v in blocks.items() if k != primary})
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": desc, "count_per_gpu": count, "split": dict((str(l), c) for l, c in MIXED_SPLIT),
+                   "nkeys": nkeys_total, "plan": info, "autotune_s": tune_s,
+                   "l2": "inputs (%d MB) larger than L2 (129 MB); no flush" % (words * 8 // 2 ** 20)},
+        "correct": correct and single_ok and staged_ok and e2e_ok,
+        "latency_ms": {"p50": pct(per_ms, 50), "p99": pct(per_ms, 99), "max": max(per_ms),
+                       "what": "one mixed batch of %d decryptions (graph launch to completion)" % count},
+        "single_mixed_kernel": {"value": total / (single_ms * 1e-3), "ms_per_step": single_ms, "correct": single_ok},
+        "per_level_fused": {"value": total / (levels_ms * 1e-3), "ms_per_step": levels_ms, "launches_per_step": 3},
+        "plain_per_stage": {"value": total / (staged_ms * 1e-3), "unit": UNIT, "ms_per_step": staged_ms,
+                            "launches_per_step": 9, "correct": staged_ok},
+        "roofline": roofline,
+        "e2e": {"value": total / (e2e_ms * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": int(arena_h.numel() * 8 + items_h.numel()), "d2h_bytes_per_step": m_bytes,
+                "api": "hqc_decrypt_mixed with the pinned host arena and item list copied in, m copied out"},
+        "gpu_launches": args.steps * (1 if info["form"] == "mixed-single-kernel" else 3),
+        "clocks": clocks,
+    }
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        rates = {}
+        for lvl, cnt in MIXED_SPLIT:
+            rates[lvl] = oracle_rate(lvl, 16, args.cpu_seconds / 3, cores)
+        t_total = sum(cnt / rates[l][0] for l, cnt in MIXED_SPLIT)
+        line["cpu_baseline"] = {"value": count / t_total, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": "per level %s ciphertexts timed separately, combined in the 40/35/25 mix"
+                                          % {l: rates[l][1] for l, _ in MIXED_SPLIT}}
+    plan.destroy()
+    for l in (1, 3, 5):
+        per[l][1].free()
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+    dist.close()
+    return 0
+
+
 def run_ours(args):
     import torch
     import paper_2512_12904_gb300 as hqc
+
+    if args.workload == "mixed":
+        return run_mixed(args)
 
     dist = Dist(args.gpus)
     device = torch.device("cuda", dist.local)

@@ -194,6 +194,35 @@ int hqc_set_launch_config(int level, const hqc_launch_cfg_t* cfg);
  * grid size of the persistent launch (keyed selects the kernel variant). */
 int hqc_get_launch_shape(int level, int keyed, int32_t* warps, int32_t* ctas_per_sm, int32_t* grid);
 
+/* Plans: one fixed batch (these exact pointers and count) captured in a
+ * CUDA graph and replayed with hqc_plan_launch (one graph launch per
+ * batch).  Creating a plan allocates small plan-owned device buffers and,
+ * with autotune != 0, first times candidate launch shapes on `stream` with
+ * the caller's data (which writes m_out); launching allocates nothing.  The
+ * data behind the pointers may change between launches, the pointers and
+ * count may not.
+ *   keyed: the fused kernel of hqc_decrypt_batch_keyed; the tuner picks
+ *          warps per block and blocks per SM.
+ *   mixed: the items of hqc_decrypt_mixed.  The tuner compares the single
+ *          mixed persistent kernel (form 1) with two level-split forms: the
+ *          list is split by level once at creation, then one persistent
+ *          kernel per level runs either side by side as parallel graph
+ *          branches on a tuned share of the SMs each (form 2) or one after
+ *          another on the whole GPU (form 3). */
+typedef struct hqc_plan_s hqc_plan_t;
+int hqc_plan_create_keyed(int level, int64_t count, const uint64_t* u, const uint64_t* v, const hqc_keyset_t* keys,
+                          const int32_t* key_idx, uint8_t* m_out, int autotune, void* stream, hqc_plan_t** out);
+int hqc_plan_create_mixed(int64_t count, const hqc_item_t* items, const uint64_t* arena, int64_t arena_words,
+                          const hqc_keyset_t* const keys[3], uint8_t* m_arena, int64_t m_bytes, int autotune,
+                          void* stream, hqc_plan_t** out);
+int hqc_plan_launch(hqc_plan_t* plan, void* stream);
+/* form: 0 keyed, 1 mixed single kernel, 2 mixed level-partitioned, 3 mixed
+ * per-level sequential; cfg: the
+ * chosen shape (forms 0, 1); grids3: blocks per level 1/3/5 (form 2);
+ * tuned_ms: the best time the tuner measured (0 without autotune). */
+int hqc_plan_info(const hqc_plan_t* plan, int32_t* form, hqc_launch_cfg_t* cfg, int32_t* grids3, float* tuned_ms);
+int hqc_plan_destroy(hqc_plan_t* plan);
+
 /* Key generation core of Algorithm 3: s = x + h*y per key.
  * h, s_out [nkeys][W_u_pitch]; x, y [nkeys][w] (device). */
 int hqc_keygen_batch(int level, int64_t nkeys, const uint64_t* h, const uint32_t* x, const uint32_t* y,

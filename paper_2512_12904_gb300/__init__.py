@@ -22,7 +22,7 @@ __all__ = [
     "hqc_keys_register", "hqc_decrypt_batch_keyed", "hqc_staged_workspace_bytes",
     "hqc_decrypt_batch_staged", "hqc_decrypt_batch_staged_noalloc", "hqc_decrypt_debug", "hqc_mixed_workspace_bytes",
     "hqc_decrypt_mixed", "hqc_set_launch_config", "hqc_get_launch_shape", "hqc_keygen_batch",
-    "hqc_encrypt_batch", "LEVELS",
+    "hqc_encrypt_batch", "LEVELS", "Plan", "hqc_plan_create_keyed", "hqc_plan_create_mixed",
 ]
 
 LEVELS = (1, 3, 5)
@@ -82,6 +82,11 @@ def load(build_if_missing: bool = True):
             "hqc_decrypt_mixed": (i32, [i64, P, P, i64, P, P, i64, P, sz, P]),
             "hqc_set_launch_config": (i32, [i32, P]),
             "hqc_get_launch_shape": (i32, [i32, i32, P, P, P]),
+            "hqc_plan_create_keyed": (i32, [i32, i64, P, P, P, P, P, i32, P, P]),
+            "hqc_plan_create_mixed": (i32, [i64, P, P, i64, P, P, i64, i32, P, P]),
+            "hqc_plan_launch": (i32, [P, P]),
+            "hqc_plan_info": (i32, [P, P, P, P, P]),
+            "hqc_plan_destroy": (i32, [P]),
             "hqc_keygen_batch": (i32, [i32, i64, P, P, P, P, P]),
             "hqc_encrypt_batch": (i32, [i32, i64, P, P, i64, P, P, P, P, P, P, P, P]),
         }
@@ -384,3 +389,66 @@ def hqc_encrypt_batch(level, h, s, key_idx, m, r1, r2, e, u_out=None, v_out=None
                                     _dev_ptr(u_out, torch.int64, (cnt, P.W_u_pitch), "u_out"),
                                     _dev_ptr(v_out, torch.int64, (cnt, P.W_v), "v_out"), _stream(stream)))
     return u_out, v_out
+
+
+class Plan:
+    """A batch captured in a CUDA graph (hqc_plan_create_*); keeps the
+    tensors it points at alive."""
+
+    def __init__(self, handle, keep):
+        self._h = handle
+        self._keep = keep
+
+    def launch(self, stream=None):
+        _check(load().hqc_plan_launch(self._h, _stream(stream)))
+
+    def info(self):
+        form = ctypes.c_int32()
+        cfg = _LaunchCfg()
+        grids = (ctypes.c_int32 * 3)()
+        ms = ctypes.c_float()
+        _check(load().hqc_plan_info(self._h, ctypes.byref(form), ctypes.byref(cfg), grids, ctypes.byref(ms)))
+        return dict(form={0: "keyed", 1: "mixed-single-kernel", 2: "mixed-level-partitioned",
+                          3: "mixed-per-level-sequential"}[form.value],
+                    warps_per_cta=cfg.warps_per_cta, ctas_per_sm=cfg.ctas_per_sm, grids=list(grids),
+                    tuned_ms=ms.value)
+
+    def destroy(self):
+        if self._h:
+            _check(load().hqc_plan_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def hqc_plan_create_keyed(level, u, v, keys: Keyset, key_idx, m_out, autotune=True, stream=None) -> Plan:
+    torch = _torch()
+    P = hqc_get_params(level)
+    u, v = _as_u64(u), _as_u64(v)
+    cnt = u.shape[0]
+    h = ctypes.c_void_p()
+    _check(load().hqc_plan_create_keyed(level, cnt, _dev_ptr(u, torch.int64, (cnt, P.W_u_pitch), "u"),
+                                        _dev_ptr(v, torch.int64, (cnt, P.W_v), "v"), keys.handle,
+                                        _dev_ptr(key_idx, torch.int32, (cnt,), "key_idx"),
+                                        _dev_ptr(m_out, torch.uint8, (cnt, P.k), "m_out"), int(bool(autotune)),
+                                        _stream(stream), ctypes.byref(h)))
+    return Plan(h, (u, v, keys, key_idx, m_out))
+
+
+def hqc_plan_create_mixed(items, arena, keys, m_arena, autotune=True, stream=None) -> Plan:
+    torch = _torch()
+    if items.dtype != torch.uint8 or items.numel() % ITEM_DTYPE.itemsize:
+        raise TypeError("items must be a uint8 tensor of packed ITEM_DTYPE records")
+    cnt = items.numel() // ITEM_DTYPE.itemsize
+    arena = _as_u64(arena)
+    karr = (ctypes.c_void_p * 3)(*[(k.handle if k is not None else None) for k in keys])
+    h = ctypes.c_void_p()
+    _check(load().hqc_plan_create_mixed(cnt, _dev_ptr(items, torch.uint8, None, "items"),
+                                        _dev_ptr(arena, torch.int64, None, "arena"), arena.numel(), karr,
+                                        _dev_ptr(m_arena, torch.uint8, None, "m_arena"), m_arena.numel(),
+                                        int(bool(autotune)), _stream(stream), ctypes.byref(h)))
+    return Plan(h, (items, arena, keys, m_arena))

@@ -13,13 +13,6 @@
 #include "hqc_internal.h"
 #include "hqc_params.cuh"
 
-struct hqc_keyset_s {
-  int level;
-  int64_t nkeys;
-  int device;
-  uint32_t* d_table;  // [nkeys][w]
-};
-
 namespace {
 
 thread_local std::string g_err;

@@ -24,27 +24,47 @@ template <> struct FusedBound<3> { static constexpr int threads = 640; };
 template <> struct FusedBound<5> { static constexpr int threads = 416; };
 constexpr int MIXED_MAX_THREADS = 416;
 
+// Ciphertexts a warp takes per turn: their Reed-Solomon stages run side by
+// side on 32 / G lanes each.  Measured on GB300 (G = 1, 2, 4): two per turn
+// pays for HQC-1 (+6 %), one is best for HQC-3 and HQC-5.
+template <int LEVEL> struct FusedGroup { static constexpr int G = 1; };
+template <> struct FusedGroup<1> { static constexpr int G = 2; };
+
+template <int LEVEL>
+__host__ __device__ constexpr int fused_words() { return fused_warp_words<Level<LEVEL>, FusedGroup<LEVEL>::G>(); }
+
 // ---------------------------------------------------------------------------
-// Fused persistent kernel, one level.
+// Fused persistent kernel, one level.  Warp w takes groups of G consecutive
+// ciphertexts w, w + (all warps), ...
 // ---------------------------------------------------------------------------
 template <int LEVEL, bool KEYED>
 __global__ void __launch_bounds__(FusedBound<LEVEL>::threads, 1) k_decrypt_fused(DecArgs a) {
   using LV = Level<LEVEL>;
+  constexpr int G = FusedGroup<LEVEL>::G;
   extern __shared__ __align__(16) uint8_t smem[];
   gf_tables_init(smem, threadIdx.x, blockDim.x);
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const GF gf(smem, lane);
-  uint32_t* ws = reinterpret_cast<uint32_t*>(smem + GF_TABLE_BYTES) + warp * LV::WARP_WORDS;
-  for (int64_t it = (int64_t)blockIdx.x * nw + warp; it < a.count; it += (int64_t)gridDim.x * nw) {
-    const uint32_t* yrow;
-    if (KEYED) {
-      const uint32_t ki = (uint32_t)__ldg(a.key_idx + it);
-      yrow = a.y + (ki < (uint64_t)a.nkeys ? (int64_t)ki : 0) * LV::w;  // out-of-range index -> key 0
-    } else {
-      yrow = a.y + it * LV::w;
-    }
-    decrypt_one<LV, !KEYED>(gf, ws, lane, a.u + it * LV::W_u_pitch, a.v + it * LV::W_v, yrow, a.m + it * LV::k);
+  uint32_t* ws = reinterpret_cast<uint32_t*>(smem + GF_TABLE_BYTES) + warp * fused_words<LEVEL>();
+  const int64_t ngroups = (a.count + G - 1) / G;
+  for (int64_t q = (int64_t)blockIdx.x * nw + warp; q < ngroups; q += (int64_t)gridDim.x * nw) {
+    auto rows = [&](int g, const uint64_t*& u, const uint64_t*& v, const uint32_t*& y, uint8_t*& m) {
+      const int64_t it0 = q * G + g;
+      const bool ok = it0 < a.count;
+      const int64_t it = ok ? it0 : q * G;
+      if (KEYED) {
+        const uint32_t ki = (uint32_t)__ldg(a.key_idx + it);
+        y = a.y + (ki < (uint64_t)a.nkeys ? (int64_t)ki : 0) * LV::w;  // out-of-range index -> key 0
+      } else {
+        y = a.y + it * LV::w;
+      }
+      u = a.u + it * LV::W_u_pitch;
+      v = a.v + it * LV::W_v;
+      m = a.m + it * LV::k;
+      return ok;
+    };
+    decrypt_group<LV, G, !KEYED>(gf, ws, lane, rows);
   }
 }
 
@@ -54,7 +74,8 @@ __global__ void __launch_bounds__(FusedBound<LEVEL>::threads, 1) k_decrypt_fused
 // given); shared memory per warp is sized for HQC-5.  Items whose level,
 // key or offsets fall outside the given arrays are skipped.
 // ---------------------------------------------------------------------------
-constexpr int MIXED_WARP_WORDS = cmax(Level<1>::WARP_WORDS, cmax(Level<3>::WARP_WORDS, Level<5>::WARP_WORDS));
+constexpr int MIXED_WARP_WORDS =
+    cmax(fused_warp_words<Level<1>, 1>(), cmax(fused_warp_words<Level<3>, 1>(), fused_warp_words<Level<5>, 1>()));
 
 template <class LV>
 __device__ __forceinline__ void mixed_item(const GF& gf, uint32_t* ws, int lane, const MixedArgs& a,
@@ -94,6 +115,42 @@ __global__ void __launch_bounds__(MIXED_MAX_THREADS, 1) k_decrypt_mixed(MixedArg
     } else {
       it += stride;
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent kernel over the items of ONE level taken from a mixed list
+// (the item list was partitioned by level beforehand).  Static stride:
+// every item of a level costs the same.  Used by the level-partitioned
+// plan, which runs one of these per level side by side in a CUDA graph.
+// ---------------------------------------------------------------------------
+template <int LEVEL>
+__global__ void __launch_bounds__(FusedBound<LEVEL>::threads, 1) k_decrypt_items(MixedArgs a) {
+  using LV = Level<LEVEL>;
+  constexpr int G = FusedGroup<LEVEL>::G;
+  constexpr int li = LEVEL == 1 ? 0 : LEVEL == 3 ? 1 : 2;
+  extern __shared__ __align__(16) uint8_t smem[];
+  gf_tables_init(smem, threadIdx.x, blockDim.x);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const GF gf(smem, lane);
+  uint32_t* ws = reinterpret_cast<uint32_t*>(smem + GF_TABLE_BYTES) + warp * fused_words<LEVEL>();
+  const int64_t ngroups = (a.count + G - 1) / G;
+  for (int64_t q = (int64_t)blockIdx.x * nw + warp; q < ngroups; q += (int64_t)gridDim.x * nw) {
+    auto rows = [&](int g, const uint64_t*& u, const uint64_t*& v, const uint32_t*& y, uint8_t*& m) {
+      const int64_t it = q * G + g;
+      if (it >= a.count) return false;
+      const MixedItem item = a.items[it];
+      const bool ok = item.level == LEVEL && (uint32_t)item.key < (uint64_t)a.nkeys[li] && item.u_off >= 0 &&
+                      (item.u_off & 1) == 0 && item.u_off + LV::W_u_pitch <= a.arena_words && item.v_off >= 0 &&
+                      item.v_off + LV::W_v <= a.arena_words && item.m_off >= 0 && item.m_off + LV::k <= a.m_bytes;
+      u = a.arena + (ok ? item.u_off : 0);
+      v = a.arena + (ok ? item.v_off : 0);
+      y = a.keys[li] + (ok ? (int64_t)item.key * LV::w : 0);
+      m = a.m + (ok ? item.m_off : 0);
+      return ok;
+    };
+    decrypt_group<LV, G, false>(gf, ws, lane, rows);
   }
 }
 
@@ -151,13 +208,13 @@ __global__ void __launch_bounds__(STAGE_THREADS) k_stage_rm(int64_t count, const
 }
 
 // K3: one warp per ciphertext: Reed-Solomon decode (and the debug dump).
-constexpr int RS_SCRATCH_WORDS = 192;
+constexpr int RS_SCRATCH_WORDS = 24 + RS_SCRATCH;  // the n1 received bytes, then the RS scratch
 
 template <int LEVEL, bool DEBUG>
 __global__ void __launch_bounds__(STAGE_THREADS) k_stage_rs(int64_t count, const uint8_t* __restrict__ r_in,
                                                            uint8_t* __restrict__ m_out, DebugArgs d) {
   using LV = Level<LEVEL>;
-  static_assert(LV::RS_END - LV::RS_R <= RS_SCRATCH_WORDS, "RS scratch");
+  static_assert(LV::n1 <= 96, "received bytes fit in 24 words");
   extern __shared__ __align__(16) uint8_t smem[];
   gf_tables_init(smem, threadIdx.x, blockDim.x);
   __syncthreads();
@@ -165,16 +222,16 @@ __global__ void __launch_bounds__(STAGE_THREADS) k_stage_rs(int64_t count, const
   const int64_t it = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
   if (it >= count) return;
   const GF gf(smem, lane);
-  uint32_t* rs = reinterpret_cast<uint32_t*>(smem + GF_TABLE_BYTES) + warp * RS_SCRATCH_WORDS;
-  uint8_t* rb = reinterpret_cast<uint8_t*>(rs);
+  uint32_t* base = reinterpret_cast<uint32_t*>(smem + GF_TABLE_BYTES) + warp * RS_SCRATCH_WORDS;
+  uint8_t* rb = reinterpret_cast<uint8_t*>(base);
   for (int j = lane; j < LV::n1; j += 32) rb[j] = r_in[it * LV::n1 + j];
   __syncwarp();
   if (DEBUG) {
     RSDebugRow row{d.S + it * LV::NR, d.lam + it * LV::CAP, d.L + it,  d.errmask + it * LV::n1,
                    d.errval + it * LV::n1, d.cw + it * LV::n1, d.flag + it};
-    rs_decode_warp<LV, true>(gf, rs, lane, m_out + it * LV::k, &row);
+    rs_decode_seg<LV, 32, true>(gf, base + 24, rb, lane, true, m_out + it * LV::k, &row);
   } else {
-    rs_decode_warp<LV, false>(gf, rs, lane, m_out + it * LV::k, nullptr);
+    rs_decode_seg<LV, 32, false>(gf, base + 24, rb, lane, true, m_out + it * LV::k, nullptr);
   }
 }
 
@@ -182,8 +239,8 @@ __global__ void __launch_bounds__(STAGE_THREADS) k_stage_rs(int64_t count, const
 // Launch helpers
 // ---------------------------------------------------------------------------
 template <int LEVEL>
-static size_t fused_smem(int warps) {
-  return (size_t)GF_TABLE_BYTES + (size_t)warps * Level<LEVEL>::WARP_WORDS * 4;
+[[maybe_unused]] static size_t fused_smem(int warps) {
+  return (size_t)GF_TABLE_BYTES + (size_t)warps * fused_words<LEVEL>() * 4;
 }
 
 static int device_props(int* sms, int* smem_optin) {
@@ -229,13 +286,13 @@ static cudaError_t fused_level(const DecArgs& a, cudaStream_t st, const LaunchCf
   int nw = 0, c = 0, g = 0;
   size_t sm = 0;
   cudaError_t e = shape_for(k_decrypt_fused<LEVEL, KEYED>, FusedBound<LEVEL>::threads,
-                            (size_t)Level<LEVEL>::WARP_WORDS * 4, cfg, &nw, &c, &g, &sm);
+                            (size_t)fused_words<LEVEL>() * 4, cfg, &nw, &c, &g, &sm);
   if (e != cudaSuccess) return e;
   if (warps) *warps = nw;
   if (ctas) *ctas = c;
   if (grid) *grid = g;
   if (!launch || a.count == 0) return cudaSuccess;
-  const int64_t need = (a.count + nw - 1) / nw;
+  const int64_t need = (a.count + (int64_t)nw * FusedGroup<LEVEL>::G - 1) / ((int64_t)nw * FusedGroup<LEVEL>::G);
   if (need < g) g = (int)need;
   k_decrypt_fused<LEVEL, KEYED><<<g, nw * 32, sm, st>>>(a);
   return cudaGetLastError();
@@ -270,6 +327,54 @@ cudaError_t launch_mixed(const MixedArgs& a, cudaStream_t st, const LaunchCfg& c
   if (need < g) g = (int)need;
   k_decrypt_mixed<<<g, nw * 32, sm, st>>>(a);
   return cudaGetLastError();
+}
+
+template <int LEVEL>
+static cudaError_t items_level(const MixedArgs& a, int grid, cudaStream_t st, const LaunchCfg& cfg, bool launch,
+                               int* warps, int* ctas, int* full_grid) {
+  int nw = 0, c = 0, g = 0;
+  size_t sm = 0;
+  cudaError_t e = shape_for(k_decrypt_items<LEVEL>, FusedBound<LEVEL>::threads, (size_t)fused_words<LEVEL>() * 4,
+                            cfg, &nw, &c, &g, &sm);
+  if (e != cudaSuccess) return e;
+  if (warps) *warps = nw;
+  if (ctas) *ctas = c;
+  if (full_grid) *full_grid = g;
+  if (!launch || a.count == 0) return cudaSuccess;
+  if (grid <= 0 || grid > g) grid = g;
+  const int64_t need = (a.count + (int64_t)nw * FusedGroup<LEVEL>::G - 1) / ((int64_t)nw * FusedGroup<LEVEL>::G);
+  if (need < grid) grid = (int)need;
+  k_decrypt_items<LEVEL><<<grid, nw * 32, sm, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_items(int level, const MixedArgs& a, int grid, cudaStream_t st, const LaunchCfg& cfg) {
+  switch (level) {
+    case 1: return items_level<1>(a, grid, st, cfg, true, 0, 0, 0);
+    case 3: return items_level<3>(a, grid, st, cfg, true, 0, 0, 0);
+    case 5: return items_level<5>(a, grid, st, cfg, true, 0, 0, 0);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t items_occupancy(int level, const LaunchCfg& cfg, int* warps, int* ctas, int* grid) {
+  MixedArgs none;
+  switch (level) {
+    case 1: return items_level<1>(none, 0, 0, cfg, false, warps, ctas, grid);
+    case 3: return items_level<3>(none, 0, 0, cfg, false, warps, ctas, grid);
+    case 5: return items_level<5>(none, 0, 0, cfg, false, warps, ctas, grid);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t mixed_occupancy(const LaunchCfg& cfg, int* warps, int* ctas, int* grid) {
+  int nw = 0, c = 0, g = 0;
+  size_t sm = 0;
+  cudaError_t e = shape_for(k_decrypt_mixed, MIXED_MAX_THREADS, (size_t)MIXED_WARP_WORDS * 4, cfg, &nw, &c, &g, &sm);
+  if (warps) *warps = nw;
+  if (ctas) *ctas = c;
+  if (grid) *grid = g;
+  return e;
 }
 
 template <int LEVEL, bool KEYED, bool DEBUG>

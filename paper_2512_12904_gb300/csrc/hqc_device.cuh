@@ -322,18 +322,19 @@ __device__ __forceinline__ void rm_decode_warp(const uint32_t* w, uint8_t* r, in
 }
 
 // ---------------------------------------------------------------------------
-// S8-S9: Reed-Solomon decoding of one received word by one warp.
+// S8-S9: Reed-Solomon decoding, SEG lanes per received word (a warp decodes
+// 32 / SEG words side by side; all shuffles stay inside a segment).
 //   syndromes S_i = sum_j r_j alpha^{i j}, i = 1..2 delta    (Sec. III-D)
 //   Berlekamp-Massey, exactly 2 delta iterations, Lambda and x^m B kept
-//   with 2 delta + 1 coefficients spread over the lanes
+//   with 2 delta + 1 coefficients spread over the segment's lanes
 //   Chien: position j in error iff Lambda(alpha^{-j}) = 0
 //   Forney: e_j = Omega(alpha^{-j}) / Lambda'(alpha^{-j}), Omega = S Lambda
 //   mod x^{2 delta}
-// The received bytes r[0, n1) are the first bytes of the scratch rs (at
-// least RS_END - RS_R words of shared memory).  With
-// ALL_POS false only the k message positions are evaluated (m is all the
-// decryption returns); with ALL_POS true every position is evaluated and
-// the intermediates are written to dbg.
+// r: the n1 received bytes of this segment's word; rs: RS_SCRATCH words of
+// shared scratch for it.  With ALL_POS false only the k message positions
+// are evaluated (m is all the decryption returns); with ALL_POS true every
+// position is evaluated and the intermediates are written to dbg.  A
+// segment with active == false computes but stores nothing.
 // ---------------------------------------------------------------------------
 struct RSDebugRow {
   uint8_t* S;        // 2 delta
@@ -345,24 +346,27 @@ struct RSDebugRow {
   int32_t* flag;     // 1
 };
 
-template <class LV, bool ALL_POS>
-__device__ __forceinline__ void rs_decode_warp(const GF& gf, uint32_t* rs, int lane, uint8_t* __restrict__ m_out,
-                                               const RSDebugRow* dbg) {
-  constexpr int n1 = LV::n1, k = LV::k, NR = LV::NR, CAP = LV::CAP, delta = LV::delta;
-  const uint8_t* r = reinterpret_cast<const uint8_t*>(rs);
-  uint16_t* logr = reinterpret_cast<uint16_t*>(rs + (LV::RS_LOGR - LV::RS_R));
-  uint16_t* logS = reinterpret_cast<uint16_t*>(rs + (LV::RS_LOGS - LV::RS_R));
-  uint16_t* logLam = reinterpret_cast<uint16_t*>(rs + (LV::RS_LOGLAM - LV::RS_R));
-  uint16_t* logOm = reinterpret_cast<uint16_t*>(rs + (LV::RS_LOGOM - LV::RS_R));
+constexpr int RS_SCRATCH = 144;  // words: log r (96 halfwords), log S, log Lambda, log Omega (64 halfwords each)
 
-  for (int j = lane; j < n1; j += 32) logr[j] = (uint16_t)gf.log(r[j]);
+template <class LV, int SEG, bool ALL_POS>
+__device__ __forceinline__ void rs_decode_seg(const GF& gf, uint32_t* rs, const uint8_t* r, int lane, bool active,
+                                              uint8_t* __restrict__ m_out, const RSDebugRow* dbg) {
+  constexpr int n1 = LV::n1, k = LV::k, NR = LV::NR, CAP = LV::CAP, delta = LV::delta;
+  static_assert(n1 <= 96 && CAP <= 64, "RS scratch sizes");
+  const int sl = lane % SEG;
+  uint16_t* logr = reinterpret_cast<uint16_t*>(rs);
+  uint16_t* logS = reinterpret_cast<uint16_t*>(rs + 48);
+  uint16_t* logLam = reinterpret_cast<uint16_t*>(rs + 80);
+  uint16_t* logOm = reinterpret_cast<uint16_t*>(rs + 112);
+
+  for (int j = sl; j < n1; j += SEG) logr[j] = (uint16_t)gf.log(r[j]);
   __syncwarp();
 
-  // syndromes: lane owns i = lane + 1 + 32 s
-  constexpr int NS = cdiv(NR, 32);
+  // syndromes: lane owns i = sl + 1 + SEG s
+  constexpr int NS = cdiv(NR, SEG);
 #pragma unroll
   for (int s = 0; s < NS; s++) {
-    const uint32_t i = (uint32_t)(lane + 1 + 32 * s);
+    const uint32_t i = (uint32_t)(sl + 1 + SEG * s);
     uint32_t acc = 0, e = 0;
 #pragma unroll 2
     for (int j = 0; j < n1; j++) {
@@ -372,17 +376,17 @@ __device__ __forceinline__ void rs_decode_warp(const GF& gf, uint32_t* rs, int l
     }
     if (i <= (uint32_t)NR) {
       logS[i - 1] = (uint16_t)gf.log(acc);
-      if (ALL_POS) dbg->S[i - 1] = (uint8_t)acc;
+      if (ALL_POS && active) dbg->S[i - 1] = (uint8_t)acc;
     }
   }
   __syncwarp();
 
-  // Berlekamp-Massey; lane owns coefficient c = lane + 32 x
-  constexpr int NC = cdiv(CAP, 32);
+  // Berlekamp-Massey; lane owns coefficient c = sl + SEG x
+  constexpr int NC = cdiv(CAP, SEG);
   uint32_t lam[NC], bp[NC];
 #pragma unroll
   for (int x = 0; x < NC; x++) {
-    const int c = lane + 32 * x;
+    const int c = sl + SEG * x;
     lam[x] = c == 0;
     bp[x] = c == 1;  // x^m B with m = 1, B = 1
   }
@@ -392,13 +396,13 @@ __device__ __forceinline__ void rs_decode_warp(const GF& gf, uint32_t* rs, int l
     uint32_t part = 0;
 #pragma unroll
     for (int x = 0; x < NC; x++) {
-      const int c = lane + 32 * x;
+      const int c = sl + SEG * x;
       const bool in = c <= rr;
       const uint32_t ls = logS[in ? rr - c : 0];
       part ^= sel(in, gf.mul_l(gf.log(lam[x]), ls), 0u);
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) part ^= __shfl_xor_sync(FULL_MASK, part, o);
+    for (int o = SEG / 2; o > 0; o >>= 1) part ^= __shfl_xor_sync(FULL_MASK, part, o, SEG);
     const uint32_t d = part;
     const uint32_t ld = gf.log(d);
     const uint32_t lcoef = sel(d == 0, GF_LOG_ZERO, sel(ld >= lb, ld - lb, ld + 255u - lb));
@@ -412,34 +416,34 @@ __device__ __forceinline__ void rs_decode_warp(const GF& gf, uint32_t* rs, int l
     }
 #pragma unroll
     for (int x = 0; x < NC; x++) {
-      const uint32_t up = __shfl_up_sync(FULL_MASK, src[x], 1);
-      const uint32_t carry = x > 0 ? __shfl_sync(FULL_MASK, src[x > 0 ? x - 1 : 0], 31) : 0u;
-      const uint32_t nb = lane == 0 ? carry : up;
-      bp[x] = (lane + 32 * x) < CAP ? nb : 0u;
+      const uint32_t up = __shfl_up_sync(FULL_MASK, src[x], 1, SEG);
+      const uint32_t carry = x > 0 ? __shfl_sync(FULL_MASK, src[x > 0 ? x - 1 : 0], SEG - 1, SEG) : 0u;
+      const uint32_t nb = sl == 0 ? carry : up;
+      bp[x] = (sl + SEG * x) < CAP ? nb : 0u;
     }
     lb = sel(cond, ld, lb);
     L = sel(cond, (uint32_t)rr + 1u - L, L);
   }
 #pragma unroll
   for (int x = 0; x < NC; x++) {
-    const int c = lane + 32 * x;
+    const int c = sl + SEG * x;
     if (c < CAP) {
       logLam[c] = (uint16_t)gf.log(lam[x]);
-      if (ALL_POS) dbg->lam[c] = (uint8_t)lam[x];
+      if (ALL_POS && active) dbg->lam[c] = (uint8_t)lam[x];
     }
   }
-  if (ALL_POS && lane == 0) *dbg->L = (int32_t)L;
+  if (ALL_POS && active && sl == 0) *dbg->L = (int32_t)L;
   __syncwarp();
 
   // Omega_k = sum_{c <= k} Lambda_c S_{k+1-c}, k < 2 delta
 #pragma unroll
   for (int x = 0; x < NS; x++) {
-    const int kk = lane + 32 * x;
+    const int kk = sl + SEG * x;
     uint32_t om = 0;
 #pragma unroll 4
     for (int c = 0; c < NR; c++) {
       const bool in = c <= kk;
-      const uint32_t t = gf.mul_l(logLam[c], logS[in ? kk - c : 0]);
+      const uint32_t t = gf.mul_l(logLam[c], logS[in && kk < NR ? kk - c : 0]);
       om ^= sel(in, t, 0u);
     }
     if (kk < NR) logOm[kk] = (uint16_t)gf.log(om);
@@ -447,12 +451,13 @@ __device__ __forceinline__ void rs_decode_warp(const GF& gf, uint32_t* rs, int l
   __syncwarp();
 
   // Chien + Forney at position j: powers of alpha^{-j}
-  constexpr int NPOS = ALL_POS ? cdiv(n1, 32) : 1;
+  constexpr int NPOS = ALL_POS ? cdiv(n1, SEG) : cdiv(k, SEG);
   uint32_t roots = 0;
 #pragma unroll
   for (int y = 0; y < NPOS; y++) {
-    const int j = ALL_POS ? lane + 32 * y : (n1 - k) + lane;
-    const bool valid = ALL_POS ? j < n1 : lane < k;
+    const int pos = sl + SEG * y;
+    const int j = ALL_POS ? pos : (n1 - k) + pos;
+    const bool valid = ALL_POS ? pos < n1 : pos < k;
     const uint32_t jj = valid ? (uint32_t)j : 0u;
     const uint32_t step = jj == 0 ? 0u : 255u - jj;
     uint32_t ec = 0, ecp = 0, lamv = 0, omv = 0, dlv = 0;
@@ -470,28 +475,29 @@ __device__ __forceinline__ void rs_decode_warp(const GF& gf, uint32_t* rs, int l
     const uint32_t ev = sel(root, gf.div_l(gf.log(omv), gf.log(dlv)), 0u);
     const uint32_t cwj = (uint32_t)r[jj] ^ ev;
     if (ALL_POS) {
-      roots += __popc(__ballot_sync(FULL_MASK, root && valid));
-      if (valid) {
+      const uint32_t segmask = SEG == 32 ? FULL_MASK : (((1u << SEG) - 1u) << (lane - sl));
+      roots += __popc(__ballot_sync(FULL_MASK, root && valid) & segmask);
+      if (valid && active) {
         dbg->errmask[j] = (uint8_t)root;
         dbg->errval[j] = (uint8_t)ev;
         dbg->cw[j] = (uint8_t)cwj;
         if (j >= n1 - k) m_out[j - (n1 - k)] = (uint8_t)cwj;
       }
-    } else if (valid) {
-      m_out[lane] = (uint8_t)cwj;
+    } else if (valid && active) {
+      m_out[pos] = (uint8_t)cwj;
     }
   }
-  if (ALL_POS && lane == 0) *dbg->flag = (int32_t)((L > (uint32_t)delta) || (roots != L));
+  if (ALL_POS && active && sl == 0) *dbg->flag = (int32_t)((L > (uint32_t)delta) || (roots != L));
 }
 
 // ---------------------------------------------------------------------------
-// Whole decryption of one ciphertext by one warp (S1-S9).
-// ws: WARP_WORDS of shared memory owned by this warp.
+// S1-S7 of one ciphertext by one warp: product, XOR with v, RM decode; the
+// n1 RM bytes go to r_out.  ws: U2W + WP words owned by this warp.
 // ---------------------------------------------------------------------------
 template <class LV, bool MASKED>
-__device__ __forceinline__ void decrypt_one(const GF& gf, uint32_t* ws, int lane, const uint64_t* __restrict__ urow,
-                                            const uint64_t* __restrict__ vrow, const uint32_t* __restrict__ yrow,
-                                            uint8_t* __restrict__ mrow) {
+__device__ __forceinline__ void product_rm_one(uint32_t* ws, int lane, const uint64_t* __restrict__ urow,
+                                               const uint64_t* __restrict__ vrow, const uint32_t* __restrict__ yrow,
+                                               uint8_t* r_out) {
   constexpr int WPT = LV::WPT, W_v32 = LV::W_v32;
   uint32_t* u2 = ws;
   uint32_t* sup = ws + LV::U2W;
@@ -513,11 +519,56 @@ __device__ __forceinline__ void decrypt_one(const GF& gf, uint32_t* ws, int lane
     if (i < W_v32) u2[i] = acc[k];
   }
   __syncwarp();
-  uint8_t* r = reinterpret_cast<uint8_t*>(ws + LV::RS_R);
-  rm_decode_warp<LV>(u2, r, lane);
+  rm_decode_warp<LV>(u2, r_out, lane);
   __syncwarp();
-  rs_decode_warp<LV, false>(gf, ws + LV::RS_R, lane, mrow, nullptr);
+}
+
+// Per-warp shared memory of the fused kernels: u2 and the support list,
+// then the RM bytes of up to G ciphertexts kept for the grouped RS stage.
+// (a multiple of 4 words, so every warp's u2 stays 16-byte aligned for the
+// vector stores that stage u)
+template <class LV, int G>
+__host__ __device__ constexpr int fused_warp_words() {
+  return round_up(LV::U2W + LV::WP + G * cdiv(LV::n1, 4), 4);
+}
+
+// Whole decryption (S1-S9) of G ciphertexts by one warp: product and RM
+// for each in turn, then Reed-Solomon for all G side by side on 32 / G
+// lanes each.  rows(g, u, v, y, m) fills ciphertext g's rows and returns
+// false for a slot past the end of the batch (skipped, nothing stored).
+template <class LV, int G, bool MASKED, class Rows>
+__device__ __forceinline__ void decrypt_group(const GF& gf, uint32_t* ws, int lane, const Rows& rows) {
+  constexpr int RB = cdiv(LV::n1, 4) * 4;  // bytes per stored RM word
+  static_assert(G * RS_SCRATCH <= LV::U2W, "RS scratch of G words fits in u2");
+  static_assert(fused_warp_words<LV, G>() % 4 == 0 && LV::U2W % 4 == 0 && LV::WP % 4 == 0, "16-byte alignment");
+  uint8_t* rbuf = reinterpret_cast<uint8_t*>(ws + LV::U2W + LV::WP);
+  const uint64_t* u;
+  const uint64_t* v;
+  const uint32_t* y;
+  uint8_t* m;
+#pragma unroll 1
+  for (int g = 0; g < G; g++)
+    if (rows(g, u, v, y, m)) product_rm_one<LV, MASKED>(ws, lane, u, v, y, rbuf + g * RB);
+  constexpr int SEG = 32 / G;
+  const int seg = lane / SEG;
+  const bool act = rows(seg, u, v, y, m);
+  rs_decode_seg<LV, SEG, false>(gf, ws + seg * RS_SCRATCH, rbuf + seg * RB, lane, act, m, nullptr);
   __syncwarp();
+}
+
+// One ciphertext (G = 1), as used by the mixed-level kernel.
+template <class LV, bool MASKED>
+__device__ __forceinline__ void decrypt_one(const GF& gf, uint32_t* ws, int lane, const uint64_t* __restrict__ urow,
+                                            const uint64_t* __restrict__ vrow, const uint32_t* __restrict__ yrow,
+                                            uint8_t* __restrict__ mrow) {
+  auto rows = [&](int, const uint64_t*& u, const uint64_t*& v, const uint32_t*& y, uint8_t*& m) {
+    u = urow;
+    v = vrow;
+    y = yrow;
+    m = mrow;
+    return true;
+  };
+  decrypt_group<LV, 1, MASKED>(gf, ws, lane, rows);
 }
 
 }  // namespace hqc

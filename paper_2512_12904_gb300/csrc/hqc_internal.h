@@ -5,6 +5,14 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+// A registered keyset (public handle hqc_keyset_t).
+struct hqc_keyset_s {
+  int level;
+  int64_t nkeys;
+  int device;
+  uint32_t* d_table;  // [nkeys][w] support positions, each < n, distinct per row
+};
+
 namespace hqc {
 
 // Launch shape of the persistent fused kernel: warps per block and blocks
@@ -66,6 +74,11 @@ cudaError_t launch_staged(int level, bool keyed, const DecArgs& a, uint64_t* w_w
 cudaError_t launch_debug(int level, const DecArgs& a, const DebugArgs& d, cudaStream_t st);
 cudaError_t launch_mixed(const MixedArgs& a, cudaStream_t st, const LaunchCfg& cfg);
 cudaError_t fused_occupancy(int level, bool keyed, const LaunchCfg& cfg, int* warps, int* ctas_per_sm, int* grid);
+// One level's items of a mixed list (a.items all of that level), at most
+// `grid` blocks (0 = a full persistent grid).
+cudaError_t launch_items(int level, const MixedArgs& a, int grid, cudaStream_t st, const LaunchCfg& cfg);
+cudaError_t items_occupancy(int level, const LaunchCfg& cfg, int* warps, int* ctas_per_sm, int* grid);
+cudaError_t mixed_occupancy(const LaunchCfg& cfg, int* warps, int* ctas_per_sm, int* grid);
 
 cudaError_t launch_keygen(int level, int64_t nkeys, const uint64_t* h, const uint32_t* x, const uint32_t* y,
                           uint64_t* s, cudaStream_t st);

@@ -35,8 +35,8 @@ __host__ __device__ constexpr int round_up(int a, int b) { return cdiv(a, b) * b
 //   u2[U2W]   the 2n-bit string u||u (second copy starts at bit n) so a
 //             rotation by p is the 32-bit window at bit offset 32 i + n - p;
 //   sup[WP]   one packed word per support entry (see pack_support).
-// After the product the w = v + u*y words overwrite u2[0, W_v32) and the
-// Reed-Solomon scratch lives in u2[W_v32, U2W).
+// After the product the w = v + u*y words overwrite u2[0, W_v32); once the
+// RM bytes are out, u2 is scratch for the Reed-Solomon stage.
 template <int LEVEL> struct Level : LevelConst<LEVEL> {
   using C = LevelConst<LEVEL>;
   static constexpr int level = LEVEL;
@@ -54,7 +54,7 @@ template <int LEVEL> struct Level : LevelConst<LEVEL> {
   // highest u2 word a lane may read: 32*WPT - 1 + (n >> 5) + 1
   static constexpr int U2W = round_up(cmax(cdiv(2 * C::n, 32), 32 * WPT + (C::n >> 5) + 1), 4);
   static constexpr int WP = round_up(C::w, 4);
-  static constexpr int WARP_WORDS = U2W + WP;       // shared words per warp
+  static constexpr int WARP_WORDS = U2W + WP;       // u2 and the support list
   // full-length (n-bit) product used by key generation and encryption
   static constexpr int WPT_FULL = odd_at_least(cdiv(N32, 32));
   static constexpr int U2W_FULL = round_up(cmax(cdiv(2 * C::n, 32), 32 * WPT_FULL + (C::n >> 5) + 1), 4);
@@ -62,12 +62,7 @@ template <int LEVEL> struct Level : LevelConst<LEVEL> {
   static_assert(C::n1 * n2 % 64 == 0, "v is a whole number of words");
   static_assert(C::n1 - C::k == NR, "RS code has n1 - k = 2 delta");
   static_assert(C::k <= 32, "one message byte per lane");
-  // Reed-Solomon scratch behind w: r (n1 bytes, 24 words), log r (96
-  // halfwords), log S, log Lambda, log Omega (64 halfwords each)
-  static constexpr int RS_R = W_v32, RS_LOGR = W_v32 + 24, RS_LOGS = RS_LOGR + 48,
-                       RS_LOGLAM = RS_LOGS + 32, RS_LOGOM = RS_LOGLAM + 32, RS_END = RS_LOGOM + 32;
   static_assert(C::n1 <= 96 && CAP <= 64, "RS scratch sizes");
-  static_assert(RS_END <= U2W, "RS scratch fits behind w");
 };
 
 }  // namespace hqc

@@ -194,3 +194,71 @@ def test_full_size_hqc1_bulk_sampled(hqc):
     sample = synth.below(65536, 128, tag=14)
     want = oracle.decrypt(1, wl.u[sample], wl.v[sample], wl.y_rows[sample])
     assert (got[sample] == want).all()
+
+
+def _mixed_batch(hqc, counts=((1, 40), (3, 35), (5, 25)), first_ct=30000, tag=15):
+    parts = {lvl: honest(lvl, 6, cnt, first_ct=first_ct, tag=tag) for lvl, cnt in counts}
+    seq = [(lvl, i) for lvl, cnt in counts for i in range(cnt)]
+    order = synth.shuffle(np.arange(len(seq), dtype=np.int32), tag=tag + 1)
+    seq = [seq[j] for j in order]
+    items = np.zeros(len(seq), dtype=hqc.ITEM_DTYPE)
+    arena, m_off, words, want = [], 0, 0, []
+    for idx, (lvl, i) in enumerate(seq):
+        wl = parts[lvl]
+        items[idx] = (lvl, wl.key_idx[i], words, words + wl.P.W_u_pitch, m_off)
+        arena += [wl.u[i], wl.v[i]]
+        words += wl.P.W_u_pitch + wl.P.W_v
+        m_off += wl.P.k
+        want.append(wl.m[i])
+    keys = [hqc.Keyset(l, parts[l].y) if l in parts else None for l in (1, 3, 5)]
+    return dev(items.view(np.uint8)), u64(np.concatenate(arena)), keys, m_off, np.concatenate(want)
+
+
+def test_mixed_plan_graph_autotuned(hqc):
+    items, arena, keys, nbytes, want = _mixed_batch(hqc)
+    m = torch.zeros(nbytes, dtype=torch.uint8, device="cuda")
+    plan = hqc.hqc_plan_create_mixed(items, arena, keys, m, autotune=True)
+    info = plan.info()
+    assert info["form"] in ("mixed-single-kernel", "mixed-level-partitioned", "mixed-per-level-sequential")
+    for _ in range(2):
+        m.zero_()
+        plan.launch()
+        torch.cuda.synchronize()
+        assert (host(m) == want).all()
+    plan.destroy()
+    # without tuning: the single-kernel form with the default shape
+    plan2 = hqc.hqc_plan_create_mixed(items, arena, keys, m, autotune=False)
+    m.zero_()
+    plan2.launch()
+    torch.cuda.synchronize()
+    assert plan2.info()["form"] == "mixed-single-kernel" and (host(m) == want).all()
+    plan2.destroy()
+
+
+def test_mixed_plan_single_level_present(hqc):
+    items, arena, keys, nbytes, want = _mixed_batch(hqc, counts=((3, 30),), first_ct=31000, tag=17)
+    m = torch.zeros(nbytes, dtype=torch.uint8, device="cuda")
+    plan = hqc.hqc_plan_create_mixed(items, arena, keys, m, autotune=True)
+    plan.launch()
+    torch.cuda.synchronize()
+    assert (host(m) == want).all()
+    plan.destroy()
+
+
+@pytest.mark.parametrize("level", LEVELS)
+def test_keyed_plan_graph_replay(hqc, level):
+    wl = honest(level, 8, 300 if level == 1 else 120, first_ct=32000, tag=18)
+    keys = hqc.Keyset(level, wl.y)
+    ud, vd = u64(wl.u), u64(wl.v)
+    kidx = dev(wl.key_idx.astype(np.int32))
+    m = torch.zeros((ud.shape[0], wl.P.k), dtype=torch.uint8, device="cuda")
+    plan = hqc.hqc_plan_create_keyed(level, ud, vd, keys, kidx, m, autotune=True)
+    direct = host(hqc.hqc_decrypt_batch_keyed(level, ud, vd, keys, kidx))
+    for _ in range(3):
+        m.zero_()
+        plan.launch()
+        torch.cuda.synchronize()
+        assert (host(m) == direct).all() and (direct == wl.m).all()
+    assert plan.info()["tuned_ms"] > 0
+    plan.destroy()
+    keys.free()
