@@ -598,7 +598,7 @@ def run_ours(args):
 
 def traffic_from_profile(level):
     """DRAM bytes per launch of the fused kernel from the committed ncu summary, if current."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    path = os.path.join(ROOT, "profiles", "dram_traffic_per_launch.txt")
     try:
         with open(path) as f:
             rec = json.load(f)
