@@ -223,6 +223,56 @@ int hqc_plan_launch(hqc_plan_t* plan, void* stream);
 int hqc_plan_info(const hqc_plan_t* plan, int32_t* form, hqc_launch_cfg_t* cfg, int32_t* grids3, float* tuned_ms);
 int hqc_plan_destroy(hqc_plan_t* plan);
 
+/* Continuous-batching service loop over an open-loop request trace.
+ *
+ * Request i (i < count) arrives arrival_ns[i] nanoseconds after the call
+ * starts (non-decreasing) and uses ring entry j = i % ring->period: level
+ * ring->level[j], key ring->key[j] (an index into keys[level]), its u row
+ * then v row at ring->words + ring->word_off[j] (PINNED host memory,
+ * entries contiguous in ring order, word_off[period] = total words), and
+ * its k result bytes at m_out + ring->m_off[j] (host; NULL to drop results;
+ * a later request on the same entry overwrites them).
+ * One host thread admits arrived requests into batches for `streams` CUDA
+ * streams while a batch fits that stream's budget_bytes / streams of
+ * device memory and max_batch requests; each batch is one copy in, one
+ * persistent kernel per level present, one copy out.  Batches run
+ * concurrently, and new arrivals are admitted whenever a stream frees up.
+ * A request that arrives while max_queue requests wait is rejected.
+ * Outputs per request: status[i] (HQC_STATUS_*) and latency_ns[i] =
+ * completion time - arrival time (-1 unless DONE).  The call allocates the
+ * budget at start and frees it before returning; it returns when every
+ * request is answered. */
+#define HQC_STATUS_DONE 0
+#define HQC_STATUS_QUEUED 1
+#define HQC_STATUS_RUNNING 2
+#define HQC_STATUS_REJECTED 3   /* queue full when it arrived */
+#define HQC_STATUS_INVALID 4    /* bad level, absent keyset or key index out of range */
+#define HQC_STATUS_TOO_LARGE 5  /* does not fit one stream's memory share */
+typedef struct hqc_serve_cfg_s {
+  int32_t streams;        /* batches in flight, 1..16 */
+  int32_t max_batch;      /* requests per batch at most */
+  int64_t budget_bytes;   /* device memory for request data, split over the streams */
+  int64_t max_queue;      /* waiting requests at most */
+  int32_t warps_per_cta;  /* launch shape of the per-level kernels (0 = default) */
+} hqc_serve_cfg_t;
+typedef struct hqc_serve_ring_s {
+  int64_t period;
+  const int32_t* level;     /* [period] */
+  const int32_t* key;       /* [period] */
+  const int64_t* word_off;  /* [period + 1] */
+  const uint64_t* words;    /* pinned host */
+  const int64_t* m_off;     /* [period + 1] */
+} hqc_serve_ring_t;
+typedef struct hqc_serve_stats_s {
+  int64_t completed, rejected_queue, rejected_invalid, rejected_size, batches;
+  double mean_batch;
+  int64_t wall_ns;          /* start to last completion */
+  int64_t items_per_slot;   /* batch capacity the budget allows */
+} hqc_serve_stats_t;
+int hqc_serve_run(const hqc_serve_cfg_t* cfg, const hqc_keyset_t* const keys[3], const hqc_serve_ring_t* ring,
+                  int64_t count, const int64_t* arrival_ns, int32_t* status, int64_t* latency_ns, uint8_t* m_out,
+                  hqc_serve_stats_t* stats);
+
 /* Key generation core of Algorithm 3: s = x + h*y per key.
  * h, s_out [nkeys][W_u_pitch]; x, y [nkeys][w] (device). */
 int hqc_keygen_batch(int level, int64_t nkeys, const uint64_t* h, const uint32_t* x, const uint32_t* y,

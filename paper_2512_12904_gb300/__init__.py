@@ -22,7 +22,8 @@ __all__ = [
     "hqc_keys_register", "hqc_decrypt_batch_keyed", "hqc_staged_workspace_bytes",
     "hqc_decrypt_batch_staged", "hqc_decrypt_batch_staged_noalloc", "hqc_decrypt_debug", "hqc_mixed_workspace_bytes",
     "hqc_decrypt_mixed", "hqc_set_launch_config", "hqc_get_launch_shape", "hqc_keygen_batch",
-    "hqc_encrypt_batch", "LEVELS", "Plan", "hqc_plan_create_keyed", "hqc_plan_create_mixed",
+    "hqc_encrypt_batch", "LEVELS", "Plan", "hqc_plan_create_keyed", "hqc_plan_create_mixed", "hqc_serve_run",
+    "SERVE_STATUS",
 ]
 
 LEVELS = (1, 3, 5)
@@ -87,6 +88,7 @@ def load(build_if_missing: bool = True):
             "hqc_plan_launch": (i32, [P, P]),
             "hqc_plan_info": (i32, [P, P, P, P, P]),
             "hqc_plan_destroy": (i32, [P]),
+            "hqc_serve_run": (i32, [P, P, P, i64, P, P, P, P, P]),
             "hqc_keygen_batch": (i32, [i32, i64, P, P, P, P, P]),
             "hqc_encrypt_batch": (i32, [i32, i64, P, P, i64, P, P, P, P, P, P, P, P]),
         }
@@ -452,3 +454,59 @@ def hqc_plan_create_mixed(items, arena, keys, m_arena, autotune=True, stream=Non
                                         _dev_ptr(m_arena, torch.uint8, None, "m_arena"), m_arena.numel(),
                                         int(bool(autotune)), _stream(stream), ctypes.byref(h)))
     return Plan(h, (items, arena, keys, m_arena))
+
+
+class _ServeCfg(ctypes.Structure):
+    _fields_ = [("streams", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("budget_bytes", ctypes.c_int64),
+                ("max_queue", ctypes.c_int64), ("warps_per_cta", ctypes.c_int32)]
+
+
+class _ServeRing(ctypes.Structure):
+    _fields_ = [("period", ctypes.c_int64), ("level", ctypes.c_void_p), ("key", ctypes.c_void_p),
+                ("word_off", ctypes.c_void_p), ("words", ctypes.c_void_p), ("m_off", ctypes.c_void_p)]
+
+
+class _ServeStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("rejected_queue", ctypes.c_int64),
+                ("rejected_invalid", ctypes.c_int64), ("rejected_size", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("mean_batch", ctypes.c_double), ("wall_ns", ctypes.c_int64),
+                ("items_per_slot", ctypes.c_int64)]
+
+
+SERVE_STATUS = {0: "done", 1: "queued", 2: "running", 3: "rejected", 4: "invalid", 5: "too_large"}
+
+
+def hqc_serve_run(keys, ring_level, ring_key, ring_word_off, ring_words, ring_m_off, arrival_ns, streams=4,
+                  max_batch=8192, budget_bytes=256 << 20, max_queue=1 << 20, warps_per_cta=0, want_m=True):
+    """Run the continuous-batching loop over a request trace (hqc_serve_run).
+
+    ring_words must be a PINNED uint64/int64 CPU tensor; the other ring
+    arrays are numpy.  Returns (status, latency_ns, m_out or None, stats)."""
+    torch = _torch()
+    if not isinstance(ring_words, torch.Tensor) or ring_words.is_cuda or not ring_words.is_pinned():
+        raise ValueError("ring_words must be a pinned CPU tensor")
+    lvl = np.ascontiguousarray(ring_level, np.int32)
+    key = np.ascontiguousarray(ring_key, np.int32)
+    woff = np.ascontiguousarray(ring_word_off, np.int64)
+    moff = np.ascontiguousarray(ring_m_off, np.int64)
+    arr = np.ascontiguousarray(arrival_ns, np.int64)
+    period = lvl.size
+    if key.size != period or woff.size != period + 1 or moff.size != period + 1:
+        raise ValueError("ring arrays disagree on the period")
+    if woff[-1] > ring_words.numel():
+        raise ValueError("ring_words is shorter than word_off says")
+    cnt = arr.size
+    status = np.zeros(cnt, np.int32)
+    lat = np.zeros(cnt, np.int64)
+    m_out = np.zeros(int(moff[-1]), np.uint8) if want_m else None
+    cfg = _ServeCfg(streams, max_batch, budget_bytes, max_queue, warps_per_cta)
+    ring = _ServeRing(period, lvl.ctypes.data_as(ctypes.c_void_p), key.ctypes.data_as(ctypes.c_void_p),
+                      woff.ctypes.data_as(ctypes.c_void_p), ctypes.c_void_p(ring_words.data_ptr()),
+                      moff.ctypes.data_as(ctypes.c_void_p))
+    karr = (ctypes.c_void_p * 3)(*[(k.handle if k is not None else None) for k in keys])
+    st = _ServeStats()
+    _check(load().hqc_serve_run(ctypes.byref(cfg), karr, ctypes.byref(ring), cnt, arr.ctypes.data_as(ctypes.c_void_p),
+                                status.ctypes.data_as(ctypes.c_void_p), lat.ctypes.data_as(ctypes.c_void_p),
+                                m_out.ctypes.data_as(ctypes.c_void_p) if want_m else None, ctypes.byref(st)))
+    stats = {f: getattr(st, f) for f, _ in _ServeStats._fields_}
+    return status, lat, m_out, stats

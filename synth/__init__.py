@@ -161,3 +161,33 @@ def splitmix_raw(seed: int, length: int) -> np.ndarray:
     out = np.zeros(length, np.uint64)
     _load().synth_splitmix_raw(seed, _p(out), length)
     return out
+
+
+def burst_trace(rate_per_s: float, duration_s: float, tag: int, max_burst: int = 512,
+                master: int = MASTER_SEED) -> np.ndarray:
+    """Open-loop arrival times (ns, non-decreasing) of single requests.
+
+    Bursts arrive as a Poisson process; a burst carries B requests with B a
+    log-uniform integer in [1, max_burst] (B = floor(exp(U ln(max_burst+1))),
+    U uniform in [0, 1)), all with the burst's arrival time.  The burst rate
+    is rate_per_s / E[B], so requests arrive at rate_per_s on average."""
+    ln = np.log(max_burst + 1.0)
+    b = np.arange(1, max_burst + 1, dtype=np.float64)
+    mean_b = float(((np.log(b + 1) - np.log(b)) / ln * b).sum())
+    n_bursts = max(1, int(rate_per_s * duration_s / mean_b * 1.2) + 16)
+    u = (words(2 * n_bursts, tag=tag, index=1, master=master) >> np.uint64(11)).astype(np.float64) / 2.0 ** 53
+    gaps = -np.log1p(-u[:n_bursts]) / (rate_per_s / mean_b)
+    sizes = np.floor(np.exp(u[n_bursts:] * ln)).astype(np.int64).clip(1, max_burst)
+    t = np.cumsum(gaps)
+    keep = t < duration_s
+    t, sizes = t[keep], sizes[keep]
+    return np.repeat((t * 1e9).astype(np.int64), sizes)
+
+
+def level_mix(n: int, shares, tag: int, master: int = MASTER_SEED) -> np.ndarray:
+    """n levels drawn with the given {level: share} weights, shuffled."""
+    levels = []
+    for lvl, share in shares:
+        levels += [lvl] * int(round(n * share))
+    levels = np.array((levels + [shares[0][0]] * n)[:n], np.int32)
+    return shuffle(levels, tag=tag, master=master)
