@@ -249,14 +249,32 @@ __device__ __forceinline__ uint32_t rm_decode_pair(const uint32_t* blk, uint32_t
       }
     }
   }
+  // Packed counts of positions q and q + 16: the count planes are first
+  // bit-interleaved so one shift and one mask extract a whole count
+  // (positions q, q+1 for mult 3; q..q+2 in residue classes mod 4 for 5).
   uint32_t R[32];
 #pragma unroll
   for (int tt = 0; tt < 2; tt++) {
+    if (MULT == 3) {
+      const uint32_t z0 = (p0[tt] & 0x55555555u) | ((p1[tt] & 0x55555555u) << 1);  // even q
+      const uint32_t z1 = ((p0[tt] & 0xAAAAAAAAu) >> 1) | (p1[tt] & 0xAAAAAAAAu);  // odd q
 #pragma unroll
-    for (int q = 0; q < 16; q++) {
-      uint32_t cnt = ((p0[tt] >> q) & 0x10001u) + (((p1[tt] >> q) & 0x10001u) << 1);
-      if (MULT == 5) cnt += ((p2[tt] >> q) & 0x10001u) << 2;
-      R[16 * tt + q] = K - 2u * cnt;
+      for (int q = 0; q < 16; q++) {
+        const uint32_t cnt = ((q & 1 ? z1 : z0) >> (q & ~1)) & 0x00030003u;
+        R[16 * tt + q] = K - 2u * cnt;
+      }
+    } else {
+      uint32_t z[4];
+#pragma unroll
+      for (int rr = 0; rr < 4; rr++) {
+        const uint32_t mk = 0x11111111u << rr;
+        z[rr] = ((p0[tt] & mk) >> rr) | (((p1[tt] & mk) >> rr) << 1) | (((p2[tt] & mk) >> rr) << 2);
+      }
+#pragma unroll
+      for (int q = 0; q < 16; q++) {
+        const uint32_t cnt = (z[q & 3] >> (q & ~3)) & 0x00070007u;
+        R[16 * tt + q] = K - 2u * cnt;
+      }
     }
   }
 #pragma unroll
