@@ -650,7 +650,7 @@ def run_ours(args):
     }
     primary = max(("smem", "alu"), key=lambda k: blocks[k]["frac"] or 0)
     roofline = dict(blocks[primary])
-    roofline["kernel"] = "k_decrypt_fused<%d,keyed>" % level
+    roofline["kernel"] = ("k_decrypt_team<%d,keyed>" if level == 5 else "k_decrypt_fused<%d,keyed>") % level
     roofline["traffic"] = traffic_from_profile(level)
     roofline["others"] = {k: v for k, v in blocks.items() if k != primary}
 
@@ -697,7 +697,7 @@ def traffic_from_profile(level):
         return None
     from paper_2512_12904_gb300 import _build
     ent = rec.get("hqc%d" % level)
-    if not ent or ent.get("source_digest") != _build._digest():
+    if not ent or ent.get("kernel_digest") != _build.kernel_digest():
         return None
     return ent.get("dram_bytes_per_launch")
 

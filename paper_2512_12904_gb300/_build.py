@@ -39,6 +39,17 @@ def _digest() -> str:
     return h.hexdigest()
 
 
+def kernel_digest() -> str:
+    """Digest of the sources of the decryption kernels alone (hqc_decrypt.cu
+    and the headers it includes): profile counters stay valid while it holds."""
+    h = hashlib.sha256()
+    for f in ("hqc_decrypt.cu", "hqc_device.cuh", "hqc_params.cuh", "hqc_internal.h"):
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(fh.read())
+    h.update(" ".join(ARCH + FLAGS).encode())
+    return h.hexdigest()
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     """Compile if the sources changed since the last build; return the .so path."""
     os.makedirs(BUILD, exist_ok=True)

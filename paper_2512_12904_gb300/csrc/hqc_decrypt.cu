@@ -8,6 +8,8 @@
 //     that dumps every intermediate.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "hqc_device.cuh"
 #include "hqc_internal.h"
 
@@ -65,6 +67,52 @@ __global__ void __launch_bounds__(FusedBound<LEVEL>::threads, 1) k_decrypt_fused
       return ok;
     };
     decrypt_group<LV, G, !KEYED>(gf, ws, lane, rows);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fused persistent kernel with two-warp teams (HQC-3 and HQC-5): team t of
+// the grid takes pairs of consecutive ciphertexts t, t + (all teams), ...
+// At most 15 teams per block (named barriers 1..15).
+// ---------------------------------------------------------------------------
+template <int LEVEL> struct TeamBound;
+template <> struct TeamBound<1> { static constexpr int threads = 960; };
+template <> struct TeamBound<3> { static constexpr int threads = 960; };
+template <> struct TeamBound<5> { static constexpr int threads = 768; };
+// Levels that use the team kernels.  Measured on GB300: HQC-5 gains 26 %
+// (24 warps per SM instead of 13); HQC-3 loses 17 % (its half strips waste
+// 8.6 % of the product and 20 solo warps already hide enough latency).
+template <int LEVEL> struct UseTeam { static constexpr bool value = LEVEL == 5; };
+
+template <int LEVEL, bool KEYED>
+__global__ void __launch_bounds__(TeamBound<LEVEL>::threads, 1) k_decrypt_team(DecArgs a) {
+  using LV = Level<LEVEL>;
+  extern __shared__ __align__(16) uint8_t smem[];
+  gf_tables_init(smem, threadIdx.x, blockDim.x);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int team = warp >> 1, wt = warp & 1, nteams = blockDim.x >> 6;
+  const GF gf(smem, lane);
+  uint32_t* ws = reinterpret_cast<uint32_t*>(smem + GF_TABLE_BYTES) + team * Team<LV>::WORDS;
+  const TeamSync sync{(uint32_t)(1 + team)};
+  const int64_t ngroups = (a.count + 1) / 2;
+  for (int64_t q = (int64_t)blockIdx.x * nteams + team; q < ngroups; q += (int64_t)gridDim.x * nteams) {
+    auto rows = [&](int g, const uint64_t*& u, const uint64_t*& v, const uint32_t*& y, uint8_t*& m) {
+      const int64_t it0 = 2 * q + g;
+      const bool ok = it0 < a.count;
+      const int64_t it = ok ? it0 : 2 * q;
+      if (KEYED) {
+        const uint32_t ki = (uint32_t)__ldg(a.key_idx + it);
+        y = a.y + (ki < (uint64_t)a.nkeys ? (int64_t)ki : 0) * LV::w;  // out-of-range index -> key 0
+      } else {
+        y = a.y + it * LV::w;
+      }
+      u = a.u + it * LV::W_u_pitch;
+      v = a.v + it * LV::W_v;
+      m = a.m + it * LV::k;
+      return ok;
+    };
+    decrypt_team<LV, !KEYED>(gf, ws, wt, lane, sync, rows);
   }
 }
 
@@ -151,6 +199,37 @@ __global__ void __launch_bounds__(FusedBound<LEVEL>::threads, 1) k_decrypt_items
       return ok;
     };
     decrypt_group<LV, G, false>(gf, ws, lane, rows);
+  }
+}
+
+template <int LEVEL>
+__global__ void __launch_bounds__(TeamBound<LEVEL>::threads, 1) k_decrypt_items_team(MixedArgs a) {
+  using LV = Level<LEVEL>;
+  constexpr int li = LEVEL == 1 ? 0 : LEVEL == 3 ? 1 : 2;
+  extern __shared__ __align__(16) uint8_t smem[];
+  gf_tables_init(smem, threadIdx.x, blockDim.x);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int team = warp >> 1, wt = warp & 1, nteams = blockDim.x >> 6;
+  const GF gf(smem, lane);
+  uint32_t* ws = reinterpret_cast<uint32_t*>(smem + GF_TABLE_BYTES) + team * Team<LV>::WORDS;
+  const TeamSync sync{(uint32_t)(1 + team)};
+  const int64_t ngroups = (a.count + 1) / 2;
+  for (int64_t q = (int64_t)blockIdx.x * nteams + team; q < ngroups; q += (int64_t)gridDim.x * nteams) {
+    auto rows = [&](int g, const uint64_t*& u, const uint64_t*& v, const uint32_t*& y, uint8_t*& m) {
+      const int64_t it = 2 * q + g;
+      if (it >= a.count) return false;
+      const MixedItem item = a.items[it];
+      const bool ok = item.level == LEVEL && (uint32_t)item.key < (uint64_t)a.nkeys[li] && item.u_off >= 0 &&
+                      (item.u_off & 1) == 0 && item.u_off + LV::W_u_pitch <= a.arena_words && item.v_off >= 0 &&
+                      item.v_off + LV::W_v <= a.arena_words && item.m_off >= 0 && item.m_off + LV::k <= a.m_bytes;
+      u = a.arena + (ok ? item.u_off : 0);
+      v = a.arena + (ok ? item.v_off : 0);
+      y = a.keys[li] + (ok ? (int64_t)item.key * LV::w : 0);
+      m = a.m + (ok ? item.m_off : 0);
+      return ok;
+    };
+    decrypt_team<LV, false>(gf, ws, wt, lane, sync, rows);
   }
 }
 
@@ -251,18 +330,21 @@ static int device_props(int* sms, int* smem_optin) {
   return dev;
 }
 
+// per_warp: shared bytes per warp (for teams: per team / 2); teams: the
+// warp count must be even and at most 30 (15 named barriers).
 template <class KernelT>
 static cudaError_t shape_for(KernelT kern, int max_threads, size_t per_warp, const LaunchCfg& cfg, int* warps,
-                             int* ctas, int* grid, size_t* smem_bytes) {
+                             int* ctas, int* grid, size_t* smem_bytes, bool teams = false) {
   int sms = 0, optin = 0;
   device_props(&sms, &optin);
   int nw = cfg.warps_per_cta;
   if (nw <= 0) {
     nw = (int)((optin - GF_TABLE_BYTES) / per_warp);
     if (nw > max_threads / 32) nw = max_threads / 32;
+    if (teams) nw = std::min(nw & ~1, 30);
   }
-  if (nw < 1) nw = 1;
-  if (nw > max_threads / 32) return cudaErrorInvalidValue;
+  if (nw < 1 || (teams && (nw & 1))) return cudaErrorInvalidValue;
+  if (nw > max_threads / 32 || (teams && nw > 30)) return cudaErrorInvalidValue;
   const size_t sm = GF_TABLE_BYTES + (size_t)nw * per_warp;
   if (sm > (size_t)optin) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -281,8 +363,27 @@ static cudaError_t shape_for(KernelT kern, int max_threads, size_t per_warp, con
 }
 
 template <int LEVEL, bool KEYED>
+static cudaError_t team_level(const DecArgs& a, cudaStream_t st, const LaunchCfg& cfg, bool launch, int* warps,
+                              int* ctas, int* grid) {
+  int nw = 0, c = 0, g = 0;
+  size_t sm = 0;
+  cudaError_t e = shape_for(k_decrypt_team<LEVEL, KEYED>, TeamBound<LEVEL>::threads,
+                            (size_t)Team<Level<LEVEL>>::WORDS * 2, cfg, &nw, &c, &g, &sm, true);
+  if (e != cudaSuccess) return e;
+  if (warps) *warps = nw;
+  if (ctas) *ctas = c;
+  if (grid) *grid = g;
+  if (!launch || a.count == 0) return cudaSuccess;
+  const int64_t need = (a.count + nw - 1) / nw;  // nw / 2 teams, two ciphertexts each
+  if (need < g) g = (int)need;
+  k_decrypt_team<LEVEL, KEYED><<<g, nw * 32, sm, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int LEVEL, bool KEYED>
 static cudaError_t fused_level(const DecArgs& a, cudaStream_t st, const LaunchCfg& cfg, bool launch, int* warps,
                                int* ctas, int* grid) {
+  if (UseTeam<LEVEL>::value) return team_level<LEVEL, KEYED>(a, st, cfg, launch, warps, ctas, grid);
   int nw = 0, c = 0, g = 0;
   size_t sm = 0;
   cudaError_t e = shape_for(k_decrypt_fused<LEVEL, KEYED>, FusedBound<LEVEL>::threads,
@@ -330,8 +431,30 @@ cudaError_t launch_mixed(const MixedArgs& a, cudaStream_t st, const LaunchCfg& c
 }
 
 template <int LEVEL>
+static cudaError_t items_team_level(const MixedArgs& a, int grid, cudaStream_t st, const LaunchCfg& cfg, bool launch,
+                                    int* warps, int* ctas, int* full_grid) {
+  int nw = 0, c = 0, g = 0;
+  size_t sm = 0;
+  LaunchCfg tc = cfg;  // teams need an even warp count
+  if (tc.warps_per_cta > 0) tc.warps_per_cta = std::max(2, tc.warps_per_cta & ~1);
+  cudaError_t e = shape_for(k_decrypt_items_team<LEVEL>, TeamBound<LEVEL>::threads,
+                            (size_t)Team<Level<LEVEL>>::WORDS * 2, tc, &nw, &c, &g, &sm, true);
+  if (e != cudaSuccess) return e;
+  if (warps) *warps = nw;
+  if (ctas) *ctas = c;
+  if (full_grid) *full_grid = g;
+  if (!launch || a.count == 0) return cudaSuccess;
+  if (grid <= 0 || grid > g) grid = g;
+  const int64_t need = (a.count + nw - 1) / nw;
+  if (need < grid) grid = (int)need;
+  k_decrypt_items_team<LEVEL><<<grid, nw * 32, sm, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int LEVEL>
 static cudaError_t items_level(const MixedArgs& a, int grid, cudaStream_t st, const LaunchCfg& cfg, bool launch,
                                int* warps, int* ctas, int* full_grid) {
+  if (UseTeam<LEVEL>::value) return items_team_level<LEVEL>(a, grid, st, cfg, launch, warps, ctas, full_grid);
   int nw = 0, c = 0, g = 0;
   size_t sm = 0;
   cudaError_t e = shape_for(k_decrypt_items<LEVEL>, FusedBound<LEVEL>::threads, (size_t)fused_words<LEVEL>() * 4,

@@ -86,13 +86,20 @@ struct GF {
 // word) are cleared, so garbage there never reaches the product.
 // PITCH64 = 64-bit words per HBM row (even, 16-byte aligned rows).
 // ---------------------------------------------------------------------------
-template <int N, int PITCH64, int U2W>
-__device__ __forceinline__ void build_doubled(uint32_t* u2, const uint64_t* __restrict__ urow, int lane) {
+struct WarpSync {
+  __device__ __forceinline__ void operator()() const { __syncwarp(); }
+};
+
+// NT threads (tid in [0, NT)) build it together; sync() orders their
+// shared-memory writes (__syncwarp for one warp, a named barrier for a team).
+template <int N, int PITCH64, int U2W, int NT = 32, class Sync = WarpSync>
+__device__ __forceinline__ void build_doubled(uint32_t* u2, const uint64_t* __restrict__ urow, int tid,
+                                              const Sync& sync = Sync()) {
   constexpr int N32 = (N + 31) / 32, R = N & 31, F = N >> 5;
   const uint4* src = reinterpret_cast<const uint4*>(urow);
   uint4* dst = reinterpret_cast<uint4*>(u2);
 #pragma unroll 2
-  for (int i = lane; i < PITCH64 / 2; i += 32) {
+  for (int i = tid; i < PITCH64 / 2; i += NT) {
     uint4 x = __ldcs(src + i);
     uint32_t wv[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
@@ -104,28 +111,28 @@ __device__ __forceinline__ void build_doubled(uint32_t* u2, const uint64_t* __re
     }
     dst[i] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
   }
-  __syncwarp();
+  sync();
   // second copy: word a >= N32 holds bits [32a - N, 32a - N + 32) of u
 #pragma unroll 2
-  for (int a = N32 + lane; a < U2W; a += 32) {
+  for (int a = N32 + tid; a < U2W; a += NT) {
     const int o = 32 * a - N;
     const int kw = o >> 5, sh = o & 31;
     const uint32_t lo = kw < N32 ? u2[kw] : 0u;
     const uint32_t hi = kw + 1 < N32 ? u2[kw + 1] : 0u;
     u2[a] = __funnelshift_r(lo, hi, sh);
   }
-  __syncwarp();
+  sync();
   // straddle word: the first bits of the second copy start at bit R of word F
-  if (R && lane == 0) u2[F] |= u2[0] << R;
-  __syncwarp();
+  if (R && tid == 0) u2[F] |= u2[0] << R;
+  sync();
 }
 
 // Support entry p -> packed word: q0 = n - p (so the rotation by p reads
 // u2 from bit 32 i + q0), bit 31 = "p < n".  An entry p >= n packs to 0 and
 // its contribution is masked off.
-template <int N, int W>
-__device__ __forceinline__ void load_supports(uint32_t* sup, const uint32_t* __restrict__ yrow, int lane) {
-  for (int t = lane; t < W; t += 32) {
+template <int N, int W, int NT = 32>
+__device__ __forceinline__ void load_supports(uint32_t* sup, const uint32_t* __restrict__ yrow, int tid) {
+  for (int t = tid; t < W; t += NT) {
     const uint32_t p = __ldg(yrow + t);
     const uint32_t q0 = (uint32_t)N - p;
     sup[t] = sel(p < (uint32_t)N, q0 | 0x80000000u, 0u);
@@ -134,7 +141,8 @@ __device__ __forceinline__ void load_supports(uint32_t* sup, const uint32_t* __r
 
 // ---------------------------------------------------------------------------
 // S3 (Eq. 1): t = XOR over p in Supp(y) of x^p u, truncated to the first
-// 32*32*WPT bits.  Lane l owns output words [l*WPT, l*WPT + WPT).
+// (strips)*32*WPT bits.  Strip l (a lane, or a lane of a team) owns output
+// words [l*WPT, l*WPT + WPT).
 // Word i of x^p u is the 32-bit window of u2 at bit 32 i + n - p: two
 // neighbouring u2 words joined by one funnel shift.  The lane's strip of
 // WPT + 1 u2 words is read once per support entry; WPT odd keeps the
@@ -325,14 +333,15 @@ __device__ __forceinline__ uint32_t rm_decode_pair(const uint32_t* blk, uint32_t
   return a | ((1u - (best & 1u)) << 7);
 }
 
-// All n1 blocks of one ciphertext by one warp: 16 lane pairs per round.
+// All n1 blocks of one ciphertext by NP lane pairs (16 for one warp, 32
+// for a two-warp team), tid in [0, 2 NP).
 // w: the n1*n2-bit word vector (shared or global, 16-byte aligned).
-template <class LV>
-__device__ __forceinline__ void rm_decode_warp(const uint32_t* w, uint8_t* r, int lane) {
-  const uint32_t hb = lane & 1;
+template <class LV, int NP = 16>
+__device__ __forceinline__ void rm_decode_warp(const uint32_t* w, uint8_t* r, int tid) {
+  const uint32_t hb = tid & 1;
 #pragma unroll 1
-  for (int j0 = 0; j0 < LV::n1; j0 += 16) {
-    const int j = j0 + (lane >> 1);
+  for (int j0 = 0; j0 < LV::n1; j0 += NP) {
+    const int j = j0 + (tid >> 1);
     const int jj = j < LV::n1 ? j : LV::n1 - 1;
     const uint32_t byte = rm_decode_pair<LV::mult>(w + jj * (LV::n2 / 32), hb);
     if (j < LV::n1 && hb == 0) r[j] = (uint8_t)byte;
@@ -587,6 +596,80 @@ __device__ __forceinline__ void decrypt_one(const GF& gf, uint32_t* ws, int lane
     return true;
   };
   decrypt_group<LV, 1, MASKED>(gf, ws, lane, rows);
+}
+
+// ---------------------------------------------------------------------------
+// Two-warp teams.  Both warps of a team share one doubled operand: each
+// computes half of the product's output words (strips of WPT2 words), the
+// RM blocks spread over the team's 32 lane pairs, and the two warps decode
+// the Reed-Solomon stage of the team's two ciphertexts at the same time.
+// Half the shared memory per warp, so twice the warps fit on an SM (HQC-3
+// and HQC-5 are limited by shared memory, not registers).
+// Members synchronise with a named barrier of 64 threads.
+// ---------------------------------------------------------------------------
+struct TeamSync {
+  uint32_t id;
+  __device__ __forceinline__ void operator()() const { asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory"); }
+};
+
+template <class LV>
+struct Team {
+  static constexpr int WPT2 = odd_at_least(cdiv(LV::W_v32, 64));
+  static constexpr int U2W = round_up(cmax(cdiv(2 * LV::n, 32), 64 * WPT2 + (LV::n >> 5) + 1), 4);
+  static constexpr int RB = cdiv(LV::n1, 4) * 4;  // bytes per stored RM word
+  static constexpr int WORDS = round_up(U2W + LV::WP + 2 * (RB / 4), 4);  // shared words per team
+  static_assert(2 * RS_SCRATCH <= U2W, "two RS scratches fit in u2");
+  static_assert(U2W % 4 == 0 && LV::WP % 4 == 0 && WORDS % 4 == 0, "16-byte alignment");
+};
+
+// S1-S7 of one ciphertext by a team (tid in [0, 64)).
+template <class LV, bool MASKED>
+__device__ __forceinline__ void product_rm_team(uint32_t* ws, int tid, const TeamSync& sync,
+                                                const uint64_t* __restrict__ urow, const uint64_t* __restrict__ vrow,
+                                                const uint32_t* __restrict__ yrow, uint8_t* r_out) {
+  using T = Team<LV>;
+  constexpr int WPT = T::WPT2, W_v32 = LV::W_v32;
+  uint32_t* u2 = ws;
+  uint32_t* sup = ws + T::U2W;
+  load_supports<LV::n, LV::w, 64>(sup, yrow, tid);
+  build_doubled<LV::n, LV::W_u_pitch, T::U2W, 64>(u2, urow, tid, sync);
+  uint32_t acc[WPT];
+  rot_xor_product<WPT, LV::w, MASKED>(u2, sup, tid, acc);
+  const uint32_t* v32 = reinterpret_cast<const uint32_t*>(vrow);
+#pragma unroll
+  for (int k = 0; k < WPT; k++) {
+    const int i = tid * WPT + k;
+    if (i < W_v32) acc[k] ^= __ldcs(v32 + i);
+  }
+  sync();
+#pragma unroll
+  for (int k = 0; k < WPT; k++) {
+    const int i = tid * WPT + k;
+    if (i < W_v32) u2[i] = acc[k];
+  }
+  sync();
+  rm_decode_warp<LV, 32>(u2, r_out, tid);
+  sync();
+}
+
+// Two ciphertexts per turn: product and RM of each by the whole team, then
+// warp wt of the team runs the RS stage of ciphertext wt.
+template <class LV, bool MASKED, class Rows>
+__device__ __forceinline__ void decrypt_team(const GF& gf, uint32_t* ws, int wt, int lane, const TeamSync& sync,
+                                             const Rows& rows) {
+  using T = Team<LV>;
+  const int tid = (wt << 5) | lane;
+  uint8_t* rbuf = reinterpret_cast<uint8_t*>(ws + T::U2W + LV::WP);
+  const uint64_t* u;
+  const uint64_t* v;
+  const uint32_t* y;
+  uint8_t* m;
+#pragma unroll 1
+  for (int g = 0; g < 2; g++)
+    if (rows(g, u, v, y, m)) product_rm_team<LV, MASKED>(ws, tid, sync, u, v, y, rbuf + g * T::RB);
+  const bool act = rows(wt, u, v, y, m);
+  rs_decode_seg<LV, 32, false>(gf, ws + wt * RS_SCRATCH, rbuf + wt * T::RB, lane, act, m, nullptr);
+  sync();  // the RS scratch lives in u2: the next turn rebuilds it
 }
 
 }  // namespace hqc

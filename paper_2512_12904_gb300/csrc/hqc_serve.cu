@@ -52,6 +52,10 @@ struct Slot {
   int64_t first = 0, last = 0;       // requests [first, last)
 };
 
+// Batches of at most this many requests run as one mixed-kernel launch
+// (lowest latency); larger ones as one persistent kernel per level.
+constexpr int64_t kSmallBatch = 512;
+
 inline int64_t now_ns() {
   return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
       .count();
@@ -235,6 +239,25 @@ extern "C" int hqc_serve_run(const hqc_serve_cfg_t* cfg, const hqc_keyset_t* con
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(s.d_items, s.h_items, (size_t)nitems * sizeof(hqc::MixedItem), cudaMemcpyHostToDevice,
                             s.st);
+      if (nitems <= kSmallBatch && e == cudaSuccess) {
+        // a small batch: one launch of the mixed kernel on small blocks, so
+        // its items spread over many SMs and finish together
+        hqc::MixedArgs a;
+        a.count = nitems;
+        a.items = s.d_items;
+        a.arena = s.d_words;
+        a.arena_words = wbytes / 8;
+        for (int k = 0; k < 3; k++) {
+          a.keys[k] = keys[k] ? keys[k]->d_table : nullptr;
+          a.nkeys[k] = keys[k] ? keys[k]->nkeys : 0;
+        }
+        a.m = s.d_m;
+        a.m_bytes = mbytes;
+        hqc::LaunchCfg small;
+        small.warps_per_cta = 4;
+        e = hqc::launch_mixed(a, s.st, small);
+        for (auto& l : lists) l.clear();
+      }
       for (int li = 0; li < 3 && e == cudaSuccess; li++) {
         if (lists[li].empty()) continue;
         hqc::MixedArgs a;
