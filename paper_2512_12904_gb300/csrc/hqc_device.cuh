@@ -27,9 +27,13 @@ constexpr int GF_LOG_BYTES = 256 * 32 * 2;
 constexpr int GF_TABLE_BYTES = GF_EXP_BYTES + GF_LOG_BYTES;
 constexpr uint32_t GF_LOG_ZERO = 511;
 
+// c ? a : b as one predicated select (no branch).
 __device__ __forceinline__ uint32_t sel(bool c, uint32_t a, uint32_t b) {
-  uint32_t m = 0u - (uint32_t)c;
-  return (a & m) | (b & ~m);
+  uint32_t d;
+  asm("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %3, 0;\n\tselp.b32 %0, %1, %2, p;\n\t}"
+      : "=r"(d)
+      : "r"(a), "r"(b), "r"((uint32_t)c));
+  return d;
 }
 
 __device__ __forceinline__ uint32_t gf_xtime(uint32_t a) {
@@ -55,19 +59,17 @@ __device__ inline void gf_tables_init(uint8_t* smem, int tid, int nthreads) {
 }
 
 struct GF {
-  const uint8_t* ex;
-  const uint16_t* lg;
+  const uint8_t* ex;   // this lane's column: exp table + 4 * lane
+  const uint16_t* lg;  // this lane's column: log table + 2 * lane (halfwords)
   uint32_t lane;
   __device__ __forceinline__ GF(const uint8_t* smem, uint32_t lane_)
-      : ex(smem), lg(reinterpret_cast<const uint16_t*>(smem + GF_EXP_BYTES)), lane(lane_) {}
-  // e in [0, 511]
-  __device__ __forceinline__ uint32_t exp(uint32_t e) const {
-    return ex[((e & ~3u) << 5) + (lane << 2) + (e & 3u)];
-  }
-  // a in [0, 255]
-  __device__ __forceinline__ uint32_t log(uint32_t a) const {
-    return lg[((a & ~1u) << 5) + (lane << 1) + (a & 1u)];
-  }
+      : ex(smem + 4 * lane_), lg(reinterpret_cast<const uint16_t*>(smem + GF_EXP_BYTES) + 2 * lane_), lane(lane_) {}
+  // e in [0, 511].  Entry e sits at byte ((e & ~3) << 5) + (e & 3) of the
+  // lane's column, i.e. 32 e - 31 (e & 3): written as multiplies so the
+  // address arithmetic can run on the multiply-add pipe.
+  __device__ __forceinline__ uint32_t exp(uint32_t e) const { return ex[e * 32u - (e & 3u) * 31u]; }
+  // a in [0, 255]: halfword 32 a - 31 (a & 1) of the lane's column
+  __device__ __forceinline__ uint32_t log(uint32_t a) const { return lg[a * 32u - (a & 1u) * 31u]; }
   // product of two elements given by their logs (511 = zero)
   __device__ __forceinline__ uint32_t mul_l(uint32_t la, uint32_t lb) const {
     return exp(min(la + lb, GF_LOG_ZERO));
@@ -373,7 +375,9 @@ struct RSDebugRow {
   int32_t* flag;     // 1
 };
 
-constexpr int RS_SCRATCH = 144;  // words: log r (96 halfwords), log S, log Lambda, log Omega (64 halfwords each)
+// words: log r (96 halfwords), log S behind 64 halfwords of log-zero padding
+// (128), log Lambda and log Omega (64 halfwords each)
+constexpr int RS_SCRATCH = 176;
 
 template <class LV, int SEG, bool ALL_POS>
 __device__ __forceinline__ void rs_decode_seg(const GF& gf, uint32_t* rs, const uint8_t* r, int lane, bool active,
@@ -382,11 +386,14 @@ __device__ __forceinline__ void rs_decode_seg(const GF& gf, uint32_t* rs, const 
   static_assert(n1 <= 96 && CAP <= 64, "RS scratch sizes");
   const int sl = lane % SEG;
   uint16_t* logr = reinterpret_cast<uint16_t*>(rs);
-  uint16_t* logS = reinterpret_cast<uint16_t*>(rs + 48);
-  uint16_t* logLam = reinterpret_cast<uint16_t*>(rs + 80);
-  uint16_t* logOm = reinterpret_cast<uint16_t*>(rs + 112);
+  // logS[i] for i in [-64, 64): negative indices read log 0, so terms of
+  // Lambda_c S_{r+1-c} with c > r vanish without a select
+  uint16_t* logS = reinterpret_cast<uint16_t*>(rs + 48) + 64;
+  uint16_t* logLam = reinterpret_cast<uint16_t*>(rs + 112);
+  uint16_t* logOm = reinterpret_cast<uint16_t*>(rs + 144);
 
   for (int j = sl; j < n1; j += SEG) logr[j] = (uint16_t)gf.log(r[j]);
+  for (int j = sl; j < 64; j += SEG) logS[j - 64] = (uint16_t)GF_LOG_ZERO;
   __syncwarp();
 
   // syndromes: lane owns i = sl + 1 + SEG s
@@ -423,10 +430,8 @@ __device__ __forceinline__ void rs_decode_seg(const GF& gf, uint32_t* rs, const 
     uint32_t part = 0;
 #pragma unroll
     for (int x = 0; x < NC; x++) {
-      const int c = sl + SEG * x;
-      const bool in = c <= rr;
-      const uint32_t ls = logS[in ? rr - c : 0];
-      part ^= sel(in, gf.mul_l(gf.log(lam[x]), ls), 0u);
+      const int c = sl + SEG * x;  // rr - c >= -64: padding covers c > rr
+      part ^= gf.mul_l(gf.log(lam[x]), logS[rr - c]);
     }
 #pragma unroll
     for (int o = SEG / 2; o > 0; o >>= 1) part ^= __shfl_xor_sync(FULL_MASK, part, o, SEG);
@@ -469,9 +474,8 @@ __device__ __forceinline__ void rs_decode_seg(const GF& gf, uint32_t* rs, const 
     uint32_t om = 0;
 #pragma unroll 4
     for (int c = 0; c < NR; c++) {
-      const bool in = c <= kk;
-      const uint32_t t = gf.mul_l(logLam[c], logS[in && kk < NR ? kk - c : 0]);
-      om ^= sel(in, t, 0u);
+      const int idx = kk < NR ? kk - c : -1;  // c > kk reads the log-zero padding
+      om ^= gf.mul_l(logLam[c], logS[idx]);
     }
     if (kk < NR) logOm[kk] = (uint16_t)gf.log(om);
   }
