@@ -129,15 +129,19 @@ __device__ __forceinline__ void build_doubled(uint32_t* u2, const uint64_t* __re
   sync();
 }
 
-// Support entry p -> packed word: q0 = n - p (so the rotation by p reads
-// u2 from bit 32 i + q0), bit 31 = "p < n".  An entry p >= n packs to 0 and
-// its contribution is masked off.
+// Support entry p -> two words: with q0 = n - p the rotation by p reads u2
+// from bit 32 i + q0, i.e. word i + (q0 >> 5) at shift q0 & 31.  Stored as
+// sup[2t] = 4 (q0 >> 5) (a byte offset) and sup[2t+1] = (q0 & 31) | (p < n)
+// << 31; an entry p >= n stores offset 0 and no flag, and its contribution
+// is masked off.  (Funnel shifts use the shift modulo 32, so the flag bit
+// can stay in place.)
 template <int N, int W, int NT = 32>
 __device__ __forceinline__ void load_supports(uint32_t* sup, const uint32_t* __restrict__ yrow, int tid) {
   for (int t = tid; t < W; t += NT) {
     const uint32_t p = __ldg(yrow + t);
+    const bool ok = p < (uint32_t)N;
     const uint32_t q0 = (uint32_t)N - p;
-    sup[t] = sel(p < (uint32_t)N, q0 | 0x80000000u, 0u);
+    *reinterpret_cast<uint2*>(sup + 2 * t) = make_uint2(sel(ok, (q0 >> 5) << 2, 0u), sel(ok, (q0 & 31u) | 0x80000000u, 0u));
   }
 }
 
@@ -155,19 +159,18 @@ __device__ __forceinline__ void rot_xor_product(const uint32_t* u2, const uint32
                                                 uint32_t (&acc)[WPT]) {
 #pragma unroll
   for (int k = 0; k < WPT; k++) acc[k] = 0;
-  const uint32_t* base = u2 + lane * WPT;
+  const char* base = reinterpret_cast<const char*>(u2 + lane * WPT);
   if (MASKED) {
 #pragma unroll 1
     for (int t = 0; t < W; t++) {
-      const uint32_t e = sup[t];
-      const uint32_t s = e & 31u;
-      const uint32_t msk = (uint32_t)((int32_t)e >> 31);
-      const uint32_t* src = base + ((e & 0x7FFFFFFFu) >> 5);
+      const uint2 e = *reinterpret_cast<const uint2*>(sup + 2 * t);
+      const uint32_t msk = (uint32_t)((int32_t)e.y >> 31);
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(base + e.x);
       uint32_t lo = src[0];
 #pragma unroll
       for (int k = 0; k < WPT; k++) {
         const uint32_t hi = src[k + 1];
-        acc[k] ^= __funnelshift_r(lo, hi, s) & msk;
+        acc[k] ^= __funnelshift_r(lo, hi, e.y) & msk;
         lo = hi;
       }
     }
@@ -176,28 +179,26 @@ __device__ __forceinline__ void rot_xor_product(const uint32_t* u2, const uint32
     // is a single three-input XOR
 #pragma unroll 1
     for (int t = 0; t + 1 < W; t += 2) {
-      const uint2 e = *reinterpret_cast<const uint2*>(sup + t);
-      const uint32_t s0 = e.x & 31u, s1 = e.y & 31u;
-      const uint32_t* a0 = base + ((e.x & 0x7FFFFFFFu) >> 5);
-      const uint32_t* a1 = base + ((e.y & 0x7FFFFFFFu) >> 5);
+      const uint4 e = *reinterpret_cast<const uint4*>(sup + 2 * t);
+      const uint32_t* a0 = reinterpret_cast<const uint32_t*>(base + e.x);
+      const uint32_t* a1 = reinterpret_cast<const uint32_t*>(base + e.z);
       uint32_t lo0 = a0[0], lo1 = a1[0];
 #pragma unroll
       for (int k = 0; k < WPT; k++) {
         const uint32_t hi0 = a0[k + 1], hi1 = a1[k + 1];
-        acc[k] ^= __funnelshift_r(lo0, hi0, s0) ^ __funnelshift_r(lo1, hi1, s1);
+        acc[k] ^= __funnelshift_r(lo0, hi0, e.y) ^ __funnelshift_r(lo1, hi1, e.w);
         lo0 = hi0;
         lo1 = hi1;
       }
     }
     if (W & 1) {
-      const uint32_t e = sup[W - 1];
-      const uint32_t s = e & 31u;
-      const uint32_t* src = base + ((e & 0x7FFFFFFFu) >> 5);
+      const uint2 e = *reinterpret_cast<const uint2*>(sup + 2 * (W - 1));
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(base + e.x);
       uint32_t lo = src[0];
 #pragma unroll
       for (int k = 0; k < WPT; k++) {
         const uint32_t hi = src[k + 1];
-        acc[k] ^= __funnelshift_r(lo, hi, s);
+        acc[k] ^= __funnelshift_r(lo, hi, e.y);
         lo = hi;
       }
     }

@@ -34,7 +34,8 @@ __host__ __device__ constexpr int round_up(int a, int b) { return cdiv(a, b) * b
 // Layout in shared memory for one ciphertext (32-bit words):
 //   u2[U2W]   the 2n-bit string u||u (second copy starts at bit n) so a
 //             rotation by p is the 32-bit window at bit offset 32 i + n - p;
-//   sup[WP]   one packed word per support entry (see pack_support).
+//   sup[WP]   two words per support entry: the byte offset of the
+//             window's first u2 word and the bit shift (see load_supports).
 // After the product the w = v + u*y words overwrite u2[0, W_v32); once the
 // RM bytes are out, u2 is scratch for the Reed-Solomon stage.
 template <int LEVEL> struct Level : LevelConst<LEVEL> {
@@ -53,12 +54,12 @@ template <int LEVEL> struct Level : LevelConst<LEVEL> {
   static constexpr int WPT = odd_at_least(cdiv(W_v32, 32));
   // highest u2 word a lane may read: 32*WPT - 1 + (n >> 5) + 1
   static constexpr int U2W = round_up(cmax(cdiv(2 * C::n, 32), 32 * WPT + (C::n >> 5) + 1), 4);
-  static constexpr int WP = round_up(C::w, 4);
+  static constexpr int WP = round_up(2 * C::w, 4);    // two words per support entry
   static constexpr int WARP_WORDS = U2W + WP;       // u2 and the support list
   // full-length (n-bit) product used by key generation and encryption
   static constexpr int WPT_FULL = odd_at_least(cdiv(N32, 32));
   static constexpr int U2W_FULL = round_up(cmax(cdiv(2 * C::n, 32), 32 * WPT_FULL + (C::n >> 5) + 1), 4);
-  static constexpr int WP_R = round_up(C::wr, 4);
+  static constexpr int WP_R = round_up(2 * C::wr, 4);
   static_assert(C::n1 * n2 % 64 == 0, "v is a whole number of words");
   static_assert(C::n1 - C::k == NR, "RS code has n1 - k = 2 delta");
   static_assert(C::k <= 32, "one message byte per lane");
