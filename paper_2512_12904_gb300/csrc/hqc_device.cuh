@@ -299,21 +299,23 @@ __device__ __forceinline__ uint32_t rm_decode_pair(const uint32_t* blk, uint32_t
       }
     }
   }
-  // index bit 6: lane 0 keeps x + y, lane 1 keeps x - y (x = lane 0's value)
+  // index bit 6: lane 0 keeps x + y, lane 1 keeps y - x (x = own value,
+  // y = partner's): own * (+-1) + y + (-+bias), one multiply-add
+  const uint32_t sgn = hb ? 0xFFFFFFFFu : 1u;
+  const uint32_t cst = hb ? BP : (0u - BP);
 #pragma unroll
   for (int r = 0; r < 32; r++) {
     const uint32_t Y = __shfl_xor_sync(FULL_MASK, R[r], 1);
-    R[r] = hb ? (Y - R[r] + BP) : (R[r] + Y - BP);
+    R[r] = R[r] * sgn + (Y + cst);
   }
   uint32_t mp[4] = {0, 0, 0, 0}, mn[4] = {0, 0, 0, 0};
   const uint32_t cbase = (63u - 32u * hb) * 0x10001u;
 #pragma unroll
   for (int r = 0; r < 32; r++) {
-    // index bit 4: low half -> lo + hi, high half -> lo - hi
+    // index bit 4: low half -> lo + hi - bias, high half -> lo - hi + bias,
+    // as lo * 0x10001 + hi * (1 - 2^16) + bias * (2^16 - 1) (mod 2^32)
     const uint32_t X = R[r];
-    const uint32_t Xs = __byte_perm(X, 0, 0x1032);
-    const uint32_t A = X + Xs - BP, D = Xs - X + BP;
-    const uint32_t P = __byte_perm(A, D, 0x7610);
+    const uint32_t P = (X & 0xFFFFu) * 0x10001u + (X >> 16) * 0xFFFF0001u + (BIAS * 0xFFFFu);
     const uint32_t C = cbase - (uint32_t)r * 0x10001u;
     mp[r & 3] = vmax_u16x2(mp[r & 3], P * 32u + C);
     mn[r & 3] = vmax_u16x2(mn[r & 3], (KN + C) - P * 32u);
