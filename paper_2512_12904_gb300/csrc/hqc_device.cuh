@@ -228,6 +228,11 @@ __device__ __forceinline__ uint32_t vmax_u16x2(uint32_t a, uint32_t b) {
   return d;
 }
 
+// max of three pairs of unsigned 16-bit halves
+__device__ __forceinline__ uint32_t vmax3_u16x2(uint32_t a, uint32_t b, uint32_t c) {
+  return __vimax3_u16x2(a, b, c);
+}
+
 template <int MULT>
 __device__ __forceinline__ uint32_t rm_decode_pair(const uint32_t* blk, uint32_t hb) {
   constexpr uint32_t BIAS = 640u;
@@ -311,17 +316,24 @@ __device__ __forceinline__ uint32_t rm_decode_pair(const uint32_t* blk, uint32_t
   uint32_t mp[4] = {0, 0, 0, 0}, mn[4] = {0, 0, 0, 0};
   const uint32_t cbase = (63u - 32u * hb) * 0x10001u;
 #pragma unroll
-  for (int r = 0; r < 32; r++) {
+  for (int r = 0; r < 32; r += 2) {
     // index bit 4: low half -> lo + hi - bias, high half -> lo - hi + bias,
     // as lo * 0x10001 + hi * (1 - 2^16) + bias * (2^16 - 1) (mod 2^32)
-    const uint32_t X = R[r];
-    const uint32_t P = (X & 0xFFFFu) * 0x10001u + (X >> 16) * 0xFFFF0001u + (BIAS * 0xFFFFu);
-    const uint32_t C = cbase - (uint32_t)r * 0x10001u;
-    mp[r & 3] = vmax_u16x2(mp[r & 3], P * 32u + C);
-    mn[r & 3] = vmax_u16x2(mn[r & 3], (KN + C) - P * 32u);
+    uint32_t kp[2], kn[2];
+#pragma unroll
+    for (int d = 0; d < 2; d++) {
+      const uint32_t X = R[r + d];
+      const uint32_t P = (X & 0xFFFFu) * 0x10001u + (X >> 16) * 0xFFFF0001u + (BIAS * 0xFFFFu);
+      const uint32_t C = cbase - (uint32_t)(r + d) * 0x10001u;
+      kp[d] = P * 32u + C;
+      kn[d] = (KN + C) - P * 32u;
+    }
+    const int a = (r >> 1) & 3;
+    mp[a] = vmax3_u16x2(mp[a], kp[0], kp[1]);
+    mn[a] = vmax3_u16x2(mn[a], kn[0], kn[1]);
   }
-  uint32_t MP = vmax_u16x2(vmax_u16x2(mp[0], mp[1]), vmax_u16x2(mp[2], mp[3]));
-  uint32_t MN = vmax_u16x2(vmax_u16x2(mn[0], mn[1]), vmax_u16x2(mn[2], mn[3]));
+  uint32_t MP = vmax3_u16x2(mp[0], mp[1], vmax_u16x2(mp[2], mp[3]));
+  uint32_t MN = vmax3_u16x2(mn[0], mn[1], vmax_u16x2(mn[2], mn[3]));
   MP = vmax_u16x2(MP, __shfl_xor_sync(FULL_MASK, MP, 1));
   MN = vmax_u16x2(MN, __shfl_xor_sync(FULL_MASK, MN, 1));
   uint32_t best = 0;
