@@ -132,6 +132,23 @@ int hqc_decrypt_batch_staged_noalloc(int level, int64_t count, const uint64_t* u
                                      const uint32_t* y, const hqc_keyset_t* keys, const int32_t* key_idx,
                                      uint8_t* m_out, void* stream);
 
+/* Decryption straight from host buffers, with uploads overlapped with the
+ * kernels: the batch is cut into chunks of `chunk` ciphertexts that
+ * alternate between two device slots in `workspace` (device memory of at
+ * least hqc_host_workspace_bytes(level, chunk) bytes), uploaded on an
+ * internal copy stream while the previous chunk is decrypted and its m
+ * copied back on an internal compute stream (both created once per
+ * device).  chunk <= 0 picks whole waves of the persistent grid, about
+ * eight chunks per batch, as large as the workspace holds.  u_host, v_host,
+ * key_idx_host and m_host are HOST memory and should be pinned for the
+ * copies to overlap.  The call is ordered after
+ * earlier work on `stream`, and `stream` waits for its completion; m_host is
+ * valid once `stream` reaches that point. */
+size_t hqc_host_workspace_bytes(int level, int64_t chunk);
+int hqc_decrypt_host_keyed(int level, int64_t count, const uint64_t* u_host, const uint64_t* v_host,
+                           const hqc_keyset_t* keys, const int32_t* key_idx_host, uint8_t* m_host, int64_t chunk,
+                           void* workspace, size_t workspace_bytes, void* stream);
+
 /* Every intermediate of Algorithm 2, per ciphertext (device arrays):
  *   t    [count][W_v]  u*y truncated to n1*n2 bits
  *   w    [count][W_v]  v + t

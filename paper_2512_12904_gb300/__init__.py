@@ -23,7 +23,7 @@ __all__ = [
     "hqc_decrypt_batch_staged", "hqc_decrypt_batch_staged_noalloc", "hqc_decrypt_debug", "hqc_mixed_workspace_bytes",
     "hqc_decrypt_mixed", "hqc_set_launch_config", "hqc_get_launch_shape", "hqc_keygen_batch",
     "hqc_encrypt_batch", "LEVELS", "Plan", "hqc_plan_create_keyed", "hqc_plan_create_mixed", "hqc_serve_run",
-    "SERVE_STATUS",
+    "SERVE_STATUS", "hqc_decrypt_host_keyed", "hqc_host_workspace_bytes",
 ]
 
 LEVELS = (1, 3, 5)
@@ -89,6 +89,8 @@ def load(build_if_missing: bool = True):
             "hqc_plan_info": (i32, [P, P, P, P, P]),
             "hqc_plan_destroy": (i32, [P]),
             "hqc_serve_run": (i32, [P, P, P, i64, P, P, P, P, P]),
+            "hqc_host_workspace_bytes": (sz, [i32, i64]),
+            "hqc_decrypt_host_keyed": (i32, [i32, i64, P, P, P, P, P, i64, P, sz, P]),
             "hqc_keygen_batch": (i32, [i32, i64, P, P, P, P, P]),
             "hqc_encrypt_batch": (i32, [i32, i64, P, P, i64, P, P, P, P, P, P, P, P]),
         }
@@ -510,3 +512,41 @@ def hqc_serve_run(keys, ring_level, ring_key, ring_word_off, ring_words, ring_m_
                                 m_out.ctypes.data_as(ctypes.c_void_p) if want_m else None, ctypes.byref(st)))
     stats = {f: getattr(st, f) for f, _ in _ServeStats._fields_}
     return status, lat, m_out, stats
+
+
+def hqc_host_workspace_bytes(level: int, chunk: int) -> int:
+    return int(load().hqc_host_workspace_bytes(level, chunk))
+
+
+def hqc_decrypt_host_keyed(level, u_host, v_host, keys: Keyset, key_idx_host, m_host=None, chunk=0,
+                           workspace=None, stream=None):
+    """Decrypt from (pinned) HOST tensors with chunked copy/compute overlap.
+
+    u_host [count][W_u_pitch] int64, v_host [count][W_v] int64, key_idx_host
+    [count] int32, m_host [count][k] uint8 (CPU tensors); workspace: a CUDA
+    uint8 tensor of at least hqc_host_workspace_bytes(level, chunk) bytes
+    (allocated here when None; chunk 0 lets the library choose, bounded by
+    the workspace).  Returns m_host (valid once the stream reaches the end
+    of the call)."""
+    torch = _torch()
+    P = hqc_get_params(level)
+    u_host, v_host = _as_u64(u_host), _as_u64(v_host)
+    cnt = u_host.shape[0]
+    for t, name in ((u_host, "u_host"), (v_host, "v_host"), (key_idx_host, "key_idx_host")):
+        if t.is_cuda or not t.is_contiguous():
+            raise ValueError("%s must be a contiguous CPU tensor" % name)
+    if tuple(u_host.shape) != (cnt, P.W_u_pitch) or tuple(v_host.shape) != (cnt, P.W_v):
+        raise ValueError("u_host / v_host shapes")
+    if key_idx_host.dtype != torch.int32 or tuple(key_idx_host.shape) != (cnt,):
+        raise ValueError("key_idx_host must be int32 [count]")
+    if m_host is None:
+        m_host = torch.empty((cnt, P.k), dtype=torch.uint8).pin_memory()
+    if workspace is None:
+        workspace = torch.empty(hqc_host_workspace_bytes(level, chunk if chunk > 0 else max(1, min(cnt, 16384))),
+                                dtype=torch.uint8, device="cuda")
+    _check(load().hqc_decrypt_host_keyed(level, cnt, ctypes.c_void_p(u_host.data_ptr()),
+                                         ctypes.c_void_p(v_host.data_ptr()), keys.handle,
+                                         ctypes.c_void_p(key_idx_host.data_ptr()), ctypes.c_void_p(m_host.data_ptr()),
+                                         int(chunk), _dev_ptr(workspace, torch.uint8, None, "workspace"),
+                                         workspace.numel(), _stream(stream)))
+    return m_host

@@ -80,6 +80,10 @@ int launch_result(cudaError_t e, const char* what) { return e == cudaSuccess ? H
 
 void hqc::set_last_error(const char* msg) { g_err = msg; }
 
+namespace hqc {
+LaunchCfg level_cfg(int level) { return level_index(level) < 0 ? LaunchCfg{} : g_cfg[level_index(level) + 1]; }
+}  // namespace hqc
+
 extern "C" {
 
 int hqc_get_params(int level, hqc_params_t* out) {

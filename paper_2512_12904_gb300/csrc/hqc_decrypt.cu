@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "hqc_device.cuh"
 #include "hqc_internal.h"
@@ -406,6 +407,22 @@ cudaError_t launch_fused(int level, bool keyed, const DecArgs& a, cudaStream_t s
     case 5: return keyed ? fused_level<5, true>(a, st, cfg, true, 0, 0, 0) : fused_level<5, false>(a, st, cfg, true, 0, 0, 0);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t fused_wave(int level, bool keyed, const LaunchCfg& cfg, int64_t* items) {
+  int w = 0, c = 0, g = 0;
+  cudaError_t e = fused_occupancy(level, keyed, cfg, &w, &c, &g);
+  if (e != cudaSuccess) return e;
+  // ciphertexts per two warps: one for a team, 2G for single-warp groups
+  auto per2 = [](auto lv) {
+    constexpr int L = decltype(lv)::value;
+    return UseTeam<L>::value ? 1 : 2 * FusedGroup<L>::G;
+  };
+  const int64_t per_two = level == 1   ? per2(std::integral_constant<int, 1>{})
+                          : level == 3 ? per2(std::integral_constant<int, 3>{})
+                                       : per2(std::integral_constant<int, 5>{});
+  *items = (int64_t)g * w * per_two / 2;
+  return cudaSuccess;
 }
 
 cudaError_t fused_occupancy(int level, bool keyed, const LaunchCfg& cfg, int* warps, int* ctas, int* grid) {

@@ -74,6 +74,10 @@ cudaError_t launch_staged(int level, bool keyed, const DecArgs& a, uint64_t* w_w
 cudaError_t launch_debug(int level, const DecArgs& a, const DebugArgs& d, cudaStream_t st);
 cudaError_t launch_mixed(const MixedArgs& a, cudaStream_t st, const LaunchCfg& cfg);
 cudaError_t fused_occupancy(int level, bool keyed, const LaunchCfg& cfg, int* warps, int* ctas_per_sm, int* grid);
+// Ciphertexts one full wave of the persistent fused grid decrypts at once.
+cudaError_t fused_wave(int level, bool keyed, const LaunchCfg& cfg, int64_t* items);
+// The launch shape hqc_set_launch_config chose for a level (1, 3, 5).
+LaunchCfg level_cfg(int level);
 // One level's items of a mixed list (a.items all of that level), at most
 // `grid` blocks (0 = a full persistent grid).
 cudaError_t launch_items(int level, const MixedArgs& a, int grid, cudaStream_t st, const LaunchCfg& cfg);

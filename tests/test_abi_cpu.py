@@ -88,3 +88,20 @@ def test_workspace_sizes(level):
 
 def test_item_record_layout():
     assert hqc.ITEM_DTYPE.itemsize == 32
+
+
+@pytest.mark.parametrize("level", [1, 3, 5])
+def test_host_pipeline_workspace_and_argument_checks(level):
+    lib = hqc.load()
+    p = hqc.hqc_get_params(level)
+    for chunk in (1, 5, 8192):
+        b = hqc.hqc_host_workspace_bytes(level, chunk)
+        assert b >= 2 * chunk * ((p.W_u_pitch + p.W_v) * 8 + 4 + p.k) and b % 16 == 0
+    assert hqc.hqc_host_workspace_bytes(level, 0) == 0
+    assert hqc.hqc_host_workspace_bytes(2, 16) == 0
+    N = None
+    assert lib.hqc_decrypt_host_keyed(2, 1, N, N, N, N, N, 16, N, 0, N) == -1
+    assert lib.hqc_decrypt_host_keyed(level, -1, N, N, N, N, N, 16, N, 0, N) == -1
+    assert lib.hqc_decrypt_host_keyed(level, 0, N, N, N, N, N, 16, N, 0, N) == 0
+    assert lib.hqc_decrypt_host_keyed(level, 3, N, N, N, N, N, 16, N, 0, N) == -1
+    assert b"NULL" in lib.hqc_last_error()

@@ -262,3 +262,26 @@ def test_keyed_plan_graph_replay(hqc, level):
     assert plan.info()["tuned_ms"] > 0
     plan.destroy()
     keys.free()
+
+
+@pytest.mark.parametrize("level", LEVELS)
+def test_host_pipelined_matches_oracle(hqc, level):
+    """Chunked host-buffer decryption: ragged last chunk, one-item chunks,
+    a single chunk larger than the batch, the empty batch and a short
+    workspace."""
+    wl = honest(level, 5, 75, first_ct=9000, tag=8)
+    keys = hqc.Keyset(level, wl.y)
+    u_h = torch.from_numpy(wl.u.view(np.int64).copy()).pin_memory()
+    v_h = torch.from_numpy(wl.v.view(np.int64).copy()).pin_memory()
+    k_h = torch.from_numpy(wl.key_idx.astype(np.int32)).pin_memory()
+    for chunk in (1, 16, 32, 200):
+        ws = torch.empty(hqc.hqc_host_workspace_bytes(level, chunk), dtype=torch.uint8, device="cuda")
+        m_h = hqc.hqc_decrypt_host_keyed(level, u_h, v_h, keys, k_h, chunk=chunk, workspace=ws)
+        torch.cuda.current_stream().synchronize()
+        assert (m_h.numpy() == wl.m).all(), chunk
+    m0 = hqc.hqc_decrypt_host_keyed(level, u_h[:0], v_h[:0], keys, k_h[:0], chunk=8, workspace=ws)
+    assert m0.shape == (0, wl.P.k)
+    short = torch.empty(hqc.hqc_host_workspace_bytes(level, 64) - 16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(hqc.HqcError):
+        hqc.hqc_decrypt_host_keyed(level, u_h, v_h, keys, k_h, chunk=64, workspace=short)
+    keys.free()
