@@ -19,6 +19,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "hqc_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "kem_oracle.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libhqc_oracle.so")
 _lock = threading.Lock()
@@ -31,11 +32,10 @@ def build(force: bool = False) -> str:
     """Compile the oracle into ``oracle/_build/libhqc_oracle.so``."""
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(f) for f in _SRCS)):
         return _LIB_PATH
     tmp = _LIB_PATH + ".tmp%d" % os.getpid()
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread",
-                           _SRC, "-o", tmp])
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread"] + _SRCS + ["-o", tmp])
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -64,6 +64,14 @@ def _load():
                 "oracle_decrypt_batch": (ctypes.c_int, [ctypes.c_int, i64, P, P, P, P, ctypes.c_int]),
                 "oracle_decrypt_dump": (ctypes.c_int, [ctypes.c_int] + [P] * 14),
                 "oracle_concat_encode": (ctypes.c_int, [ctypes.c_int, P, P]),
+                "oracle_keccak_f1600": (None, [P]),
+                "oracle_shake256": (None, [P, i64, P, i64]),
+                "oracle_fixed_weight": (None, [ctypes.c_int, ctypes.c_int, P, P]),
+                "oracle_kem_theta": (None, [ctypes.c_int, P, P, P]),
+                "oracle_kem_randomness": (ctypes.c_int, [ctypes.c_int, P, P, P, P]),
+                "oracle_kem_keygen": (ctypes.c_int, [ctypes.c_int, i64, P, P, P, P, P, P]),
+                "oracle_kem_encaps": (ctypes.c_int, [ctypes.c_int, i64, P, P, P, P, P, P, P, P]),
+                "oracle_kem_decaps": (ctypes.c_int, [ctypes.c_int, i64, P, P, P, P, P, P, P, P, P, P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -286,3 +294,97 @@ def concat_encode(level: int, m: np.ndarray) -> np.ndarray:
     out = np.zeros(P.W_v, np.uint64)
     assert _load().oracle_concat_encode(level, _p(m), _p(out)) == 0
     return out
+
+
+# --------------------------------------------------------------------------
+# SHAKE256, fixed-weight sampling and the KEM (kem_oracle.c, readings A16-A22)
+# --------------------------------------------------------------------------
+def keccak_f1600(state: bytes) -> bytes:
+    """Keccak-f[1600] on a 200-byte state (FIPS 202 Sec. 3)."""
+    st = np.frombuffer(bytes(state), np.uint8).copy()
+    assert st.size == 200
+    _load().oracle_keccak_f1600(_p(st))
+    return st.tobytes()
+
+
+def shake256(msg: bytes, outlen: int) -> bytes:
+    """SHAKE256 (FIPS 202 Sec. 6.2, reading A16)."""
+    m = np.frombuffer(bytes(msg) + b"\0", np.uint8).copy()
+    out = np.zeros(max(outlen, 1), np.uint8)
+    _load().oracle_shake256(_p(m), len(msg), _p(out), outlen)
+    return out[:outlen].tobytes()
+
+
+def fixed_weight(n: int, w: int, R) -> np.ndarray:
+    """Floyd / Sendrier constant-weight sampler on 32-bit draws (A17)."""
+    R = np.ascontiguousarray(R, np.uint32)
+    assert R.size == w
+    pos = np.zeros(w, np.uint32)
+    _load().oracle_fixed_weight(n, w, _p(R), _p(pos))
+    return pos
+
+
+def kem_theta(level: int, m: bytes, salt: bytes) -> bytes:
+    """theta = G(m, salt) (A19)."""
+    P = params(level)
+    mm = np.frombuffer(bytes(m), np.uint8).copy()
+    ss = np.frombuffer(bytes(salt), np.uint8).copy()
+    assert mm.size == P.k and ss.size == 16
+    th = np.zeros(32, np.uint8)
+    _load().oracle_kem_theta(P.k, _p(mm), _p(ss), _p(th))
+    return th.tobytes()
+
+
+def kem_randomness(level: int, theta: bytes):
+    """(r1, r2, e) supports drawn from theta (A17, A18)."""
+    P = params(level)
+    th = np.frombuffer(bytes(theta), np.uint8).copy()
+    r1 = np.zeros(P.wr, np.uint32)
+    r2 = np.zeros(P.wr, np.uint32)
+    e = np.zeros(P.we, np.uint32)
+    assert _load().oracle_kem_randomness(level, _p(th), _p(r1), _p(r2), _p(e)) == 0
+    return r1, r2, e
+
+
+def kem_keygen(level: int, seed_sk: np.ndarray, seed_pk: np.ndarray):
+    """(h, x, y, s) from 32-byte seeds [nkeys][32] (A22, Algorithm 3)."""
+    P = params(level)
+    seed_sk = np.ascontiguousarray(seed_sk, np.uint8)
+    seed_pk = np.ascontiguousarray(seed_pk, np.uint8)
+    nk = seed_sk.shape[0]
+    h = np.zeros((nk, P.W_u_pitch), np.uint64)
+    s = np.zeros((nk, P.W_u_pitch), np.uint64)
+    x = np.zeros((nk, P.w), np.uint32)
+    y = np.zeros((nk, P.w), np.uint32)
+    assert _load().oracle_kem_keygen(level, nk, _p(seed_sk), _p(seed_pk), _p(h), _p(x), _p(y), _p(s)) == 0
+    return h, x, y, s
+
+
+def kem_encaps(level: int, h, s, key_idx, m, salt):
+    """(u, v, K) per item (A18-A20, Algorithm 1)."""
+    P = params(level)
+    key_idx = np.ascontiguousarray(key_idx, np.int32)
+    m = np.ascontiguousarray(m, np.uint8)
+    salt = np.ascontiguousarray(salt, np.uint8)
+    cnt = key_idx.size
+    u = np.zeros((cnt, P.W_u_pitch), np.uint64)
+    v = np.zeros((cnt, P.W_v), np.uint64)
+    K = np.zeros((cnt, 32), np.uint8)
+    assert _load().oracle_kem_encaps(level, cnt, _p(np.ascontiguousarray(h, np.uint64)),
+                                     _p(np.ascontiguousarray(s, np.uint64)), _p(key_idx), _p(m), _p(salt),
+                                     _p(u), _p(v), _p(K)) == 0
+    return u, v, K
+
+
+def kem_decaps(level: int, h, s, y, sigma, key_idx, u, v, salt):
+    """(K, ok) per item: decrypt, re-encrypt, compare, implicit rejection (A21)."""
+    P = params(level)
+    key_idx = np.ascontiguousarray(key_idx, np.int32)
+    cnt = key_idx.size
+    K = np.zeros((cnt, 32), np.uint8)
+    ok = np.zeros(cnt, np.int32)
+    args = [np.ascontiguousarray(h, np.uint64), np.ascontiguousarray(s, np.uint64), np.ascontiguousarray(y, np.uint32),
+            np.ascontiguousarray(sigma, np.uint8), key_idx, np.ascontiguousarray(u, np.uint64),
+            np.ascontiguousarray(v, np.uint64), np.ascontiguousarray(salt, np.uint8)]
+    assert _load().oracle_kem_decaps(level, cnt, *[_p(a) for a in args], _p(K), _p(ok)) == 0
+    return K, ok.astype(bool)
