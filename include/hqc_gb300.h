@@ -149,6 +149,57 @@ int hqc_decrypt_host_keyed(int level, int64_t count, const uint64_t* u_host, con
                            const hqc_keyset_t* keys, const int32_t* key_idx_host, uint8_t* m_host, int64_t chunk,
                            void* workspace, size_t workspace_bytes, void* stream);
 
+/* ---------------------------------------------------------------------
+ * KEM (Sec. II-B: SHAKE-based sampling, domain-separated G and K, the HHK
+ * transform with implicit rejection; Algorithms 1-3).  The paper names
+ * these functions but not their inputs; this library's reading:
+ *   theta   = SHAKE256(m || salt || 0x03)[0:32]          (G)
+ *   r1 r2 e = 32-bit little-endian words of SHAKE256(theta || 0x01), in
+ *             that order, each support through the sampler below
+ *   K       = SHAKE256(x || U || V || salt || 0x04)[0:32], x = m, or sigma
+ *             when decapsulation rejects; U = ceil(n/8) bytes of u with bits
+ *             >= n cleared, V = n1 n2 / 8 bytes of v
+ *   h       = first n bits of SHAKE256(seed_pk || 0x02); x then y from the
+ *             words of SHAKE256(seed_sk || 0x01) through the sampler
+ * Sampler on draws R_i: pos_i = i + floor(R_i (n - i) / 2^32), then for
+ * i = w-2 down to 0, pos_i = i if it already occurs among pos_{i+1..w-1}.
+ * salt: 16 bytes per ciphertext.  All buffers are device memory, rows
+ * contiguous; m, salt, sigma, K, seeds 8-byte aligned; u, v, h, s 16-byte.
+ * Not claimed bit-compatible with other HQC implementations. */
+
+/* SHAKE256 (FIPS 202) of `count` rows of `len` bytes: msg [count][len] ->
+ * out [count][outlen], one row per GPU thread. */
+int hqc_shake256_batch(int64_t count, const uint8_t* msg, int32_t len, uint8_t* out, int32_t outlen, void* stream);
+
+/* Key pairs from seeds (Algorithm 3): seed_sk, seed_pk [nkeys][32] ->
+ * h_out, s_out [nkeys][W_u_pitch] (pad word zero), x_out, y_out [nkeys][w]
+ * (register y_out with hqc_keys_register for decapsulation). */
+int hqc_kem_keygen(int level, int64_t nkeys, const uint8_t* seed_sk, const uint8_t* seed_pk, uint64_t* h_out,
+                   uint32_t* x_out, uint32_t* y_out, uint64_t* s_out, void* stream);
+
+/* Device workspace that hqc_kem_encaps / hqc_kem_decaps need for `count`
+ * items (0 for a bad level or count <= 0). */
+size_t hqc_kem_workspace_bytes(int level, int64_t count);
+
+/* Encapsulation: item i encrypts m[i] under key key_idx[i] of (h, s)
+ * ([nkeys][W_u_pitch]) with the randomness drawn from G(m[i], salt[i]),
+ * writes (u_out, v_out) and K_out [count][32].  Three kernels: derive,
+ * encrypt, K.  HQC_ENOMEM if the workspace is short. */
+int hqc_kem_encaps(int level, int64_t count, const uint64_t* h, const uint64_t* s, int64_t nkeys,
+                   const int32_t* key_idx, const uint8_t* m, const uint8_t* salt, uint64_t* u_out, uint64_t* v_out,
+                   uint8_t* K_out, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Decapsulation: decrypt with the registered y (keys), re-derive the
+ * randomness, re-encrypt under (h, s) of the same key and compare with
+ * (u, v) on the n and n1 n2 bits; K_out [count][32] = K(m', c) on a match,
+ * K(sigma[key], c) otherwise (sigma [nkeys][k]), selected by mask.  ok_out
+ * (optional, [count] uint32) receives 1 on a match.  Four kernels: fused
+ * decrypt, derive, re-encrypt-and-compare, K. */
+int hqc_kem_decaps(int level, int64_t count, const hqc_keyset_t* keys, const uint64_t* h, const uint64_t* s,
+                   const uint8_t* sigma, const int32_t* key_idx, const uint64_t* u, const uint64_t* v,
+                   const uint8_t* salt, uint8_t* K_out, uint32_t* ok_out, void* workspace, size_t workspace_bytes,
+                   void* stream);
+
 /* Every intermediate of Algorithm 2, per ciphertext (device arrays):
  *   t    [count][W_v]  u*y truncated to n1*n2 bits
  *   w    [count][W_v]  v + t

@@ -23,7 +23,8 @@ __all__ = [
     "hqc_decrypt_batch_staged", "hqc_decrypt_batch_staged_noalloc", "hqc_decrypt_debug", "hqc_mixed_workspace_bytes",
     "hqc_decrypt_mixed", "hqc_set_launch_config", "hqc_get_launch_shape", "hqc_keygen_batch",
     "hqc_encrypt_batch", "LEVELS", "Plan", "hqc_plan_create_keyed", "hqc_plan_create_mixed", "hqc_serve_run",
-    "SERVE_STATUS", "hqc_decrypt_host_keyed", "hqc_host_workspace_bytes",
+    "SERVE_STATUS", "hqc_decrypt_host_keyed", "hqc_host_workspace_bytes", "hqc_shake256_batch",
+    "hqc_kem_keygen", "hqc_kem_workspace_bytes", "hqc_kem_encaps", "hqc_kem_decaps",
 ]
 
 LEVELS = (1, 3, 5)
@@ -91,6 +92,11 @@ def load(build_if_missing: bool = True):
             "hqc_serve_run": (i32, [P, P, P, i64, P, P, P, P, P]),
             "hqc_host_workspace_bytes": (sz, [i32, i64]),
             "hqc_decrypt_host_keyed": (i32, [i32, i64, P, P, P, P, P, i64, P, sz, P]),
+            "hqc_shake256_batch": (i32, [i64, P, i32, P, i32, P]),
+            "hqc_kem_keygen": (i32, [i32, i64, P, P, P, P, P, P, P]),
+            "hqc_kem_workspace_bytes": (sz, [i32, i64]),
+            "hqc_kem_encaps": (i32, [i32, i64, P, P, i64, P, P, P, P, P, P, P, sz, P]),
+            "hqc_kem_decaps": (i32, [i32, i64, P, P, P, P, P, P, P, P, P, P, P, sz, P]),
             "hqc_keygen_batch": (i32, [i32, i64, P, P, P, P, P]),
             "hqc_encrypt_batch": (i32, [i32, i64, P, P, i64, P, P, P, P, P, P, P, P]),
         }
@@ -550,3 +556,92 @@ def hqc_decrypt_host_keyed(level, u_host, v_host, keys: Keyset, key_idx_host, m_
                                          int(chunk), _dev_ptr(workspace, torch.uint8, None, "workspace"),
                                          workspace.numel(), _stream(stream)))
     return m_host
+
+
+# ---------------------------------------------------------------------------
+# SHAKE256 and the KEM (device tensors in, device tensors out)
+# ---------------------------------------------------------------------------
+def hqc_shake256_batch(msg, outlen: int, out=None, stream=None):
+    """SHAKE256 of each row of msg (CUDA uint8 [count][len]) -> [count][outlen]."""
+    torch = _torch()
+    cnt, ln = msg.shape
+    if out is None:
+        out = torch.empty((cnt, outlen), dtype=torch.uint8, device=msg.device)
+    _check(load().hqc_shake256_batch(cnt, _dev_ptr(msg, torch.uint8, None, "msg"), ln,
+                                     _dev_ptr(out, torch.uint8, (cnt, outlen), "out"), outlen, _stream(stream)))
+    return out
+
+
+def hqc_kem_keygen(level, seed_sk, seed_pk, stream=None):
+    """(h, x, y, s) from seeds (CUDA uint8 [nkeys][32] each)."""
+    torch = _torch()
+    P = hqc_get_params(level)
+    nk = seed_sk.shape[0]
+    dev = seed_sk.device
+    h = torch.empty((nk, P.W_u_pitch), dtype=torch.int64, device=dev)
+    s = torch.empty_like(h)
+    x = torch.empty((nk, P.w), dtype=torch.int32, device=dev)
+    y = torch.empty_like(x)
+    _check(load().hqc_kem_keygen(level, nk, _dev_ptr(seed_sk, torch.uint8, (nk, 32), "seed_sk"),
+                                 _dev_ptr(seed_pk, torch.uint8, (nk, 32), "seed_pk"), _dev_ptr(h, torch.int64),
+                                 _dev_ptr(x, torch.int32), _dev_ptr(y, torch.int32), _dev_ptr(s, torch.int64),
+                                 _stream(stream)))
+    return h, x, y, s
+
+
+def hqc_kem_workspace_bytes(level: int, count: int) -> int:
+    return int(load().hqc_kem_workspace_bytes(level, count))
+
+
+def _kem_ws(level, cnt, workspace, dev):
+    torch = _torch()
+    need = hqc_kem_workspace_bytes(level, cnt)
+    if workspace is None:
+        workspace = torch.empty(max(need, 16), dtype=torch.uint8, device=dev)
+    return workspace
+
+
+def hqc_kem_encaps(level, h, s, key_idx, m, salt, u_out=None, v_out=None, K_out=None, workspace=None, stream=None):
+    """(u, v, K): encapsulation of m [count][k] with salt [count][16] under
+    key key_idx[i] of (h, s) [nkeys][W_u_pitch]; all CUDA tensors."""
+    torch = _torch()
+    P = hqc_get_params(level)
+    h, s = _as_u64(h), _as_u64(s)
+    cnt = key_idx.shape[0]
+    dev = key_idx.device
+    u_out = torch.empty((cnt, P.W_u_pitch), dtype=torch.int64, device=dev) if u_out is None else _as_u64(u_out)
+    v_out = torch.empty((cnt, P.W_v), dtype=torch.int64, device=dev) if v_out is None else _as_u64(v_out)
+    K_out = torch.empty((cnt, 32), dtype=torch.uint8, device=dev) if K_out is None else K_out
+    ws = _kem_ws(level, cnt, workspace, dev)
+    _check(load().hqc_kem_encaps(level, cnt, _dev_ptr(h, torch.int64), _dev_ptr(s, torch.int64), h.shape[0],
+                                 _dev_ptr(key_idx, torch.int32, (cnt,), "key_idx"),
+                                 _dev_ptr(m, torch.uint8, (cnt, P.k), "m"), _dev_ptr(salt, torch.uint8, (cnt, 16), "salt"),
+                                 _dev_ptr(u_out, torch.int64, (cnt, P.W_u_pitch), "u_out"),
+                                 _dev_ptr(v_out, torch.int64, (cnt, P.W_v), "v_out"),
+                                 _dev_ptr(K_out, torch.uint8, (cnt, 32), "K_out"), _dev_ptr(ws, torch.uint8),
+                                 ws.numel(), _stream(stream)))
+    return u_out, v_out, K_out
+
+
+def hqc_kem_decaps(level, keys: Keyset, h, s, sigma, key_idx, u, v, salt, K_out=None, ok_out=None, workspace=None,
+                   stream=None):
+    """(K, ok): decapsulation with implicit rejection; ok is int32 [count]
+    (1 where the re-encryption matched)."""
+    torch = _torch()
+    P = hqc_get_params(level)
+    h, s, u, v = _as_u64(h), _as_u64(s), _as_u64(u), _as_u64(v)
+    cnt = key_idx.shape[0]
+    dev = key_idx.device
+    K_out = torch.empty((cnt, 32), dtype=torch.uint8, device=dev) if K_out is None else K_out
+    ok_out = torch.empty((cnt,), dtype=torch.int32, device=dev) if ok_out is None else ok_out
+    ws = _kem_ws(level, cnt, workspace, dev)
+    _check(load().hqc_kem_decaps(level, cnt, keys.handle, _dev_ptr(h, torch.int64), _dev_ptr(s, torch.int64),
+                                 _dev_ptr(sigma, torch.uint8, (keys.nkeys, P.k), "sigma"),
+                                 _dev_ptr(key_idx, torch.int32, (cnt,), "key_idx"),
+                                 _dev_ptr(u, torch.int64, (cnt, P.W_u_pitch), "u"),
+                                 _dev_ptr(v, torch.int64, (cnt, P.W_v), "v"),
+                                 _dev_ptr(salt, torch.uint8, (cnt, 16), "salt"),
+                                 _dev_ptr(K_out, torch.uint8, (cnt, 32), "K_out"),
+                                 _dev_ptr(ok_out, torch.int32, (cnt,), "ok_out"), _dev_ptr(ws, torch.uint8),
+                                 ws.numel(), _stream(stream)))
+    return K_out, ok_out

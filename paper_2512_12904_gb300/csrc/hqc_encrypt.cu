@@ -79,13 +79,18 @@ __device__ __forceinline__ uint32_t rm_codeword_word(uint32_t B, int t) {
   return w;
 }
 
-template <int LEVEL>
+// CMP: instead of storing (u, v), compare them with (u_in, v_in) on the n
+// and n1 n2 bits (padding of u_in ignored) and store ok[item] = 1 on a match
+// (the re-encryption check of decapsulation).
+template <int LEVEL, bool CMP>
 __global__ void __launch_bounds__(ENC_THREADS) k_encrypt(int64_t count, const uint64_t* __restrict__ h,
                                                         const uint64_t* __restrict__ s, int64_t nkeys,
                                                         const int32_t* __restrict__ key_idx,
                                                         const uint8_t* __restrict__ m, const uint32_t* __restrict__ r1,
                                                         const uint32_t* __restrict__ r2, const uint32_t* __restrict__ e,
-                                                        uint64_t* __restrict__ u, uint64_t* __restrict__ v) {
+                                                        uint64_t* __restrict__ u, uint64_t* __restrict__ v,
+                                                        const uint64_t* __restrict__ u_in,
+                                                        const uint64_t* __restrict__ v_in, uint32_t* __restrict__ ok) {
   using LV = Level<LEVEL>;
   constexpr int NR = LV::NR, n1 = LV::n1, k = LV::k;
   constexpr int WARP_W = LV::U2W_FULL + LV::WP_R;
@@ -114,7 +119,18 @@ __global__ void __launch_bounds__(ENC_THREADS) k_encrypt(int64_t count, const ui
   // u = r1 + h * r2
   full_product_to_smem<LV, LV::wr, LV::WPT_FULL, LV::U2W_FULL>(u2, sup, h + key * LV::W_u_pitch, r2 + it * LV::wr, lane);
   xor_support_bits<LV::wr, LV::n>(u2, r1 + it * LV::wr, lane);
-  store_row<LV::W_u_pitch, LV::N32>(u + it * LV::W_u_pitch, u2, lane);
+  uint32_t diff = 0;
+  if constexpr (CMP) {
+    constexpr int R = LV::n & 31;
+    const uint32_t* ui = reinterpret_cast<const uint32_t*>(u_in + it * LV::W_u_pitch);
+    for (int i = lane; i < LV::N32; i += 32) {
+      uint32_t x = __ldg(ui + i);
+      if (R && i == LV::N32 - 1) x &= (1u << R) - 1u;
+      diff |= x ^ u2[i];
+    }
+  } else {
+    store_row<LV::W_u_pitch, LV::N32>(u + it * LV::W_u_pitch, u2, lane);
+  }
   __syncwarp();
 
   // s * r2, truncated to n1*n2 bits, plus e
@@ -173,7 +189,14 @@ __global__ void __launch_bounds__(ENC_THREADS) k_encrypt(int64_t count, const ui
     }
   }
   __syncwarp();
-  store_row<LV::W_v, LV::W_v32>(v + it * LV::W_v, u2, lane);
+  if constexpr (CMP) {
+    const uint32_t* vi = reinterpret_cast<const uint32_t*>(v_in + it * LV::W_v);
+    for (int i = lane; i < LV::W_v32; i += 32) diff |= __ldg(vi + i) ^ u2[i];
+    const bool differs = __any_sync(FULL_MASK, diff != 0u);
+    if (lane == 0) ok[it] = differs ? 0u : 1u;
+  } else {
+    store_row<LV::W_v, LV::W_v32>(v + it * LV::W_v, u2, lane);
+  }
 }
 
 template <int LEVEL>
@@ -189,17 +212,20 @@ static cudaError_t keygen_level(int64_t nkeys, const uint64_t* h, const uint32_t
   return cudaGetLastError();
 }
 
-template <int LEVEL>
+template <int LEVEL, bool CMP>
 static cudaError_t encrypt_level(int64_t count, const uint64_t* h, const uint64_t* s, int64_t nkeys, const int32_t* ki,
                                  const uint8_t* m, const uint32_t* r1, const uint32_t* r2, const uint32_t* e,
-                                 uint64_t* u, uint64_t* v, cudaStream_t st) {
+                                 uint64_t* u, uint64_t* v, const uint64_t* u_in, const uint64_t* v_in, uint32_t* ok,
+                                 cudaStream_t st) {
   using LV = Level<LEVEL>;
   if (count == 0) return cudaSuccess;
   const int wpb = 4;
   const size_t sm = GF_TABLE_BYTES + 64 + (size_t)wpb * (LV::U2W_FULL + LV::WP_R) * 4;
-  cudaError_t err = cudaFuncSetAttribute(k_encrypt<LEVEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t err =
+      cudaFuncSetAttribute(k_encrypt<LEVEL, CMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (err != cudaSuccess) return err;
-  k_encrypt<LEVEL><<<(unsigned)((count + wpb - 1) / wpb), wpb * 32, sm, st>>>(count, h, s, nkeys, ki, m, r1, r2, e, u, v);
+  k_encrypt<LEVEL, CMP><<<(unsigned)((count + wpb - 1) / wpb), wpb * 32, sm, st>>>(count, h, s, nkeys, ki, m, r1, r2,
+                                                                                  e, u, v, u_in, v_in, ok);
   return cudaGetLastError();
 }
 
@@ -217,9 +243,21 @@ cudaError_t launch_encrypt(int level, int64_t count, const uint64_t* h, const ui
                            const int32_t* key_idx, const uint8_t* m, const uint32_t* r1, const uint32_t* r2,
                            const uint32_t* e, uint64_t* u, uint64_t* v, cudaStream_t st) {
   switch (level) {
-    case 1: return encrypt_level<1>(count, h, s, nkeys, key_idx, m, r1, r2, e, u, v, st);
-    case 3: return encrypt_level<3>(count, h, s, nkeys, key_idx, m, r1, r2, e, u, v, st);
-    case 5: return encrypt_level<5>(count, h, s, nkeys, key_idx, m, r1, r2, e, u, v, st);
+    case 1: return encrypt_level<1, false>(count, h, s, nkeys, key_idx, m, r1, r2, e, u, v, 0, 0, 0, st);
+    case 3: return encrypt_level<3, false>(count, h, s, nkeys, key_idx, m, r1, r2, e, u, v, 0, 0, 0, st);
+    case 5: return encrypt_level<5, false>(count, h, s, nkeys, key_idx, m, r1, r2, e, u, v, 0, 0, 0, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_encrypt_compare(int level, int64_t count, const uint64_t* h, const uint64_t* s, int64_t nkeys,
+                                   const int32_t* key_idx, const uint8_t* m, const uint32_t* r1, const uint32_t* r2,
+                                   const uint32_t* e, const uint64_t* u_in, const uint64_t* v_in, uint32_t* ok,
+                                   cudaStream_t st) {
+  switch (level) {
+    case 1: return encrypt_level<1, true>(count, h, s, nkeys, key_idx, m, r1, r2, e, 0, 0, u_in, v_in, ok, st);
+    case 3: return encrypt_level<3, true>(count, h, s, nkeys, key_idx, m, r1, r2, e, 0, 0, u_in, v_in, ok, st);
+    case 5: return encrypt_level<5, true>(count, h, s, nkeys, key_idx, m, r1, r2, e, 0, 0, u_in, v_in, ok, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -105,3 +105,25 @@ def test_host_pipeline_workspace_and_argument_checks(level):
     assert lib.hqc_decrypt_host_keyed(level, 0, N, N, N, N, N, 16, N, 0, N) == 0
     assert lib.hqc_decrypt_host_keyed(level, 3, N, N, N, N, N, 16, N, 0, N) == -1
     assert b"NULL" in lib.hqc_last_error()
+
+
+def test_kem_argument_checks_without_a_gpu():
+    lib = hqc.load()
+    N = None
+    assert lib.hqc_shake256_batch(0, N, 5, N, 32, N) == 0
+    assert lib.hqc_shake256_batch(-1, N, 5, N, 32, N) == -1
+    assert lib.hqc_shake256_batch(3, N, 5, N, 32, N) == -1
+    assert lib.hqc_kem_keygen(2, 1, N, N, N, N, N, N, N) == -1
+    assert lib.hqc_kem_keygen(1, 0, N, N, N, N, N, N, N) == 0
+    assert lib.hqc_kem_keygen(1, 2, N, N, N, N, N, N, N) == -1
+    assert b"seeds" in lib.hqc_last_error()
+    for level in (1, 3, 5):
+        p = hqc.hqc_get_params(level)
+        b = hqc.hqc_kem_workspace_bytes(level, 1000)
+        assert b >= 1000 * (p.k + 4 * (2 * p.wr + p.we) + 4) and b % 16 == 0
+    assert hqc.hqc_kem_workspace_bytes(1, 0) == 0
+    assert lib.hqc_kem_encaps(1, 0, N, N, 1, N, N, N, N, N, N, N, 0, N) == 0
+    assert lib.hqc_kem_encaps(1, 5, N, N, 1, N, N, N, N, N, N, N, 0, N) == -1
+    assert lib.hqc_kem_decaps(1, 0, N, N, N, N, N, N, N, N, N, N, N, 0, N) == 0
+    assert lib.hqc_kem_decaps(1, 5, N, N, N, N, N, N, N, N, N, N, N, 0, N) == -1
+    assert b"keys" in lib.hqc_last_error()

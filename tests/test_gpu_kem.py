@@ -1,0 +1,144 @@
+"""GPU parity of SHAKE256 and the KEM kernels against the CPU oracle (and
+SHAKE256 against hashlib): bit-exact bytes, keys, ciphertexts and shared
+secrets, on accepted and implicitly rejected decapsulations."""
+import hashlib
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+LEVELS = (1, 3, 5)
+
+
+@pytest.fixture(scope="module")
+def hqc():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import paper_2512_12904_gb300 as lib
+    lib.load()
+    return lib
+
+
+def cu8(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.uint8)).cuda()
+
+
+def cu64(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.uint64).view(np.int64)).cuda()
+
+
+def cu32(a):
+    return torch.from_numpy(np.ascontiguousarray(a).astype(np.uint32).view(np.int32)).cuda()
+
+
+def host_u64(t):
+    return t.cpu().numpy().view(np.uint64)
+
+
+def rows(count, width, tag):
+    nw = (count * width + 7) // 8 + 1
+    return synth.words(nw, tag=tag).view(np.uint8)[:count * width].reshape(count, width).copy()
+
+
+@pytest.mark.parametrize("length", [0, 1, 33, 135, 136, 137, 272, 500, 4450])
+def test_shake256_batch_matches_hashlib(hqc, length):
+    count = 131  # two blocks of 128 threads, the second ragged
+    msg = rows(count, length, tag=500 + length)
+    for outlen in (1, 32, 136, 300):
+        got = hqc.hqc_shake256_batch(cu8(msg), outlen).cpu().numpy()
+        for i in (0, 1, 77, 127, 128, 130):
+            assert got[i].tobytes() == hashlib.shake_256(msg[i].tobytes()).digest(outlen), (length, outlen, i)
+        if length == 0:
+            continue
+        # every row against the oracle's SHAKE256 for one output length
+        if outlen == 32:
+            for i in range(count):
+                assert got[i].tobytes() == oracle.shake256(msg[i].tobytes(), 32)
+
+
+def _keys(level, nkeys, tag):
+    return rows(nkeys, 32, tag), rows(nkeys, 32, tag + 1)
+
+
+@pytest.mark.parametrize("level", LEVELS)
+def test_kem_keygen_matches_oracle(hqc, level):
+    sk, pk = _keys(level, 133, tag=600 + level)
+    h, x, y, s = hqc.hqc_kem_keygen(level, cu8(sk), cu8(pk))
+    oh, ox, oy, os_ = oracle.kem_keygen(level, sk, pk)
+    assert (host_u64(h) == oh).all()
+    assert (x.cpu().numpy().view(np.uint32) == ox).all()
+    assert (y.cpu().numpy().view(np.uint32) == oy).all()
+    assert (host_u64(s) == os_).all()
+
+
+def _kem_setup(hqc, level, nkeys, count, tag):
+    P = oracle.params(level)
+    sk, pk = _keys(level, nkeys, tag)
+    h, x, y, s = oracle.kem_keygen(level, sk, pk)
+    sigma = rows(nkeys, P.k, tag + 2)
+    kidx = synth.key_assignment(count, nkeys, tag=tag + 3)
+    m = rows(count, P.k, tag + 4)
+    salt = rows(count, 16, tag + 5)
+    return P, h, y, s, sigma, kidx, m, salt
+
+
+@pytest.mark.parametrize("level", LEVELS)
+def test_encaps_matches_oracle(hqc, level):
+    P, h, y, s, sigma, kidx, m, salt = _kem_setup(hqc, level, 5, 150, tag=700 + 10 * level)
+    u, v, K = hqc.hqc_kem_encaps(level, cu64(h), cu64(s), cu32(kidx), cu8(m), cu8(salt))
+    ou, ov, oK = oracle.kem_encaps(level, h, s, kidx, m, salt)
+    assert (host_u64(u) == ou).all()
+    assert (host_u64(v) == ov).all()
+    assert (K.cpu().numpy() == oK).all()
+
+
+@pytest.mark.parametrize("level", LEVELS)
+def test_decaps_accept_and_reject_match_oracle(hqc, level):
+    P, h, y, s, sigma, kidx, m, salt = _kem_setup(hqc, level, 4, 140, tag=800 + 10 * level)
+    u, v, K = oracle.kem_encaps(level, h, s, kidx, m, salt)
+    keys = hqc.Keyset(level, y)
+    # tamper with a third of the items: a v bit, the salt, or u's padding
+    ut, vt, st = u.copy(), v.copy(), salt.copy()
+    vt[0::6, 5] ^= np.uint64(1 << 9)           # rejected (decodes to m, re-encryption differs)
+    st[1::6, 3] ^= 0x40                         # rejected (other randomness)
+    ut[2::6, P.W_u:] = np.uint64(0xA5A5A5A5)    # accepted (padding ignored)
+    ut[3::6, 7] ^= np.uint64(1 << 33)           # rejected
+    Kg, okg = hqc.hqc_kem_decaps(level, keys, cu64(h), cu64(s), cu8(sigma), cu32(kidx), cu64(ut), cu64(vt), cu8(st))
+    oK, ook = oracle.kem_decaps(level, h, s, y, sigma, kidx, ut, vt, st)
+    okg = okg.cpu().numpy().astype(bool)
+    assert (okg == ook).all()
+    assert (Kg.cpu().numpy() == oK).all()
+    assert ook[2::6].all() and (oK[2::6] == K[2::6]).all()
+    assert not ook[0::6].any() and not ook[1::6].any() and not ook[3::6].any()
+    assert ook[4::6].all() and ook[5::6].all()
+    keys.free()
+
+
+def test_kem_full_size_roundtrip_sampled(hqc):
+    """65,536 HQC-1 items under 256 keys: every decapsulated K equals the
+    encapsulated one (a property at any size), and sampled items match the
+    oracle byte for byte."""
+    level, count, nkeys = 1, 65536, 256
+    P = oracle.params(level)
+    sk, pk = _keys(level, nkeys, tag=900)
+    h, x, y, s = hqc.hqc_kem_keygen(level, cu8(sk), cu8(pk))
+    sigma = cu8(rows(nkeys, P.k, 902))
+    kidx = cu32(synth.key_assignment(count, nkeys, tag=903))
+    m = cu8(rows(count, P.k, 904))
+    salt = cu8(rows(count, 16, 905))
+    u, v, K = hqc.hqc_kem_encaps(level, h, s, kidx, m, salt)
+    keys = hqc.Keyset(level, y.cpu().numpy().view(np.uint32))
+    Kd, ok = hqc.hqc_kem_decaps(level, keys, h, s, sigma, kidx, u, v, salt)
+    assert bool(ok.all().item()) and bool((Kd == K).all().item())
+    idx = [0, 1, 4095, 31337, 65535]
+    hh, ss, yy = host_u64(h), host_u64(s), y.cpu().numpy().view(np.uint32)
+    ki = kidx.cpu().numpy()[idx]
+    ou, ov, oK = oracle.kem_encaps(level, hh, ss, ki, m.cpu().numpy()[idx], salt.cpu().numpy()[idx])
+    assert (host_u64(u)[idx] == ou).all() and (host_u64(v)[idx] == ov).all()
+    assert (K.cpu().numpy()[idx] == oK).all()
+    keys.free()
