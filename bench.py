@@ -47,6 +47,14 @@ MIXED_SPLIT = ((1, 40000), (3, 35000), (5, 25000))
 WORKLOADS["serving"] = (0, 0, 384, "Serving: open-loop Poisson bursts of 1-512 requests (log-uniform), levels 40/35/25 %, "
                                    "keys resident, 256 MiB device budget over 4 streams, continuous batching")
 SERVE_LOADS = (1e5, 1e6, 1e7)
+KEM_WORKLOADS = {
+    "kem1-decaps": (1, 65536, 256, "HQC-1 KEM decapsulation: 65536 ciphertexts under 256 seeded keypairs "
+                                   "(decrypt, re-derive, re-encrypt and compare, K with implicit rejection)"),
+    "kem3-decaps": (3, 32768, 128, "HQC-3 KEM decapsulation: 32768 ciphertexts under 128 seeded keypairs"),
+    "kem5-decaps": (5, 32768, 128, "HQC-5 KEM decapsulation: 32768 ciphertexts under 128 seeded keypairs"),
+}
+WORKLOADS.update(KEM_WORKLOADS)
+KEM_UNIT = "decapsulations/s"
 
 
 def parse_args():
@@ -257,6 +265,8 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle
+    if args.workload in KEM_WORKLOADS:
+        return run_reference_kem(args)
     level, count, nkeys, desc = WORKLOADS[args.workload]
     if level == 0:
         level, nkeys = 1, nkeys // 3  # the mixed workload's reference arm times its HQC-1 share
@@ -287,6 +297,56 @@ def run_reference(args):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def kem_oracle_sample(level, nkeys, count, tag):
+    """Seeded key pairs and oracle-encapsulated ciphertexts for the KEM workloads."""
+    import oracle
+    import synth
+    P = oracle.params(level)
+
+    def rows(cnt, width, t):
+        nw = (cnt * width + 7) // 8 + 1
+        return synth.words(nw, tag=t).view(np.uint8)[:cnt * width].reshape(cnt, width).copy()
+
+    h, x, y, s = oracle.kem_keygen(level, rows(nkeys, 32, tag), rows(nkeys, 32, tag + 1))
+    sigma = rows(nkeys, P.k, tag + 2)
+    kidx = synth.key_assignment(count, nkeys, tag=tag + 3)
+    m, salt = rows(count, P.k, tag + 4), rows(count, 16, tag + 5)
+    u, v, K = oracle.kem_encaps(level, h, s, kidx, m, salt)
+    return (h, s, y, sigma, kidx, u, v, salt), K
+
+
+def run_reference_kem(args):
+    import oracle
+    level, count, nkeys, desc = WORKLOADS[args.workload]
+    nkeys = min(nkeys, 16)  # the oracle's key generation is slow; the sample reuses 16 of the key pairs
+    cores = os.cpu_count() or 1
+    probe_args, _ = kem_oracle_sample(level, nkeys, max(2 * cores, 16), tag=7000 + 100 * level)
+    t = time.perf_counter()
+    oracle.kem_decaps(level, *probe_args, nthreads=cores)
+    rate = probe_args[4].size / max(time.perf_counter() - t, 1e-6)
+    # the sample's encapsulation runs on one core: keep it to seconds
+    per_step = int(max(cores, min(count, 2000, 120.0 * rate / max(1, args.steps + args.warmup))))
+    dargs, K = kem_oracle_sample(level, nkeys, per_step, tag=7000 + 100 * level)
+    for _ in range(args.warmup):
+        oracle.kem_decaps(level, *dargs, nthreads=cores)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        Kd, ok = oracle.kem_decaps(level, *dargs, nthreads=cores)
+    dt = time.perf_counter() - t
+    assert ok.all() and (Kd == K).all()
+    value = per_step * args.steps / dt
+    sample = "%d decapsulations per step (oracle-encapsulated, %d key pairs), %d threads" % (per_step, nkeys, cores)
+    print(json.dumps({
+        "impl": "reference", "metric": "HQC KEM decapsulations/sec per GB300", "value": value, "unit": KEM_UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": desc, "level": level, "count": count, "nkeys": nkeys},
+        "cpu_baseline": {"value": value, "unit": KEM_UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": KEM_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
     return 0
 
 
@@ -564,6 +624,8 @@ def run_ours(args):
         return run_mixed(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload in KEM_WORKLOADS:
+        return run_kem(args)
 
     dist = Dist(args.gpus)
     device = torch.device("cuda", dist.local)
@@ -707,6 +769,175 @@ def run_ours(args):
         rate, n, dt = oracle_rate(level, nkeys, args.cpu_seconds, cores)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": "%d ciphertexts of the same workload recipe (oracle-encrypted), %.1f s" % (n, dt)}
+    keys.free()
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+    dist.close()
+    return 0
+
+
+def keccak_perms(n_bytes):
+    """Keccak-f[1600] calls to absorb n_bytes with SHAKE256 (rate 136)."""
+    return n_bytes // 136 + 1
+
+
+KECCAK_OPS = 180 * 24  # 32-bit funnel / 3-input logic ops per permutation (theta, rho-pi, chi, iota)
+
+
+def per_decaps_work(P):
+    """Algorithmic 32-bit ALU ops of one decapsulation, by kernel."""
+    _, _, dec_ops = per_decryption_work(P)
+    N32 = (P.n + 31) // 32
+    W_v32 = P.n1 * P.n2 // 32
+    enc_ops = 2 * P.wr * N32 + 2 * P.wr * W_v32 + P.n1 * 4 * P.mult + (P.k * (2 * P.delta)) * 4 + N32 + W_v32
+    words = 2 * P.wr + P.we
+    derive_perms = keccak_perms(P.k + 17) + 1 + (words - 1) // 34
+    derive_ops = derive_perms * KECCAK_OPS + 2 * (2 * P.wr * P.wr // 2 + P.we * P.we // 2)
+    k_len = P.k + (P.n + 7) // 8 + P.n1 * P.n2 // 8 + 17
+    K_ops = keccak_perms(k_len) * KECCAK_OPS
+    return {"decrypt": dec_ops, "derive": derive_ops, "encrypt_compare": enc_ops, "K": K_ops}
+
+
+def run_kem(args):
+    """Batched KEM decapsulation (and encapsulation) on seeded key pairs."""
+    import torch
+    import synth
+    import paper_2512_12904_gb300 as hqc
+    dist = Dist(args.gpus)
+    device = torch.device("cuda", dist.local)
+    torch.cuda.set_device(device)
+    hqc.load()
+    level, count, nkeys, desc = WORKLOADS[args.workload]
+    P = hqc.hqc_get_params(level)
+    smem_peak, int_peak = load_peaks()
+    tag = 7000 + 100 * level + 10 * dist.rank
+
+    def rows(cnt, width, t):
+        nw = (cnt * width + 7) // 8 + 1
+        a = synth.words(nw, tag=t).view(np.uint8)[:cnt * width].reshape(cnt, width)
+        return torch.from_numpy(a.copy()).to(device)
+
+    seed_sk, seed_pk = rows(nkeys, 32, tag), rows(nkeys, 32, tag + 1)
+    sigma = rows(nkeys, P.k, tag + 2)
+    kidx = torch.from_numpy(synth.key_assignment(count, nkeys, tag=tag + 3)).to(device)
+    m = rows(count, P.k, tag + 4)
+    salt = rows(count, 16, tag + 5)
+    h, x, y, s = hqc.hqc_kem_keygen(level, seed_sk, seed_pk)
+    torch.cuda.synchronize()
+    keys = hqc.Keyset(level, y.cpu().numpy().view(np.uint32))
+    ws = torch.empty(hqc.hqc_kem_workspace_bytes(level, count), dtype=torch.uint8, device=device)
+    stream = torch.cuda.Stream(device=device)
+    u = torch.empty((count, P.W_u_pitch), dtype=torch.int64, device=device)
+    v = torch.empty((count, P.W_v), dtype=torch.int64, device=device)
+    K_enc = torch.empty((count, 32), dtype=torch.uint8, device=device)
+    K_dec = torch.empty_like(K_enc)
+    ok = torch.empty((count,), dtype=torch.int32, device=device)
+    m_dec = torch.empty((count, P.k), dtype=torch.uint8, device=device)
+
+    def encaps():
+        hqc.hqc_kem_encaps(level, h, s, kidx, m, salt, u, v, K_enc, workspace=ws, stream=stream)
+
+    def decaps():
+        hqc.hqc_kem_decaps(level, keys, h, s, sigma, kidx, u, v, salt, K_dec, ok, workspace=ws, stream=stream)
+
+    def decrypt_only():
+        hqc.hqc_decrypt_batch_keyed(level, u, v, keys, kidx, m_dec, stream=stream)
+
+    with torch.cuda.stream(stream):
+        encaps()
+        for _ in range(args.warmup):
+            decaps()
+    torch.cuda.synchronize()
+    total_ms, per, clocks = timed_steps(decaps, args.steps, stream, dist, clocks_idx=dist.local)
+    max_ms = dist.max(total_ms)
+    correct = bool(ok.all().item()) and bool((K_dec == K_enc).all().item())
+    sub = max(5, min(args.steps, 50))
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            encaps()
+    enc_ms, _, _ = timed_steps(encaps, sub, stream, dist)
+    enc_ms = dist.max(enc_ms)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            decrypt_only()
+    dec_ms, _, _ = timed_steps(decrypt_only, sub, stream, dist)
+    dec_ms = dist.max(dec_ms)
+    correct = correct and bool((m_dec == m).all().item())
+    # implicit rejection on a tampered copy: every item rejected, K = K(sigma, c)
+    v_bad = v.clone()
+    v_bad[:, 1] ^= 1 << 20
+    K_bad = torch.empty_like(K_enc)
+    ok_bad = torch.empty_like(ok)
+    hqc.hqc_kem_decaps(level, keys, h, s, sigma, kidx, u, v_bad, salt, K_bad, ok_bad, workspace=ws, stream=stream)
+    torch.cuda.synchronize()
+    rejected_ok = not bool(ok_bad.any().item())
+
+    # end to end: pinned host ciphertexts and salts in, K out
+    u_h, v_h, s_h, k_h = (t.cpu().pin_memory() for t in (u, v, salt, kidx))
+    K_h = torch.empty((count, 32), dtype=torch.uint8).pin_memory()
+    u_e, v_e, s_e, k_e = (torch.empty_like(t) for t in (u, v, salt, kidx))
+    K_e = torch.empty_like(K_enc)
+
+    def e2e_step():
+        for dst, src in ((u_e, u_h), (v_e, v_h), (s_e, s_h), (k_e, k_h)):
+            dst.copy_(src, non_blocking=True)
+        hqc.hqc_kem_decaps(level, keys, h, s, sigma, k_e, u_e, v_e, s_e, K_e, ok, workspace=ws, stream=stream)
+        K_h.copy_(K_e, non_blocking=True)
+
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            e2e_step()
+    e2e_ms, _, _ = timed_steps(e2e_step, sub, stream, dist)
+    e2e_ms = dist.max(e2e_ms)
+    correct = correct and bool((K_h == K_enc.cpu()).all().item())
+    h2d = sum(t.numel() * t.element_size() for t in (u_h, v_h, s_h, k_h))
+
+    work = per_decaps_work(P)
+    ops = sum(work.values())
+    step_s = (total_ms / args.steps) * 1e-3
+    int_ach = ops * count / step_s / 1e9
+    hbm_b = 3 * (P.W_u_pitch + P.W_v) * 8 + P.k * 2 + 16 * 2 + 32 + 8 + 4 * (2 * P.wr + P.we) * 2
+    roofline = {"bound": "alu", "achieved": int_ach, "peak": int_peak / 1e9, "unit": "Gop/s",
+                "frac": int_ach / (int_peak / 1e9) if int_peak else None, "traffic": None,
+                "kernel": "whole decapsulation step (4 kernels)",
+                "ops_per_item": work,
+                "peak_source": "measured in this run: 32-bit funnel-shift + XOR issue rate, all SMs",
+                "others": {"hbm": {"bound": "hbm", "achieved": hbm_b * count / step_s / 1e9,
+                                   "peak": measured_peaks_file().get("hbm_gbs"), "unit": "GB/s"}}}
+    value = dist.sum(float(count)) * args.steps / (max_ms * 1e-3)
+    line = {
+        "metric": "HQC KEM decapsulations/sec per GB300", "value": value, "unit": KEM_UNIT, "n_gpus": dist.world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": desc, "level": level, "count_per_gpu": count, "nkeys": nkeys,
+                   "l2": "inputs (%d MB) larger than L2 (129 MB); no flush" % ((u.numel() + v.numel()) * 8 // 2 ** 20),
+                   "parallelism": "replicas" if dist.world > 1 else "single GPU"},
+        "correct": correct, "implicit_rejection_ok": rejected_ok,
+        "latency_ms": {"p50": pct(per, 50), "p99": pct(per, 99), "max": max(per)},
+        "encaps": {"value": dist.sum(float(count)) * sub / (enc_ms * 1e-3), "unit": "encapsulations/s",
+                   "ms_per_step": enc_ms / sub},
+        "decrypt_only": {"value": dist.sum(float(count)) * sub / (dec_ms * 1e-3), "unit": UNIT,
+                         "ms_per_step": dec_ms / sub},
+        "roofline": roofline,
+        "e2e": {"value": dist.sum(float(count)) * sub / (e2e_ms * 1e-3), "unit": KEM_UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": K_h.numel(), "steps": sub,
+                "api": "copy u, v, salt, key_idx in; hqc_kem_decaps; copy K out"},
+        "gpu_launches": 4 * args.steps,
+        "clocks": clocks,
+    }
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        import oracle
+        cores = os.cpu_count() or 1
+        n = max(4 * cores, 32)
+        hh, ss, yy = (t.cpu().numpy().view(np.uint64 if t.dtype == torch.int64 else np.uint32) for t in (h, s, y))
+        t0 = time.perf_counter()
+        Ko, oko = oracle.kem_decaps(level, hh, ss, yy, sigma.cpu().numpy(), kidx[:n].cpu().numpy(),
+                                    u[:n].cpu().numpy().view(np.uint64), v[:n].cpu().numpy().view(np.uint64),
+                                    salt[:n].cpu().numpy(), nthreads=cores)
+        dt = time.perf_counter() - t0
+        line["correct"] = line["correct"] and bool(oko.all()) and bool((Ko == K_enc[:n].cpu().numpy()).all())
+        line["cpu_baseline"] = {"value": n / dt, "unit": KEM_UNIT, "cores": cores, "kind": "oracle",
+                                "sample": "%d decapsulations of the same workload, %.1f s" % (n, dt)}
     keys.free()
     if dist.rank == 0:
         print(json.dumps(line), flush=True)

@@ -71,7 +71,7 @@ def _load():
                 "oracle_kem_randomness": (ctypes.c_int, [ctypes.c_int, P, P, P, P]),
                 "oracle_kem_keygen": (ctypes.c_int, [ctypes.c_int, i64, P, P, P, P, P, P]),
                 "oracle_kem_encaps": (ctypes.c_int, [ctypes.c_int, i64, P, P, P, P, P, P, P, P]),
-                "oracle_kem_decaps": (ctypes.c_int, [ctypes.c_int, i64, P, P, P, P, P, P, P, P, P, P]),
+                "oracle_kem_decaps": (ctypes.c_int, [ctypes.c_int, i64, P, P, P, P, P, P, P, P, P, P, ctypes.c_int]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -376,7 +376,7 @@ def kem_encaps(level: int, h, s, key_idx, m, salt):
     return u, v, K
 
 
-def kem_decaps(level: int, h, s, y, sigma, key_idx, u, v, salt):
+def kem_decaps(level: int, h, s, y, sigma, key_idx, u, v, salt, nthreads=1):
     """(K, ok) per item: decrypt, re-encrypt, compare, implicit rejection (A21)."""
     P = params(level)
     key_idx = np.ascontiguousarray(key_idx, np.int32)
@@ -386,5 +386,5 @@ def kem_decaps(level: int, h, s, y, sigma, key_idx, u, v, salt):
     args = [np.ascontiguousarray(h, np.uint64), np.ascontiguousarray(s, np.uint64), np.ascontiguousarray(y, np.uint32),
             np.ascontiguousarray(sigma, np.uint8), key_idx, np.ascontiguousarray(u, np.uint64),
             np.ascontiguousarray(v, np.uint64), np.ascontiguousarray(salt, np.uint8)]
-    assert _load().oracle_kem_decaps(level, cnt, *[_p(a) for a in args], _p(K), _p(ok)) == 0
+    assert _load().oracle_kem_decaps(level, cnt, *[_p(a) for a in args], _p(K), _p(ok), int(nthreads)) == 0
     return K, ok.astype(bool)

@@ -41,6 +41,7 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <pthread.h>
 
 /* ------------------------------------------------------------------ */
 /* Keccak-f[1600] (FIPS 202, Sec. 3.2): state lanes A[x][y], 64 bits,   */
@@ -319,13 +320,25 @@ int oracle_kem_encaps(int level, int64_t count, const uint64_t *h, const uint64_
 }
 
 /* Decaps (A21): y [nkeys][w], sigma [nkeys][k]; ok_out [count] (may be
- * NULL) receives 1 when the re-encryption matched. */
-int oracle_kem_decaps(int level, int64_t count, const uint64_t *h, const uint64_t *s, const uint32_t *y,
-                      const uint8_t *sigma, const int32_t *key_idx, const uint64_t *u_in, const uint64_t *v_in,
-                      const uint8_t *salt, uint8_t *K_out, int32_t *ok_out)
+ * NULL) receives 1 when the re-encryption matched.  Items are split over
+ * nthreads threads (each item is independent). */
+typedef struct {
+    int level;
+    int64_t first, last;
+    const uint64_t *h, *s, *u_in, *v_in;
+    const uint32_t *y;
+    const uint8_t *sigma, *salt;
+    const int32_t *key_idx;
+    uint8_t *K_out;
+    int32_t *ok_out;
+    int rc;
+} decaps_job;
+
+static void *decaps_range(void *arg)
 {
+    decaps_job *J = (decaps_job *)arg;
     kparams q;
-    if (kem_params(level, &q)) return -1;
+    if (kem_params(J->level, &q)) { J->rc = -1; return NULL; }
     uint32_t *r1 = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)q.wr);
     uint32_t *r2 = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)q.wr);
     uint32_t *e = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)q.we);
@@ -333,20 +346,20 @@ int oracle_kem_decaps(int level, int64_t count, const uint64_t *h, const uint64_
     uint64_t *v2 = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)q.W_v);
     uint8_t *mp = (uint8_t *)malloc((size_t)q.k);
     int rc = 0;
-    for (int64_t i = 0; i < count && rc == 0; i++) {
-        const int32_t key = key_idx[i];
-        const uint64_t *u = u_in + i * q.W_u_pitch, *v = v_in + i * q.W_v;
-        rc = oracle_decrypt_batch(level, 1, u, v, y + (int64_t)key * q.w, mp, 1);
+    for (int64_t i = J->first; i < J->last && rc == 0; i++) {
+        const int32_t key = J->key_idx[i];
+        const uint64_t *u = J->u_in + i * q.W_u_pitch, *v = J->v_in + i * q.W_v;
+        rc = oracle_decrypt_batch(J->level, 1, u, v, J->y + (int64_t)key * q.w, mp, 1);
         uint8_t theta[32];
-        oracle_kem_theta(q.k, mp, salt + 16 * i, theta);
-        oracle_kem_randomness(level, theta, r1, r2, e);
-        if (rc == 0) rc = oracle_encrypt_batch(level, 1, h, s, &key, mp, r1, r2, e, u2, v2, 1);
+        oracle_kem_theta(q.k, mp, J->salt + 16 * i, theta);
+        oracle_kem_randomness(J->level, theta, r1, r2, e);
+        if (rc == 0) rc = oracle_encrypt_batch(J->level, 1, J->h, J->s, &key, mp, r1, r2, e, u2, v2, 1);
         int same = 1;
         for (int b = 0; b < q.n; b++)
             same &= ((u[b / 64] >> (b % 64)) & 1) == ((u2[b / 64] >> (b % 64)) & 1);
         for (int wdx = 0; wdx < q.W_v; wdx++) same &= v[wdx] == v2[wdx];
-        kem_K(&q, same ? mp : sigma + (int64_t)key * q.k, u, v, salt + 16 * i, K_out + 32 * i);
-        if (ok_out) ok_out[i] = same;
+        kem_K(&q, same ? mp : J->sigma + (int64_t)key * q.k, u, v, J->salt + 16 * i, J->K_out + 32 * i);
+        if (J->ok_out) J->ok_out[i] = same;
     }
     free(r1);
     free(r2);
@@ -354,5 +367,34 @@ int oracle_kem_decaps(int level, int64_t count, const uint64_t *h, const uint64_
     free(u2);
     free(v2);
     free(mp);
+    J->rc = rc;
+    return NULL;
+}
+
+int oracle_kem_decaps(int level, int64_t count, const uint64_t *h, const uint64_t *s, const uint32_t *y,
+                      const uint8_t *sigma, const int32_t *key_idx, const uint64_t *u_in, const uint64_t *v_in,
+                      const uint8_t *salt, uint8_t *K_out, int32_t *ok_out, int nthreads)
+{
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    if (count < nthreads) nthreads = count > 0 ? (int)count : 1;
+    decaps_job jobs[256];
+    pthread_t tid[256];
+    for (int t = 0; t < nthreads; t++) {
+        decaps_job *J = &jobs[t];
+        J->level = level;
+        J->first = count * t / nthreads;
+        J->last = count * (t + 1) / nthreads;
+        J->h = h; J->s = s; J->y = y; J->sigma = sigma; J->key_idx = key_idx;
+        J->u_in = u_in; J->v_in = v_in; J->salt = salt; J->K_out = K_out; J->ok_out = ok_out;
+        J->rc = 0;
+    }
+    for (int t = 1; t < nthreads; t++) pthread_create(&tid[t], NULL, decaps_range, &jobs[t]);
+    decaps_range(&jobs[0]);
+    int rc = jobs[0].rc;
+    for (int t = 1; t < nthreads; t++) {
+        pthread_join(tid[t], NULL);
+        if (jobs[t].rc) rc = jobs[t].rc;
+    }
     return rc;
 }

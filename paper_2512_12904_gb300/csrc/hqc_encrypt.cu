@@ -11,17 +11,55 @@ namespace hqc {
 
 constexpr int ENC_THREADS = 256;
 
+// RS generator g(x) = prod_{i=1}^{2 delta} (x - alpha^i) over GF(2^8) mod
+// x^8 + x^4 + x^3 + x^2 + 1, alpha = x, computed at compile time; the
+// encoder uses the logs of its coefficients (511 for a zero coefficient).
+__host__ __device__ constexpr uint32_t ce_gf_mul(uint32_t a, uint32_t b) {
+  uint32_t r = 0;
+  for (int i = 0; i < 8; i++) {
+    if ((b >> i) & 1u) r ^= a;
+    a <<= 1;
+    if (a & 0x100u) a ^= 0x11Du;
+  }
+  return r;
+}
+__host__ __device__ constexpr uint32_t ce_gf_pow_alpha(int e) {
+  uint32_t r = 1;
+  for (int i = 0; i < e; i++) r = ce_gf_mul(r, 2u);
+  return r;
+}
+template <int NR>
+struct RsGenLog {
+  uint32_t lg[NR + 1];
+  __host__ __device__ constexpr RsGenLog() : lg() {
+    uint32_t g[NR + 1] = {};
+    g[0] = 1;
+    for (int i = 1; i <= NR; i++) {
+      const uint32_t root = ce_gf_pow_alpha(i);
+      for (int d = i; d >= 0; d--) g[d] = (d > 0 ? g[d - 1] : 0u) ^ ce_gf_mul(g[d], root);
+    }
+    for (int d = 0; d <= NR; d++) {
+      lg[d] = 511u;
+      uint32_t p = 1;
+      for (int e = 0; e < 255; e++) {
+        if (p == g[d]) { lg[d] = (uint32_t)e; break; }
+        p = ce_gf_mul(p, 2u);
+      }
+    }
+  }
+};
+
 // Product of the dense row `dense` by the support `supp` (w entries, may
 // be invalid -> masked) over the full n bits, left in u2[0, N32) with the
 // bits >= n of the last word cleared.
-template <class LV, int W, int WPT, int U2W>
+template <class LV, int W, int WPT, int U2W, bool MASKED = true>
 __device__ __forceinline__ void full_product_to_smem(uint32_t* u2, uint32_t* sup, const uint64_t* dense,
                                                      const uint32_t* supp, int lane) {
   constexpr int N32 = LV::N32, R = LV::n & 31;
   load_supports<LV::n, W>(sup, supp, lane);
   build_doubled<LV::n, LV::W_u_pitch, U2W>(u2, dense, lane);
   uint32_t acc[WPT];
-  rot_xor_product<WPT, W, true>(u2, sup, lane, acc);
+  rot_xor_product<WPT, W, MASKED>(u2, sup, lane, acc);
   __syncwarp();
 #pragma unroll
   for (int k = 0; k < WPT; k++) {
@@ -79,10 +117,13 @@ __device__ __forceinline__ uint32_t rm_codeword_word(uint32_t B, int t) {
   return w;
 }
 
+// Persistent: each warp encrypts items it, it + (warps in the grid), ...
 // CMP: instead of storing (u, v), compare them with (u_in, v_in) on the n
 // and n1 n2 bits (padding of u_in ignored) and store ok[item] = 1 on a match
-// (the re-encryption check of decapsulation).
-template <int LEVEL, bool CMP>
+// (the re-encryption check of decapsulation).  VALID: the supports are known
+// to hold distinct positions < n (drawn by the sampler), so the product
+// takes the unmasked two-entries-per-pass path.
+template <int LEVEL, bool CMP, bool VALID>
 __global__ void __launch_bounds__(ENC_THREADS) k_encrypt(int64_t count, const uint64_t* __restrict__ h,
                                                         const uint64_t* __restrict__ s, int64_t nkeys,
                                                         const int32_t* __restrict__ key_idx,
@@ -94,108 +135,111 @@ __global__ void __launch_bounds__(ENC_THREADS) k_encrypt(int64_t count, const ui
   using LV = Level<LEVEL>;
   constexpr int NR = LV::NR, n1 = LV::n1, k = LV::k;
   constexpr int WARP_W = LV::U2W_FULL + LV::WP_R;
+  constexpr int NX = cdiv(NR, 32);
+  constexpr RsGenLog<NR> GL{};
   extern __shared__ __align__(16) uint8_t smem[];
   gf_tables_init(smem, threadIdx.x, blockDim.x);
-  uint8_t* g = smem + GF_TABLE_BYTES;  // generator, NR + 1 coefficients (64 bytes reserved)
   __syncthreads();
-  if (threadIdx.x == 0) {
-    const GF gf0(smem, 0);
-    for (int d = 0; d <= NR; d++) g[d] = d == 0;
-    for (int i = 1; i <= NR; i++) {
-      const uint32_t root = gf0.exp((uint32_t)i);
-      for (int d = i; d >= 0; d--) g[d] = (uint8_t)((d > 0 ? g[d - 1] : 0u) ^ gf0.mul(g[d], root));
-    }
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t it = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-  if (it >= count) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const GF gf(smem, lane);
-  uint32_t* u2 = reinterpret_cast<uint32_t*>(smem + GF_TABLE_BYTES + 64) + warp * WARP_W;
+  uint32_t* u2 = reinterpret_cast<uint32_t*>(smem + GF_TABLE_BYTES) + warp * WARP_W;
   uint32_t* sup = u2 + LV::U2W_FULL;
-  const uint32_t ki = (uint32_t)key_idx[it];
-  const int64_t key = ki < (uint64_t)nkeys ? (int64_t)ki : 0;
-
-  // u = r1 + h * r2
-  full_product_to_smem<LV, LV::wr, LV::WPT_FULL, LV::U2W_FULL>(u2, sup, h + key * LV::W_u_pitch, r2 + it * LV::wr, lane);
-  xor_support_bits<LV::wr, LV::n>(u2, r1 + it * LV::wr, lane);
-  uint32_t diff = 0;
-  if constexpr (CMP) {
-    constexpr int R = LV::n & 31;
-    const uint32_t* ui = reinterpret_cast<const uint32_t*>(u_in + it * LV::W_u_pitch);
-    for (int i = lane; i < LV::N32; i += 32) {
-      uint32_t x = __ldg(ui + i);
-      if (R && i == LV::N32 - 1) x &= (1u << R) - 1u;
-      diff |= x ^ u2[i];
-    }
-  } else {
-    store_row<LV::W_u_pitch, LV::N32>(u + it * LV::W_u_pitch, u2, lane);
-  }
-  __syncwarp();
-
-  // s * r2, truncated to n1*n2 bits, plus e
-  build_doubled<LV::n, LV::W_u_pitch, LV::U2W_FULL>(u2, s + key * LV::W_u_pitch, lane);
-  {
-    uint32_t acc[LV::WPT];
-    rot_xor_product<LV::WPT, LV::wr, true>(u2, sup, lane, acc);
-    __syncwarp();
-#pragma unroll
-    for (int kk = 0; kk < LV::WPT; kk++) {
-      const int i = lane * LV::WPT + kk;
-      if (i < LV::W_v32) u2[i] = acc[kk];
-    }
-    __syncwarp();
-  }
-  xor_support_bits<LV::we, LV::n1 * LV::n2>(u2, e + it * LV::we, lane);
-
-  // RS systematic encoding by the division register; lane owns parity
-  // coefficient c = lane + 32 x
-  constexpr int NX = cdiv(NR, 32);
-  uint32_t par[NX];
-#pragma unroll
-  for (int x = 0; x < NX; x++) par[x] = 0;
-  const uint8_t* mrow = m + it * k;
-  for (int i = k - 1; i >= 0; i--) {
-    const uint32_t top = __shfl_sync(FULL_MASK, par[(NR - 1) / 32], (NR - 1) % 32);
-    const uint32_t fb = (uint32_t)mrow[i] ^ top;
-    uint32_t nxt[NX];
-#pragma unroll
-    for (int x = 0; x < NX; x++) {
-      const uint32_t up = __shfl_up_sync(FULL_MASK, par[x], 1);
-      const uint32_t carry = x > 0 ? __shfl_sync(FULL_MASK, par[x > 0 ? x - 1 : 0], 31) : 0u;
-      const int c = lane + 32 * x;
-      const uint32_t prev = lane == 0 ? carry : up;
-      nxt[x] = c < NR ? (prev ^ gf.mul(g[c], fb)) : 0u;
-    }
-#pragma unroll
-    for (int x = 0; x < NX; x++) par[x] = nxt[x];
-  }
-  uint8_t* cw = reinterpret_cast<uint8_t*>(u2 + LV::W_v32);
+  // log g_c of the parity coefficients c = lane + 32 x this lane owns
+  uint32_t lgc[NX];
 #pragma unroll
   for (int x = 0; x < NX; x++) {
-    const int c = lane + 32 * x;
-    if (c < NR) cw[c] = (uint8_t)par[x];
+    uint32_t val = 511u;
+#pragma unroll
+    for (int c = 0; c < NR; c++)
+      if (c == lane + 32 * x) val = GL.lg[c];
+    lgc[x] = val;
   }
-  for (int i = lane; i < k; i += 32) cw[NR + i] = mrow[i];
-  __syncwarp();
-  // duplicated RM(1,7) encoding of every symbol, added into the product
-  for (int j = lane; j < n1; j += 32) {
-    const uint32_t B = cw[j];
-#pragma unroll
-    for (int t = 0; t < 4; t++) {
-      const uint32_t cwt = rm_codeword_word(B, t);
-#pragma unroll
-      for (int rcp = 0; rcp < LV::mult; rcp++) u2[j * (LV::n2 / 32) + 4 * rcp + t] ^= cwt;
+  for (int64_t it = (int64_t)blockIdx.x * nw + warp; it < count; it += (int64_t)gridDim.x * nw) {
+    const uint32_t ki = (uint32_t)key_idx[it];
+    const int64_t key = ki < (uint64_t)nkeys ? (int64_t)ki : 0;
+
+    // u = r1 + h * r2
+    full_product_to_smem<LV, LV::wr, LV::WPT_FULL, LV::U2W_FULL, !VALID>(u2, sup, h + key * LV::W_u_pitch,
+                                                                        r2 + it * LV::wr, lane);
+    xor_support_bits<LV::wr, LV::n>(u2, r1 + it * LV::wr, lane);
+    uint32_t diff = 0;
+    if constexpr (CMP) {
+      constexpr int R = LV::n & 31;
+      const uint32_t* ui = reinterpret_cast<const uint32_t*>(u_in + it * LV::W_u_pitch);
+      for (int i = lane; i < LV::N32; i += 32) {
+        uint32_t x = __ldg(ui + i);
+        if (R && i == LV::N32 - 1) x &= (1u << R) - 1u;
+        diff |= x ^ u2[i];
+      }
+    } else {
+      store_row<LV::W_u_pitch, LV::N32>(u + it * LV::W_u_pitch, u2, lane);
     }
-  }
-  __syncwarp();
-  if constexpr (CMP) {
-    const uint32_t* vi = reinterpret_cast<const uint32_t*>(v_in + it * LV::W_v);
-    for (int i = lane; i < LV::W_v32; i += 32) diff |= __ldg(vi + i) ^ u2[i];
-    const bool differs = __any_sync(FULL_MASK, diff != 0u);
-    if (lane == 0) ok[it] = differs ? 0u : 1u;
-  } else {
-    store_row<LV::W_v, LV::W_v32>(v + it * LV::W_v, u2, lane);
+    __syncwarp();
+
+    // s * r2, truncated to n1*n2 bits, plus e
+    build_doubled<LV::n, LV::W_u_pitch, LV::U2W_FULL>(u2, s + key * LV::W_u_pitch, lane);
+    {
+      uint32_t acc[LV::WPT];
+      rot_xor_product<LV::WPT, LV::wr, !VALID>(u2, sup, lane, acc);
+      __syncwarp();
+#pragma unroll
+      for (int kk = 0; kk < LV::WPT; kk++) {
+        const int i = lane * LV::WPT + kk;
+        if (i < LV::W_v32) u2[i] = acc[kk];
+      }
+      __syncwarp();
+    }
+    xor_support_bits<LV::we, LV::n1 * LV::n2>(u2, e + it * LV::we, lane);
+
+    // RS systematic encoding by the division register; lane owns parity
+    // coefficient c = lane + 32 x
+    uint32_t par[NX];
+#pragma unroll
+    for (int x = 0; x < NX; x++) par[x] = 0;
+    const uint8_t* mrow = m + it * k;
+    for (int i = k - 1; i >= 0; i--) {
+      const uint32_t top = __shfl_sync(FULL_MASK, par[(NR - 1) / 32], (NR - 1) % 32);
+      const uint32_t lfb = gf.log((uint32_t)mrow[i] ^ top);
+      uint32_t nxt[NX];
+#pragma unroll
+      for (int x = 0; x < NX; x++) {
+        const uint32_t up = __shfl_up_sync(FULL_MASK, par[x], 1);
+        const uint32_t carry = x > 0 ? __shfl_sync(FULL_MASK, par[x > 0 ? x - 1 : 0], 31) : 0u;
+        const int c = lane + 32 * x;
+        const uint32_t prev = lane == 0 ? carry : up;
+        nxt[x] = c < NR ? (prev ^ gf.mul_l(lgc[x], lfb)) : 0u;
+      }
+#pragma unroll
+      for (int x = 0; x < NX; x++) par[x] = nxt[x];
+    }
+    uint8_t* cw = reinterpret_cast<uint8_t*>(u2 + LV::W_v32);
+#pragma unroll
+    for (int x = 0; x < NX; x++) {
+      const int c = lane + 32 * x;
+      if (c < NR) cw[c] = (uint8_t)par[x];
+    }
+    for (int i = lane; i < k; i += 32) cw[NR + i] = mrow[i];
+    __syncwarp();
+    // duplicated RM(1,7) encoding of every symbol, added into the product
+    for (int j = lane; j < n1; j += 32) {
+      const uint32_t B = cw[j];
+#pragma unroll
+      for (int t = 0; t < 4; t++) {
+        const uint32_t cwt = rm_codeword_word(B, t);
+#pragma unroll
+        for (int rcp = 0; rcp < LV::mult; rcp++) u2[j * (LV::n2 / 32) + 4 * rcp + t] ^= cwt;
+      }
+    }
+    __syncwarp();
+    if constexpr (CMP) {
+      const uint32_t* vi = reinterpret_cast<const uint32_t*>(v_in + it * LV::W_v);
+      for (int i = lane; i < LV::W_v32; i += 32) diff |= __ldg(vi + i) ^ u2[i];
+      const bool differs = __any_sync(FULL_MASK, diff != 0u);
+      if (lane == 0) ok[it] = differs ? 0u : 1u;
+    } else {
+      store_row<LV::W_v, LV::W_v32>(v + it * LV::W_v, u2, lane);
+    }
+    __syncwarp();
   }
 }
 
@@ -212,20 +256,28 @@ static cudaError_t keygen_level(int64_t nkeys, const uint64_t* h, const uint32_t
   return cudaGetLastError();
 }
 
-template <int LEVEL, bool CMP>
+template <int LEVEL, bool CMP, bool VALID>
 static cudaError_t encrypt_level(int64_t count, const uint64_t* h, const uint64_t* s, int64_t nkeys, const int32_t* ki,
                                  const uint8_t* m, const uint32_t* r1, const uint32_t* r2, const uint32_t* e,
                                  uint64_t* u, uint64_t* v, const uint64_t* u_in, const uint64_t* v_in, uint32_t* ok,
                                  cudaStream_t st) {
   using LV = Level<LEVEL>;
   if (count == 0) return cudaSuccess;
-  const int wpb = 4;
-  const size_t sm = GF_TABLE_BYTES + 64 + (size_t)wpb * (LV::U2W_FULL + LV::WP_R) * 4;
-  cudaError_t err =
-      cudaFuncSetAttribute(k_encrypt<LEVEL, CMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  constexpr int wpb = ENC_THREADS / 32;
+  auto kern = k_encrypt<LEVEL, CMP, VALID>;
+  const size_t sm = GF_TABLE_BYTES + (size_t)wpb * (LV::U2W_FULL + LV::WP_R) * 4;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (err != cudaSuccess) return err;
-  k_encrypt<LEVEL, CMP><<<(unsigned)((count + wpb - 1) / wpb), wpb * 32, sm, st>>>(count, h, s, nkeys, ki, m, r1, r2,
-                                                                                  e, u, v, u_in, v_in, ok);
+  int dev = 0, sms = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, ENC_THREADS, sm);
+  if (err != cudaSuccess) return err;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  int64_t grid = (int64_t)sms * occ;
+  const int64_t need = (count + wpb - 1) / wpb;
+  if (need < grid) grid = need;
+  kern<<<(unsigned)grid, ENC_THREADS, sm, st>>>(count, h, s, nkeys, ki, m, r1, r2, e, u, v, u_in, v_in, ok);
   return cudaGetLastError();
 }
 
@@ -243,9 +295,9 @@ cudaError_t launch_encrypt(int level, int64_t count, const uint64_t* h, const ui
                            const int32_t* key_idx, const uint8_t* m, const uint32_t* r1, const uint32_t* r2,
                            const uint32_t* e, uint64_t* u, uint64_t* v, cudaStream_t st) {
   switch (level) {
-    case 1: return encrypt_level<1, false>(count, h, s, nkeys, key_idx, m, r1, r2, e, u, v, 0, 0, 0, st);
-    case 3: return encrypt_level<3, false>(count, h, s, nkeys, key_idx, m, r1, r2, e, u, v, 0, 0, 0, st);
-    case 5: return encrypt_level<5, false>(count, h, s, nkeys, key_idx, m, r1, r2, e, u, v, 0, 0, 0, st);
+    case 1: return encrypt_level<1, false, false>(count, h, s, nkeys, key_idx, m, r1, r2, e, u, v, 0, 0, 0, st);
+    case 3: return encrypt_level<3, false, false>(count, h, s, nkeys, key_idx, m, r1, r2, e, u, v, 0, 0, 0, st);
+    case 5: return encrypt_level<5, false, false>(count, h, s, nkeys, key_idx, m, r1, r2, e, u, v, 0, 0, 0, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -255,9 +307,21 @@ cudaError_t launch_encrypt_compare(int level, int64_t count, const uint64_t* h, 
                                    const uint32_t* e, const uint64_t* u_in, const uint64_t* v_in, uint32_t* ok,
                                    cudaStream_t st) {
   switch (level) {
-    case 1: return encrypt_level<1, true>(count, h, s, nkeys, key_idx, m, r1, r2, e, 0, 0, u_in, v_in, ok, st);
-    case 3: return encrypt_level<3, true>(count, h, s, nkeys, key_idx, m, r1, r2, e, 0, 0, u_in, v_in, ok, st);
-    case 5: return encrypt_level<5, true>(count, h, s, nkeys, key_idx, m, r1, r2, e, 0, 0, u_in, v_in, ok, st);
+    case 1: return encrypt_level<1, true, true>(count, h, s, nkeys, key_idx, m, r1, r2, e, 0, 0, u_in, v_in, ok, st);
+    case 3: return encrypt_level<3, true, true>(count, h, s, nkeys, key_idx, m, r1, r2, e, 0, 0, u_in, v_in, ok, st);
+    case 5: return encrypt_level<5, true, true>(count, h, s, nkeys, key_idx, m, r1, r2, e, 0, 0, u_in, v_in, ok, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Encryption with sampler-drawn supports (the KEM's encapsulation).
+cudaError_t launch_encrypt_valid(int level, int64_t count, const uint64_t* h, const uint64_t* s, int64_t nkeys,
+                                 const int32_t* key_idx, const uint8_t* m, const uint32_t* r1, const uint32_t* r2,
+                                 const uint32_t* e, uint64_t* u, uint64_t* v, cudaStream_t st) {
+  switch (level) {
+    case 1: return encrypt_level<1, false, true>(count, h, s, nkeys, key_idx, m, r1, r2, e, u, v, 0, 0, 0, st);
+    case 3: return encrypt_level<3, false, true>(count, h, s, nkeys, key_idx, m, r1, r2, e, u, v, 0, 0, 0, st);
+    case 5: return encrypt_level<5, false, true>(count, h, s, nkeys, key_idx, m, r1, r2, e, u, v, 0, 0, 0, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -94,6 +94,9 @@ cudaError_t launch_encrypt_compare(int level, int64_t count, const uint64_t* h, 
                                    const int32_t* key_idx, const uint8_t* m, const uint32_t* r1, const uint32_t* r2,
                                    const uint32_t* e, const uint64_t* u_in, const uint64_t* v_in, uint32_t* ok,
                                    cudaStream_t st);
+cudaError_t launch_encrypt_valid(int level, int64_t count, const uint64_t* h, const uint64_t* s, int64_t nkeys,
+                                 const int32_t* key_idx, const uint8_t* m, const uint32_t* r1, const uint32_t* r2,
+                                 const uint32_t* e, uint64_t* u, uint64_t* v, cudaStream_t st);
 cudaError_t launch_shake256(int64_t count, const uint8_t* msg, int len, uint8_t* out, int outlen, cudaStream_t st);
 cudaError_t launch_kem_seed_keys(int level, int64_t nkeys, const uint8_t* seed_sk, const uint8_t* seed_pk,
                                  uint64_t* h, uint32_t* x, uint32_t* y, cudaStream_t st);

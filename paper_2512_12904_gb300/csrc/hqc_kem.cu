@@ -423,7 +423,7 @@ int hqc_kem_encaps(int level, int64_t count, const uint64_t* h, const uint64_t* 
   cudaStream_t st = (cudaStream_t)stream;
   int rc = kcuda(hqc::launch_kem_derive(level, count, m, salt, w.r1, w.r2, w.e, st), "derive launch");
   if (rc == HQC_OK)
-    rc = kcuda(hqc::launch_encrypt(level, count, h, s, nkeys, key_idx, m, w.r1, w.r2, w.e, u_out, v_out, st),
+    rc = kcuda(hqc::launch_encrypt_valid(level, count, h, s, nkeys, key_idx, m, w.r1, w.r2, w.e, u_out, v_out, st),
                "encrypt launch");
   if (rc == HQC_OK)
     rc = kcuda(hqc::launch_kem_K(level, count, m, nullptr, nullptr, key_idx, nkeys, u_out, v_out, salt, K_out, st),
