@@ -97,23 +97,35 @@ __device__ __forceinline__ void keccak_f1600(uint64_t (&a)[25]) {
 
 // SHAKE256 absorb of a `len`-byte message whose little-endian 64-bit word q
 // is word(q) (bytes at or past len inside the last word must be zero):
-// M || 1111 || pad10*1 in 136-byte blocks.  len is the same for every
-// thread of a launch, so the control flow is uniform.
+// M || 1111 || pad10*1 in 136-byte blocks.  word(q) is called once per q,
+// in increasing q.  The words of block b + 1 are fetched before block b is
+// permuted, so their loads overlap the permutation.  len is the same for
+// every thread of a launch, so the control flow is uniform.
 template <class WordFn>
 __device__ __forceinline__ void shake256_absorb(uint64_t (&a)[25], int len, WordFn word) {
 #pragma unroll
   for (int i = 0; i < 25; i++) a[i] = 0;
   const int nblocks = len / SHAKE256_RATE + 1;
   const int qpad = len >> 3;
+  auto fetch = [&](int blk, uint64_t (&w)[SHAKE256_RATE_WORDS]) {
+#pragma unroll
+    for (int i = 0; i < SHAKE256_RATE_WORDS; i++) {
+      const int q = blk * SHAKE256_RATE_WORDS + i;
+      w[i] = q < qpad || (q == qpad && (len & 7)) ? word(q) : 0ull;
+    }
+  };
+  uint64_t w[SHAKE256_RATE_WORDS];
+  fetch(0, w);
   for (int blk = 0; blk < nblocks; blk++) {
 #pragma unroll
     for (int i = 0; i < SHAKE256_RATE_WORDS; i++) {
       const int q = blk * SHAKE256_RATE_WORDS + i;
-      uint64_t wv = q < qpad || (q == qpad && (len & 7)) ? word(q) : 0ull;
+      uint64_t wv = w[i];
       if (q == qpad) wv ^= 0x1Full << (8 * (len & 7));
       if (i == SHAKE256_RATE_WORDS - 1 && blk == nblocks - 1) wv ^= 0x80ull << 56;
       a[i] ^= wv;
     }
+    if (blk + 1 < nblocks) fetch(blk + 1, w);
     keccak_f1600(a);
   }
 }

@@ -33,6 +33,7 @@
 namespace hqc {
 
 constexpr int KEM_THREADS = 128;
+constexpr int KEM_K_THREADS = 64;  // 1,024 blocks for 65,536 items: even spread over 152 SMs
 constexpr int KEM_SALT = 16;
 constexpr int KEM_SEED = 32;
 constexpr int KEM_KBYTES = 32;
@@ -78,7 +79,7 @@ __global__ void __launch_bounds__(KEM_THREADS) k_shake256(int64_t count, const u
 template <int WMAX>
 struct DrawSpace {
   static constexpr int BUF = 2 * SHAKE256_RATE_WORDS;  // 34 words per permutation
-  static constexpr int stride = (BUF + cdiv(WMAX, 2)) | 1;
+  static constexpr int stride = (BUF + cdiv(WMAX + 1, 2)) | 1;  // positions and one pad half
 };
 
 struct Stream {
@@ -108,19 +109,36 @@ struct Stream {
   }
 };
 
-// Draw one support of weight W over [0, N) into pos (16-bit halves) and
-// write it to dst[0..W).
+// Draw one support of weight W over [0, N) into pos (16-bit halves, pos[W]
+// = 0xFFFF as a pad that matches nothing) and write it to dst[0..W).  The
+// collision test reads the later positions two halves per 32-bit word and
+// finds an equal half as a zero half of (pair ^ v v): (t - 0x00010001) &
+// ~t & 0x80008000 is nonzero iff some 16-bit half of t is zero.
 template <int N, int W>
 __device__ __forceinline__ void draw_support(Stream& st, uint16_t* pos, uint32_t* __restrict__ dst) {
+  static_assert(N < 0xFFFF, "positions and the pad fit in 16 bits");
   for (int i = 0; i < W; i++) {
     const uint32_t R = st.next();
     pos[i] = (uint16_t)(i + __umulhi(R, (uint32_t)(N - i)));
   }
+  pos[W] = 0xFFFFu;
+  const uint32_t* pairs = reinterpret_cast<const uint32_t*>(pos);
+  constexpr int NP = (W + 1) / 2;  // pairs covering indices 0..W (W odd) or 0..W-1
   for (int i = W - 2; i >= 0; i--) {
     const uint32_t v = pos[i];
-    bool seen = false;
-    for (int j = i + 1; j < W; j++) seen |= pos[j] == v;
-    pos[i] = (uint16_t)sel(seen, (uint32_t)i, v);
+    const uint32_t vv = v * 0x10001u;
+    const int p0 = (i + 1) >> 1;
+    // i even: the first pair holds index i itself in its low half, so only
+    // its high half is compared (the zero-half test flags a pair, not which
+    // half, once a borrow crosses from a zero low half)
+    const uint32_t first = pairs[p0];
+    uint32_t t = first ^ vv;
+    uint32_t hit = (i & 1) ? ((t - 0x00010001u) & ~t & 0x80008000u) : (uint32_t)((first >> 16) == v);
+    for (int p = p0 + 1; p < NP; p++) {
+      t = pairs[p] ^ vv;
+      hit |= (t - 0x00010001u) & ~t & 0x80008000u;
+    }
+    pos[i] = (uint16_t)sel(hit != 0u, (uint32_t)i, v);
   }
   for (int i = 0; i < W; i++) dst[i] = pos[i];
 }
@@ -196,18 +214,27 @@ __global__ void __launch_bounds__(KEM_THREADS) k_kem_derive(int64_t count, const
 
 // K = SHAKE256(x || U || V || salt || 0x04)[0:32]; x = m where ok (or no
 // flags given), sigma of the item's key otherwise, chosen by mask.
+// Message words: x (k/8 words), then the u words up to the one that holds
+// the last byte of U (bits >= n cleared), then, from word P1 on, a stream
+// shifted by r = (k + ceil(n/8)) mod 8 bytes over T = [last u word,
+// v[0..W_v), salt, 0x04]: word P1 + i = (T[i+1] << 8r) | (T[i] >> (64 - 8r)).
+// The previous T word is carried, so each message word costs one load.
 template <int LEVEL>
-__global__ void __launch_bounds__(KEM_THREADS) k_kem_K(int64_t count, const uint8_t* __restrict__ m,
-                                                      const uint32_t* __restrict__ ok,
-                                                      const uint8_t* __restrict__ sigma,
-                                                      const int32_t* __restrict__ key_idx, int64_t nkeys,
-                                                      const uint64_t* __restrict__ u, const uint64_t* __restrict__ v,
-                                                      const uint8_t* __restrict__ salt, uint8_t* __restrict__ K) {
+__global__ void __launch_bounds__(KEM_K_THREADS) k_kem_K(int64_t count, const uint8_t* __restrict__ m,
+                                                        const uint32_t* __restrict__ ok,
+                                                        const uint8_t* __restrict__ sigma,
+                                                        const int32_t* __restrict__ key_idx, int64_t nkeys,
+                                                        const uint64_t* __restrict__ u,
+                                                        const uint64_t* __restrict__ v,
+                                                        const uint8_t* __restrict__ salt, uint8_t* __restrict__ K) {
   using LV = Level<LEVEL>;
   constexpr int KW = LV::k / 8;
   constexpr int UB = cdiv(LV::n, 8), VB = LV::n1 * LV::n2 / 8;
-  constexpr int OFF_V = LV::k + UB, OFF_S = OFF_V + VB, OFF_D = OFF_S + KEM_SALT;
-  constexpr int LEN = OFF_D + 1;
+  constexpr int OFF_V = LV::k + UB;
+  constexpr int LEN = OFF_V + VB + KEM_SALT + 1;
+  constexpr int P1 = OFF_V / 8, R8 = 8 * (OFF_V % 8);
+  constexpr int NT = LV::W_v + 4;  // T[1..NT): v words, two salt words, the domain byte
+  static_assert(P1 == KW + LV::W_u - 1 && R8 > 0, "U ends inside its last word");
   const int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (it >= count) return;
   const uint64_t* mrow = reinterpret_cast<const uint64_t*>(m + it * LV::k);
@@ -222,22 +249,25 @@ __global__ void __launch_bounds__(KEM_THREADS) k_kem_K(int64_t count, const uint
   const uint64_t* urow = u + it * LV::W_u_pitch;
   const uint64_t* vrow = v + it * LV::W_v;
   const uint64_t* srow = reinterpret_cast<const uint64_t*>(salt + it * KEM_SALT);
-  auto useg = [&](int i) {
-    uint64_t w = __ldg(urow + i);
-    if ((LV::n & 63) && i == LV::W_u - 1) w &= (1ull << (LV::n & 63)) - 1ull;
-    return w;
+  constexpr uint64_t UMASK = (LV::n & 63) ? (1ull << (LV::n & 63)) - 1ull : ~0ull;
+  // T[0] = last u word placed so that T[0] >> (64 - 8r) is its U bytes
+  uint64_t prev = (__ldg(urow + LV::W_u - 1) & UMASK) << (64 - R8);
+  auto tword = [&](int i) {  // T[i], i >= 1
+    return i <= LV::W_v ? __ldg(vrow + i - 1) : i <= LV::W_v + 2 ? __ldg(srow + i - 1 - LV::W_v) : 0x04ull;
   };
-  auto vseg = [&](int i) { return __ldg(vrow + i); };
-  auto sseg = [&](int i) { return __ldg(srow + i); };
-  auto dseg = [&](int) { return 0x04ull; };
   uint64_t a[25];
   shake256_absorb(a, LEN, [&](int q) {
-    uint64_t w = 0;
-    if (q < KW) w = (__ldg(mrow + q) & keep) | (__ldg(grow + q) & ~keep);
-    w ^= segment_word(q, LV::k, LV::W_u, useg);
-    w ^= segment_word(q, OFF_V, LV::W_v, vseg);
-    w ^= segment_word(q, OFF_S, 2, sseg);
-    w ^= segment_word(q, OFF_D, 1, dseg);
+    uint64_t w;
+    if (q < KW) {
+      w = (__ldg(mrow + q) & keep) | (__ldg(grow + q) & ~keep);
+    } else if (q < P1) {
+      w = __ldg(urow + q - KW);
+    } else {
+      const int i = q - P1 + 1;
+      const uint64_t cur = i < NT ? tword(i) : 0ull;
+      w = (cur << R8) | (prev >> (64 - R8));
+      prev = cur;
+    }
     return w;
   });
   uint64_t* krow = reinterpret_cast<uint64_t*>(K + it * KEM_KBYTES);
@@ -309,10 +339,11 @@ cudaError_t launch_kem_K(int level, int64_t count, const uint8_t* m, const uint3
                          const int32_t* key_idx, int64_t nkeys, const uint64_t* u, const uint64_t* v,
                          const uint8_t* salt, uint8_t* K, cudaStream_t st) {
   if (count == 0) return cudaSuccess;
+  const unsigned kb = (unsigned)((count + KEM_K_THREADS - 1) / KEM_K_THREADS);
   switch (level) {
-    case 1: k_kem_K<1><<<blocks_for(count), KEM_THREADS, 0, st>>>(count, m, ok, sigma, key_idx, nkeys, u, v, salt, K); break;
-    case 3: k_kem_K<3><<<blocks_for(count), KEM_THREADS, 0, st>>>(count, m, ok, sigma, key_idx, nkeys, u, v, salt, K); break;
-    case 5: k_kem_K<5><<<blocks_for(count), KEM_THREADS, 0, st>>>(count, m, ok, sigma, key_idx, nkeys, u, v, salt, K); break;
+    case 1: k_kem_K<1><<<kb, KEM_K_THREADS, 0, st>>>(count, m, ok, sigma, key_idx, nkeys, u, v, salt, K); break;
+    case 3: k_kem_K<3><<<kb, KEM_K_THREADS, 0, st>>>(count, m, ok, sigma, key_idx, nkeys, u, v, salt, K); break;
+    case 5: k_kem_K<5><<<kb, KEM_K_THREADS, 0, st>>>(count, m, ok, sigma, key_idx, nkeys, u, v, salt, K); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
