@@ -25,6 +25,7 @@ __all__ = [
     "hqc_encrypt_batch", "LEVELS", "Plan", "hqc_plan_create_keyed", "hqc_plan_create_mixed", "hqc_serve_run",
     "SERVE_STATUS", "hqc_decrypt_host_keyed", "hqc_host_workspace_bytes", "hqc_shake256_batch",
     "hqc_kem_keygen", "hqc_kem_workspace_bytes", "hqc_kem_encaps", "hqc_kem_decaps",
+    "hqc_kem_host_workspace_bytes", "hqc_kem_decaps_host",
 ]
 
 LEVELS = (1, 3, 5)
@@ -97,6 +98,8 @@ def load(build_if_missing: bool = True):
             "hqc_kem_workspace_bytes": (sz, [i32, i64]),
             "hqc_kem_encaps": (i32, [i32, i64, P, P, i64, P, P, P, P, P, P, P, sz, P]),
             "hqc_kem_decaps": (i32, [i32, i64, P, P, P, P, P, P, P, P, P, P, P, sz, P]),
+            "hqc_kem_host_workspace_bytes": (sz, [i32, i64]),
+            "hqc_kem_decaps_host": (i32, [i32, i64, P, P, P, P, P, P, P, P, P, P, i64, P, sz, P]),
             "hqc_keygen_batch": (i32, [i32, i64, P, P, P, P, P]),
             "hqc_encrypt_batch": (i32, [i32, i64, P, P, i64, P, P, P, P, P, P, P, P]),
         }
@@ -645,3 +648,43 @@ def hqc_kem_decaps(level, keys: Keyset, h, s, sigma, key_idx, u, v, salt, K_out=
                                  _dev_ptr(ok_out, torch.int32, (cnt,), "ok_out"), _dev_ptr(ws, torch.uint8),
                                  ws.numel(), _stream(stream)))
     return K_out, ok_out
+
+
+def hqc_kem_host_workspace_bytes(level: int, chunk: int) -> int:
+    return int(load().hqc_kem_host_workspace_bytes(level, chunk))
+
+
+def hqc_kem_decaps_host(level, keys: Keyset, h, s, sigma, key_idx_host, u_host, v_host, salt_host, K_host=None,
+                        ok_host=None, chunk=0, workspace=None, stream=None):
+    """Decapsulation from (pinned) HOST tensors with chunked copy/compute
+    overlap; h, s, sigma are CUDA tensors.  Returns (K_host, ok_host), valid
+    once the stream reaches the end of the call."""
+    torch = _torch()
+    P = hqc_get_params(level)
+    h, s = _as_u64(h), _as_u64(s)
+    u_host, v_host = _as_u64(u_host), _as_u64(v_host)
+    cnt = u_host.shape[0]
+    for t, name in ((u_host, "u_host"), (v_host, "v_host"), (key_idx_host, "key_idx_host"), (salt_host, "salt_host")):
+        if t.is_cuda or not t.is_contiguous():
+            raise ValueError("%s must be a contiguous CPU tensor" % name)
+    if tuple(u_host.shape) != (cnt, P.W_u_pitch) or tuple(v_host.shape) != (cnt, P.W_v):
+        raise ValueError("u_host / v_host shapes")
+    if key_idx_host.dtype != torch.int32 or tuple(key_idx_host.shape) != (cnt,):
+        raise ValueError("key_idx_host must be int32 [count]")
+    if salt_host.dtype != torch.uint8 or tuple(salt_host.shape) != (cnt, 16):
+        raise ValueError("salt_host must be uint8 [count][16]")
+    if K_host is None:
+        K_host = torch.empty((cnt, 32), dtype=torch.uint8).pin_memory()
+    if ok_host is None:
+        ok_host = torch.empty((cnt,), dtype=torch.int32).pin_memory()
+    if workspace is None:
+        workspace = torch.empty(hqc_kem_host_workspace_bytes(level, chunk if chunk > 0 else max(1, min(cnt, 16384))),
+                                dtype=torch.uint8, device="cuda")
+    _check(load().hqc_kem_decaps_host(level, cnt, keys.handle, _dev_ptr(h, torch.int64), _dev_ptr(s, torch.int64),
+                                      _dev_ptr(sigma, torch.uint8, (keys.nkeys, P.k), "sigma"),
+                                      ctypes.c_void_p(key_idx_host.data_ptr()), ctypes.c_void_p(u_host.data_ptr()),
+                                      ctypes.c_void_p(v_host.data_ptr()), ctypes.c_void_p(salt_host.data_ptr()),
+                                      ctypes.c_void_p(K_host.data_ptr()), ctypes.c_void_p(ok_host.data_ptr()),
+                                      int(chunk), _dev_ptr(workspace, torch.uint8, None, "workspace"),
+                                      workspace.numel(), _stream(stream)))
+    return K_host, ok_host

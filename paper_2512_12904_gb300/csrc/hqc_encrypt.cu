@@ -4,12 +4,45 @@
 // per item; used to build synthetic ciphertexts on the device.
 #include <cuda_runtime.h>
 
+#include <utility>
+
 #include "hqc_device.cuh"
 #include "hqc_internal.h"
 
 namespace hqc {
 
-constexpr int ENC_THREADS = 256;
+constexpr int ENC_THREADS = 256;  // key generation
+
+// Encryption: as many warps per block as shared memory holds (one u2 region
+// per warp), one block per SM.
+template <int LEVEL> struct EncBound;
+template <> struct EncBound<1> { static constexpr int threads = 1024; };
+template <> struct EncBound<3> { static constexpr int threads = 704; };
+template <> struct EncBound<5> { static constexpr int threads = 448; };
+
+// Compact GF(2^8) tables for the RS encoder: exp[0..511] (exp[511] = 0,
+// exp[e] = alpha^(e mod 255) below) and log[0..255] (log 0 = 511), one copy
+// per block.  The encoder's lookups are few, so bank conflicts between
+// lanes cost little, and the 32 KB lane-replicated tables of the decoder
+// would halve the warps a block can hold.
+constexpr int ENC_GF_BYTES = 512 + 512;
+
+__device__ inline void enc_gf_init(uint8_t* smem, int tid) {
+  uint8_t* ex = smem;
+  uint16_t* lg = reinterpret_cast<uint16_t*>(smem + 512);
+  if (tid == 0) {
+    uint32_t x = 1;
+    for (int e = 0; e < 255; e++) {
+      ex[e] = (uint8_t)x;
+      ex[e + 255] = (uint8_t)x;
+      lg[x] = (uint16_t)e;
+      x = gf_xtime(x);
+    }
+    ex[510] = ex[0];  // e = 510 = 2 * 255: alpha^0
+    ex[511] = 0;
+    lg[0] = (uint16_t)GF_LOG_ZERO;
+  }
+}
 
 // RS generator g(x) = prod_{i=1}^{2 delta} (x - alpha^i) over GF(2^8) mod
 // x^8 + x^4 + x^3 + x^2 + 1, alpha = x, computed at compile time; the
@@ -38,16 +71,27 @@ struct RsGenLog {
       const uint32_t root = ce_gf_pow_alpha(i);
       for (int d = i; d >= 0; d--) g[d] = (d > 0 ? g[d - 1] : 0u) ^ ce_gf_mul(g[d], root);
     }
-    for (int d = 0; d <= NR; d++) {
-      lg[d] = 511u;
-      uint32_t p = 1;
-      for (int e = 0; e < 255; e++) {
-        if (p == g[d]) { lg[d] = (uint32_t)e; break; }
-        p = ce_gf_mul(p, 2u);
-      }
+    uint32_t logt[256] = {};
+    uint32_t p = 1;
+    for (int e = 0; e < 255; e++) {
+      logt[p] = (uint32_t)e;
+      p = ce_gf_mul(p, 2u);
     }
+    for (int d = 0; d <= NR; d++) lg[d] = g[d] ? logt[g[d]] : 511u;
   }
 };
+template <int NR, int C>
+struct RsGenLogAt {
+  static constexpr uint32_t value = RsGenLog<NR>().lg[C];
+};
+// log g_c for a lane's runtime c, as a chain of selects between
+// compile-time immediates (no table in memory)
+template <int NR, int... C>
+__device__ __forceinline__ uint32_t rs_gen_log_select(int c, std::integer_sequence<int, C...>) {
+  uint32_t v = 511u;
+  ((v = (c == C) ? RsGenLogAt<NR, C>::value : v), ...);
+  return v;
+}
 
 // Product of the dense row `dense` by the support `supp` (w entries, may
 // be invalid -> masked) over the full n bits, left in u2[0, N32) with the
@@ -124,7 +168,7 @@ __device__ __forceinline__ uint32_t rm_codeword_word(uint32_t B, int t) {
 // to hold distinct positions < n (drawn by the sampler), so the product
 // takes the unmasked two-entries-per-pass path.
 template <int LEVEL, bool CMP, bool VALID>
-__global__ void __launch_bounds__(ENC_THREADS) k_encrypt(int64_t count, const uint64_t* __restrict__ h,
+__global__ void __launch_bounds__(EncBound<LEVEL>::threads, 1) k_encrypt(int64_t count, const uint64_t* __restrict__ h,
                                                         const uint64_t* __restrict__ s, int64_t nkeys,
                                                         const int32_t* __restrict__ key_idx,
                                                         const uint8_t* __restrict__ m, const uint32_t* __restrict__ r1,
@@ -136,24 +180,18 @@ __global__ void __launch_bounds__(ENC_THREADS) k_encrypt(int64_t count, const ui
   constexpr int NR = LV::NR, n1 = LV::n1, k = LV::k;
   constexpr int WARP_W = LV::U2W_FULL + LV::WP_R;
   constexpr int NX = cdiv(NR, 32);
-  constexpr RsGenLog<NR> GL{};
   extern __shared__ __align__(16) uint8_t smem[];
-  gf_tables_init(smem, threadIdx.x, blockDim.x);
+  enc_gf_init(smem, threadIdx.x);
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const GF gf(smem, lane);
-  uint32_t* u2 = reinterpret_cast<uint32_t*>(smem + GF_TABLE_BYTES) + warp * WARP_W;
+  const uint8_t* gex = smem;
+  const uint16_t* glg = reinterpret_cast<const uint16_t*>(smem + 512);
+  uint32_t* u2 = reinterpret_cast<uint32_t*>(smem + ENC_GF_BYTES) + warp * WARP_W;
   uint32_t* sup = u2 + LV::U2W_FULL;
   // log g_c of the parity coefficients c = lane + 32 x this lane owns
   uint32_t lgc[NX];
 #pragma unroll
-  for (int x = 0; x < NX; x++) {
-    uint32_t val = 511u;
-#pragma unroll
-    for (int c = 0; c < NR; c++)
-      if (c == lane + 32 * x) val = GL.lg[c];
-    lgc[x] = val;
-  }
+  for (int x = 0; x < NX; x++) lgc[x] = rs_gen_log_select<NR>(lane + 32 * x, std::make_integer_sequence<int, NR>{});
   for (int64_t it = (int64_t)blockIdx.x * nw + warp; it < count; it += (int64_t)gridDim.x * nw) {
     const uint32_t ki = (uint32_t)key_idx[it];
     const int64_t key = ki < (uint64_t)nkeys ? (int64_t)ki : 0;
@@ -199,7 +237,7 @@ __global__ void __launch_bounds__(ENC_THREADS) k_encrypt(int64_t count, const ui
     const uint8_t* mrow = m + it * k;
     for (int i = k - 1; i >= 0; i--) {
       const uint32_t top = __shfl_sync(FULL_MASK, par[(NR - 1) / 32], (NR - 1) % 32);
-      const uint32_t lfb = gf.log((uint32_t)mrow[i] ^ top);
+      const uint32_t lfb = glg[(uint32_t)mrow[i] ^ top];
       uint32_t nxt[NX];
 #pragma unroll
       for (int x = 0; x < NX; x++) {
@@ -207,7 +245,7 @@ __global__ void __launch_bounds__(ENC_THREADS) k_encrypt(int64_t count, const ui
         const uint32_t carry = x > 0 ? __shfl_sync(FULL_MASK, par[x > 0 ? x - 1 : 0], 31) : 0u;
         const int c = lane + 32 * x;
         const uint32_t prev = lane == 0 ? carry : up;
-        nxt[x] = c < NR ? (prev ^ gf.mul_l(lgc[x], lfb)) : 0u;
+        nxt[x] = c < NR ? (prev ^ (uint32_t)gex[min(lgc[x] + lfb, GF_LOG_ZERO)]) : 0u;
       }
 #pragma unroll
       for (int x = 0; x < NX; x++) par[x] = nxt[x];
@@ -263,21 +301,26 @@ static cudaError_t encrypt_level(int64_t count, const uint64_t* h, const uint64_
                                  cudaStream_t st) {
   using LV = Level<LEVEL>;
   if (count == 0) return cudaSuccess;
-  constexpr int wpb = ENC_THREADS / 32;
   auto kern = k_encrypt<LEVEL, CMP, VALID>;
-  const size_t sm = GF_TABLE_BYTES + (size_t)wpb * (LV::U2W_FULL + LV::WP_R) * 4;
-  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (err != cudaSuccess) return err;
-  int dev = 0, sms = 0, occ = 0;
+  int dev = 0, sms = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, ENC_THREADS, sm);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  constexpr size_t per_warp = (size_t)(LV::U2W_FULL + LV::WP_R) * 4;
+  int wpb = (int)((optin - ENC_GF_BYTES) / per_warp);
+  if (wpb > EncBound<LEVEL>::threads / 32) wpb = EncBound<LEVEL>::threads / 32;
+  if (wpb < 1) return cudaErrorInvalidConfiguration;
+  const size_t sm = ENC_GF_BYTES + (size_t)wpb * per_warp;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (err != cudaSuccess) return err;
+  int occ = 0;
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, wpb * 32, sm);
   if (err != cudaSuccess) return err;
   if (occ < 1) return cudaErrorInvalidConfiguration;
   int64_t grid = (int64_t)sms * occ;
   const int64_t need = (count + wpb - 1) / wpb;
   if (need < grid) grid = need;
-  kern<<<(unsigned)grid, ENC_THREADS, sm, st>>>(count, h, s, nkeys, ki, m, r1, r2, e, u, v, u_in, v_in, ok);
+  kern<<<(unsigned)grid, wpb * 32, sm, st>>>(count, h, s, nkeys, ki, m, r1, r2, e, u, v, u_in, v_in, ok);
   return cudaGetLastError();
 }
 

@@ -127,3 +127,17 @@ def test_kem_argument_checks_without_a_gpu():
     assert lib.hqc_kem_decaps(1, 0, N, N, N, N, N, N, N, N, N, N, N, 0, N) == 0
     assert lib.hqc_kem_decaps(1, 5, N, N, N, N, N, N, N, N, N, N, N, 0, N) == -1
     assert b"keys" in lib.hqc_last_error()
+
+
+def test_kem_host_pipeline_argument_checks():
+    lib = hqc.load()
+    N = None
+    for level in (1, 3, 5):
+        p = hqc.hqc_get_params(level)
+        b = hqc.hqc_kem_host_workspace_bytes(level, 100)
+        assert b >= 2 * (100 * ((p.W_u_pitch + p.W_v) * 8 + 4 + 16 + 32 + 4) + hqc.hqc_kem_workspace_bytes(level, 100))
+    assert hqc.hqc_kem_host_workspace_bytes(1, 0) == 0
+    assert lib.hqc_kem_decaps_host(1, 0, N, N, N, N, N, N, N, N, N, N, 0, N, 0, N) == 0
+    assert lib.hqc_kem_decaps_host(1, 4, N, N, N, N, N, N, N, N, N, N, 0, N, 0, N) == -1
+    assert b"NULL" in lib.hqc_last_error()
+    assert lib.hqc_kem_decaps_host(4, 4, N, N, N, N, N, N, N, N, N, N, 0, N, 0, N) == -1

@@ -142,3 +142,29 @@ def test_kem_full_size_roundtrip_sampled(hqc):
     assert (host_u64(u)[idx] == ou).all() and (host_u64(v)[idx] == ov).all()
     assert (K.cpu().numpy()[idx] == oK).all()
     keys.free()
+
+
+@pytest.mark.parametrize("level", LEVELS)
+def test_decaps_from_host_buffers_matches_device_path(hqc, level):
+    """Chunked host-buffer decapsulation (ragged last chunk, one-item chunks,
+    one chunk larger than the batch) against the oracle, with rejections."""
+    P, h, y, s, sigma, kidx, m, salt = _kem_setup(hqc, level, 3, 70, tag=1000 + 10 * level)
+    u, v, K = oracle.kem_encaps(level, h, s, kidx, m, salt)
+    v[::4, 2] ^= np.uint64(1 << 3)  # a quarter rejected
+    oK, ook = oracle.kem_decaps(level, h, s, y, sigma, kidx, u, v, salt)
+    keys = hqc.Keyset(level, y)
+    hd, sd, sig = cu64(h), cu64(s), cu8(sigma)
+    u_h = torch.from_numpy(u.view(np.int64).copy()).pin_memory()
+    v_h = torch.from_numpy(v.view(np.int64).copy()).pin_memory()
+    k_h = torch.from_numpy(kidx.astype(np.int32)).pin_memory()
+    s_h = torch.from_numpy(salt.copy()).pin_memory()
+    for chunk in (1, 16, 32, 100):
+        ws = torch.empty(hqc.hqc_kem_host_workspace_bytes(level, chunk), dtype=torch.uint8, device="cuda")
+        K_h, ok_h = hqc.hqc_kem_decaps_host(level, keys, hd, sd, sig, k_h, u_h, v_h, s_h, chunk=chunk, workspace=ws)
+        torch.cuda.current_stream().synchronize()
+        assert (K_h.numpy() == oK).all(), chunk
+        assert (ok_h.numpy().astype(bool) == ook).all(), chunk
+    short = torch.empty(hqc.hqc_kem_host_workspace_bytes(level, 64) - 16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(hqc.HqcError):
+        hqc.hqc_kem_decaps_host(level, keys, hd, sd, sig, k_h, u_h, v_h, s_h, chunk=64, workspace=short)
+    keys.free()
