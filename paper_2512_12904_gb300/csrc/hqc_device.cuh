@@ -411,42 +411,56 @@ __device__ __forceinline__ void rs_decode_seg(const GF& gf, uint32_t* rs, const 
   for (int j = sl; j < 64; j += SEG) logS[j - 64] = (uint16_t)GF_LOG_ZERO;
   __syncwarp();
 
-  // syndromes: lane owns i = sl + 1 + SEG s
+  // syndromes: lane owns i = sl + 1 + SEG s; each log r_j is loaded once
+  // for all of the lane's syndromes
   constexpr int NS = cdiv(NR, SEG);
+  {
+    uint32_t acc[NS], e[NS];
 #pragma unroll
-  for (int s = 0; s < NS; s++) {
-    const uint32_t i = (uint32_t)(sl + 1 + SEG * s);
-    uint32_t acc = 0, e = 0;
+    for (int s = 0; s < NS; s++) acc[s] = e[s] = 0;
 #pragma unroll 2
     for (int j = 0; j < n1; j++) {
-      acc ^= gf.exp(min((uint32_t)logr[j] + e, GF_LOG_ZERO));
-      e += i;
-      e = e >= 255u ? e - 255u : e;
+      const uint32_t lr = logr[j];
+#pragma unroll
+      for (int s = 0; s < NS; s++) {
+        acc[s] ^= gf.exp(min(lr + e[s], GF_LOG_ZERO));
+        e[s] += (uint32_t)(sl + 1 + SEG * s);
+        e[s] = e[s] >= 255u ? e[s] - 255u : e[s];
+      }
     }
-    if (i <= (uint32_t)NR) {
-      logS[i - 1] = (uint16_t)gf.log(acc);
-      if (ALL_POS && active) dbg->S[i - 1] = (uint8_t)acc;
+#pragma unroll
+    for (int s = 0; s < NS; s++) {
+      const uint32_t i = (uint32_t)(sl + 1 + SEG * s);
+      if (i <= (uint32_t)NR) {
+        logS[i - 1] = (uint16_t)gf.log(acc[s]);
+        if (ALL_POS && active) dbg->S[i - 1] = (uint8_t)acc[s];
+      }
     }
   }
   __syncwarp();
 
-  // Berlekamp-Massey; lane owns coefficient c = sl + SEG x
+  // Berlekamp-Massey; lane owns coefficient c = sl + SEG x.  x^m B is only
+  // ever multiplied, so it is carried in log form (lbp, 511 = zero): it
+  // shifts with the same shuffles and, when replaced by Lambda, takes the
+  // logs of Lambda already computed for the discrepancy.
   constexpr int NC = cdiv(CAP, SEG);
-  uint32_t lam[NC], bp[NC];
+  uint32_t lam[NC], lbp[NC];
 #pragma unroll
   for (int x = 0; x < NC; x++) {
     const int c = sl + SEG * x;
     lam[x] = c == 0;
-    bp[x] = c == 1;  // x^m B with m = 1, B = 1
+    lbp[x] = c == 1 ? 0u : GF_LOG_ZERO;  // x^m B with m = 1, B = 1
   }
   uint32_t lb = 0, L = 0;  // log b (b = 1), LFSR length
 #pragma unroll 1
   for (int rr = 0; rr < NR; rr++) {
+    uint32_t llam[NC];
     uint32_t part = 0;
 #pragma unroll
     for (int x = 0; x < NC; x++) {
       const int c = sl + SEG * x;  // rr - c >= -64: padding covers c > rr
-      part ^= gf.mul_l(gf.log(lam[x]), logS[rr - c]);
+      llam[x] = gf.log(lam[x]);
+      part ^= gf.mul_l(llam[x], logS[rr - c]);
     }
 #pragma unroll
     for (int o = SEG / 2; o > 0; o >>= 1) part ^= __shfl_xor_sync(FULL_MASK, part, o, SEG);
@@ -457,16 +471,15 @@ __device__ __forceinline__ void rs_decode_seg(const GF& gf, uint32_t* rs, const 
     uint32_t src[NC];
 #pragma unroll
     for (int x = 0; x < NC; x++) {
-      const uint32_t T = lam[x];
-      lam[x] = T ^ gf.mul_l(lcoef, gf.log(bp[x]));
-      src[x] = sel(cond, T, bp[x]);
+      lam[x] ^= gf.mul_l(lcoef, lbp[x]);
+      src[x] = sel(cond, llam[x], lbp[x]);
     }
 #pragma unroll
     for (int x = 0; x < NC; x++) {
       const uint32_t up = __shfl_up_sync(FULL_MASK, src[x], 1, SEG);
-      const uint32_t carry = x > 0 ? __shfl_sync(FULL_MASK, src[x > 0 ? x - 1 : 0], SEG - 1, SEG) : 0u;
+      const uint32_t carry = x > 0 ? __shfl_sync(FULL_MASK, src[x > 0 ? x - 1 : 0], SEG - 1, SEG) : GF_LOG_ZERO;
       const uint32_t nb = sl == 0 ? carry : up;
-      bp[x] = (sl + SEG * x) < CAP ? nb : 0u;
+      lbp[x] = (sl + SEG * x) < CAP ? nb : GF_LOG_ZERO;
     }
     lb = sel(cond, ld, lb);
     L = sel(cond, (uint32_t)rr + 1u - L, L);
