@@ -58,3 +58,42 @@ def test_fused_time_does_not_depend_on_the_data(hqc, level):
     keys.free()
     spread = max(times.values()) / min(times.values())
     assert spread < 1.05, times
+
+
+@pytest.mark.parametrize("level", [1, 5])
+def test_decapsulation_time_does_not_depend_on_acceptance(hqc, level):
+    """Implicit rejection must not show in the running time: batches that
+    are all accepted, all rejected (tampered v) and all garbage take the
+    same time."""
+    cnt, nkeys = (16384, 64) if level == 1 else (4096, 32)
+    P = hqc.hqc_get_params(level)
+
+    def rows(n, width, tag):
+        nw = (n * width + 7) // 8 + 1
+        a = synth.words(nw, tag=tag).view(np.uint8)[:n * width].reshape(n, width).copy()
+        return torch.from_numpy(a).cuda()
+
+    h, x, y, s = hqc.hqc_kem_keygen(level, rows(nkeys, 32, 51), rows(nkeys, 32, 52))
+    sigma = rows(nkeys, P.k, 53)
+    kidx = torch.from_numpy(synth.key_assignment(cnt, nkeys, tag=54)).cuda()
+    m, salt = rows(cnt, P.k, 55), rows(cnt, 16, 56)
+    u, v, K = hqc.hqc_kem_encaps(level, h, s, kidx, m, salt)
+    keys = hqc.Keyset(level, y.cpu().numpy().view(np.uint32))
+    v_bad = v.clone()
+    v_bad[:, 0] ^= 1 << 13
+    g_u = torch.from_numpy(synth.words(u.numel(), tag=57).view(np.int64).reshape(tuple(u.shape))).cuda()
+    g_v = torch.from_numpy(synth.words(v.numel(), tag=58).view(np.int64).reshape(tuple(v.shape))).cuda()
+    ws = torch.empty(hqc.hqc_kem_workspace_bytes(level, cnt), dtype=torch.uint8, device="cuda")
+    Kd = torch.empty_like(K)
+    ok = torch.empty((cnt,), dtype=torch.int32, device="cuda")
+    times, accepted = {}, {}
+    for name, (uu, vv) in {"accept": (u, v), "reject": (u, v_bad), "garbage": (g_u, g_v)}.items():
+        run = lambda: hqc.hqc_kem_decaps(level, keys, h, s, sigma, kidx, uu, vv, salt, Kd, ok, workspace=ws)
+        for _ in range(3):
+            run()
+        times[name] = _median_ms(run)
+        accepted[name] = int(ok.sum().item())
+    keys.free()
+    assert accepted == {"accept": cnt, "reject": 0, "garbage": 0}, accepted
+    spread = max(times.values()) / min(times.values())
+    assert spread < 1.05, times
