@@ -200,6 +200,20 @@ int hqc_kem_decaps(int level, int64_t count, const hqc_keyset_t* keys, const uin
                    const uint8_t* salt, uint8_t* K_out, uint32_t* ok_out, void* workspace, size_t workspace_bytes,
                    void* stream);
 
+/* Decapsulation from host buffers with uploads overlapped with the kernels,
+ * as hqc_decrypt_host_keyed does for decryption: key_idx_host, u_host,
+ * v_host, salt_host are HOST memory (pinned for overlap), K_host
+ * [count][32] and ok_host ([count], may be NULL) receive the results; h,
+ * s, sigma and keys are the device-resident key material of
+ * hqc_kem_decaps.  workspace: device memory of at least
+ * hqc_kem_host_workspace_bytes(level, chunk) bytes; chunk <= 0 lets the
+ * library choose, bounded by the workspace. */
+size_t hqc_kem_host_workspace_bytes(int level, int64_t chunk);
+int hqc_kem_decaps_host(int level, int64_t count, const hqc_keyset_t* keys, const uint64_t* h, const uint64_t* s,
+                        const uint8_t* sigma, const int32_t* key_idx_host, const uint64_t* u_host,
+                        const uint64_t* v_host, const uint8_t* salt_host, uint8_t* K_host, uint32_t* ok_host,
+                        int64_t chunk, void* workspace, size_t workspace_bytes, void* stream);
+
 /* Every intermediate of Algorithm 2, per ciphertext (device arrays):
  *   t    [count][W_v]  u*y truncated to n1*n2 bits
  *   w    [count][W_v]  v + t
@@ -247,6 +261,21 @@ size_t hqc_mixed_workspace_bytes(void);
 int hqc_decrypt_mixed(int64_t count, const hqc_item_t* items, const uint64_t* arena, int64_t arena_words,
                       const hqc_keyset_t* const keys[3], uint8_t* m_arena, int64_t m_bytes, void* workspace,
                       size_t workspace_bytes, void* stream);
+
+/* Mixed-level decryption from host buffers with uploads overlapped with the
+ * kernels.  items_host, arena_host (HOST memory, pinned for overlap) as for
+ * hqc_decrypt_mixed, with the items in arena order: u_off and m_off
+ * non-decreasing, so each chunk's rows and m bytes are one contiguous range
+ * (HQC_EINVAL otherwise).  Per chunk (chunk <= 0: about four) the records
+ * and the arena range go up, a one-block kernel groups the records by
+ * level, one persistent kernel per level decrypts, and the chunk's m range
+ * comes back to m_host; m bytes that no valid item writes are set to zero.
+ * workspace: device memory of at least hqc_mixed_host_workspace_bytes(count,
+ * items_host, chunk) bytes (0 on bad arguments). */
+size_t hqc_mixed_host_workspace_bytes(int64_t count, const hqc_item_t* items_host, int64_t chunk);
+int hqc_decrypt_mixed_host(int64_t count, const hqc_item_t* items_host, const uint64_t* arena_host,
+                           int64_t arena_words, const hqc_keyset_t* const keys[3], uint8_t* m_host, int64_t m_bytes,
+                           int64_t chunk, void* workspace, size_t workspace_bytes, void* stream);
 
 /* Launch shape of the persistent kernels: warps per block and blocks per
  * SM (0 = the library's default).  level 1/3/5 sets the single-level

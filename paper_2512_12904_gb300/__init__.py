@@ -25,7 +25,8 @@ __all__ = [
     "hqc_encrypt_batch", "LEVELS", "Plan", "hqc_plan_create_keyed", "hqc_plan_create_mixed", "hqc_serve_run",
     "SERVE_STATUS", "hqc_decrypt_host_keyed", "hqc_host_workspace_bytes", "hqc_shake256_batch",
     "hqc_kem_keygen", "hqc_kem_workspace_bytes", "hqc_kem_encaps", "hqc_kem_decaps",
-    "hqc_kem_host_workspace_bytes", "hqc_kem_decaps_host",
+    "hqc_kem_host_workspace_bytes", "hqc_kem_decaps_host", "hqc_mixed_host_workspace_bytes",
+    "hqc_decrypt_mixed_host",
 ]
 
 LEVELS = (1, 3, 5)
@@ -99,6 +100,8 @@ def load(build_if_missing: bool = True):
             "hqc_kem_encaps": (i32, [i32, i64, P, P, i64, P, P, P, P, P, P, P, sz, P]),
             "hqc_kem_decaps": (i32, [i32, i64, P, P, P, P, P, P, P, P, P, P, P, sz, P]),
             "hqc_kem_host_workspace_bytes": (sz, [i32, i64]),
+            "hqc_mixed_host_workspace_bytes": (sz, [i64, P, i64]),
+            "hqc_decrypt_mixed_host": (i32, [i64, P, P, i64, P, P, i64, i64, P, sz, P]),
             "hqc_kem_decaps_host": (i32, [i32, i64, P, P, P, P, P, P, P, P, P, P, i64, P, sz, P]),
             "hqc_keygen_batch": (i32, [i32, i64, P, P, P, P, P]),
             "hqc_encrypt_batch": (i32, [i32, i64, P, P, i64, P, P, P, P, P, P, P, P]),
@@ -688,3 +691,40 @@ def hqc_kem_decaps_host(level, keys: Keyset, h, s, sigma, key_idx_host, u_host, 
                                       int(chunk), _dev_ptr(workspace, torch.uint8, None, "workspace"),
                                       workspace.numel(), _stream(stream)))
     return K_host, ok_host
+
+
+def _host_u8(t, name):
+    torch = _torch()
+    if t.is_cuda or not t.is_contiguous() or t.dtype != torch.uint8:
+        raise ValueError("%s must be a contiguous CPU uint8 tensor" % name)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def hqc_mixed_host_workspace_bytes(items_host, chunk: int = 0) -> int:
+    """Device workspace for hqc_decrypt_mixed_host over these (host) items."""
+    cnt = items_host.numel() // ITEM_DTYPE.itemsize
+    return int(load().hqc_mixed_host_workspace_bytes(cnt, _host_u8(items_host, "items_host"), int(chunk)))
+
+
+def hqc_decrypt_mixed_host(items_host, arena_host, keys, m_host, chunk=0, workspace=None, stream=None):
+    """Mixed-level decryption from (pinned) HOST tensors: items_host (uint8
+    view of ITEM_DTYPE records, in arena order), arena_host (int64 words),
+    m_host (uint8); workspace a CUDA uint8 tensor (allocated here when
+    None).  m_host is valid once the stream reaches the end of the call."""
+    torch = _torch()
+    cnt = items_host.numel() // ITEM_DTYPE.itemsize
+    arena_host = _as_u64(arena_host)
+    if arena_host.is_cuda or not arena_host.is_contiguous():
+        raise ValueError("arena_host must be a contiguous CPU tensor")
+    if workspace is None:
+        need = hqc_mixed_host_workspace_bytes(items_host, chunk)
+        if need == 0:
+            raise ValueError("items are not in arena order or reach past the arena")
+        workspace = torch.empty(need, dtype=torch.uint8, device="cuda")
+    karr = (ctypes.c_void_p * 3)(*[(k.handle if k is not None else None) for k in keys])
+    _check(load().hqc_decrypt_mixed_host(cnt, _host_u8(items_host, "items_host"),
+                                         ctypes.c_void_p(arena_host.data_ptr()), arena_host.numel(), karr,
+                                         _host_u8(m_host, "m_host"), m_host.numel(), int(chunk),
+                                         _dev_ptr(workspace, torch.uint8, None, "workspace"), workspace.numel(),
+                                         _stream(stream)))
+    return m_host

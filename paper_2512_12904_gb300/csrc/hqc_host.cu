@@ -12,7 +12,9 @@
 
 #include <cstdarg>
 #include <cstdio>
+#include <cstdint>
 #include <mutex>
+#include <vector>
 
 #include "../../include/hqc_gb300.h"
 #include "hqc_internal.h"
@@ -257,4 +259,195 @@ extern "C" int hqc_kem_decaps_host(int level, int64_t count, const hqc_keyset_t*
     return rc_kem;
   }
   return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Mixed-level batches from host buffers.  Each chunk's item records and the
+// arena range its rows span go up on the copy stream; on the compute stream
+// a one-block kernel groups the chunk's records by level, then one
+// persistent kernel per level decrypts its items, and the chunk's m range
+// comes back.  The device slot holds the arena range at the same offsets as
+// the host arena minus the chunk's first row, so the records need no
+// rewriting: the kernels get an arena pointer moved back by that amount.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kGroupThreads = 1024;
+
+__global__ void __launch_bounds__(kGroupThreads) k_group_items(const hqc::MixedItem* __restrict__ in, int64_t n,
+                                                              int64_t s0, int64_t s1, int64_t s2,
+                                                              hqc::MixedItem* __restrict__ out) {
+  __shared__ unsigned int cnt[3];
+  if (threadIdx.x < 3) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t start[3] = {s0, s1, s2};
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const hqc::MixedItem it = in[i];
+    const int li = it.level == 1 ? 0 : it.level == 3 ? 1 : it.level == 5 ? 2 : -1;
+    if (li < 0) continue;
+    const unsigned int pos = atomicAdd(&cnt[li], 1u);
+    out[start[li] + pos] = it;
+  }
+}
+
+struct MixedChunk {
+  int64_t first, n, base, words, mbase, mbytes, cnt[3];
+};
+
+// Scan the items once: order checks, per-chunk ranges and level counts.
+int mixed_chunks(int64_t count, const hqc_item_t* items, int64_t arena_words, int64_t m_bytes, int64_t chunk,
+                 std::vector<MixedChunk>* out) {
+  hqc_params_t prm[3];
+  for (int li = 0; li < 3; li++) hqc_get_params(li == 0 ? 1 : li == 1 ? 3 : 5, &prm[li]);
+  out->clear();
+  for (int64_t first = 0; first < count; first += chunk) {
+    MixedChunk c{};
+    c.first = first;
+    c.n = count - first < chunk ? count - first : chunk;
+    c.base = items[first].u_off & ~(int64_t)1;
+    c.mbase = items[first].m_off;
+    int64_t end = c.base, mend = c.mbase;
+    for (int64_t i = first; i < first + c.n; i++) {
+      const hqc_item_t& it = items[i];
+      if (i > 0 && (it.u_off < items[i - 1].u_off || it.m_off < items[i - 1].m_off))
+        return hfail(HQC_EINVAL, "item %lld: items must be in arena order (u_off and m_off non-decreasing)",
+                     (long long)i);
+      const int li = hqc::level_index(it.level);
+      if (li < 0) continue;  // skipped by the kernels, as in hqc_decrypt_mixed
+      if (it.u_off < c.base || it.v_off < c.base || it.m_off < c.mbase)
+        return hfail(HQC_EINVAL, "item %lld: rows before the item's own chunk", (long long)i);
+      c.cnt[li]++;
+      const int64_t e1 = it.u_off + prm[li].W_u_pitch, e2 = it.v_off + prm[li].W_v, e3 = it.m_off + prm[li].k;
+      end = e1 > end ? e1 : end;
+      end = e2 > end ? e2 : end;
+      mend = e3 > mend ? e3 : mend;
+    }
+    if (end > arena_words || mend > m_bytes) return hfail(HQC_EINVAL, "items reach past the arena or m");
+    c.words = end - c.base;
+    c.mbytes = mend - c.mbase;
+    out->push_back(c);
+  }
+  return HQC_OK;
+}
+
+struct MixedSlot {
+  size_t words, items, grouped, m, total;
+};
+
+MixedSlot mixed_slot(int64_t chunk, int64_t max_words, int64_t max_m) {
+  MixedSlot s;
+  s.words = r16((size_t)max_words * 8);
+  s.items = r16((size_t)chunk * sizeof(hqc::MixedItem));
+  s.grouped = s.items;
+  s.m = r16((size_t)max_m);
+  s.total = s.words + s.items + s.grouped + s.m;
+  return s;
+}
+
+int64_t default_mixed_chunk(int64_t count) {
+  // about four chunks, each at least one HQC-1 wave of the persistent grid
+  int64_t wave = 0;
+  if (hqc::fused_wave(1, true, hqc::level_cfg(1), &wave) != cudaSuccess || wave <= 0) wave = 8192;
+  int64_t c = (count + 3) / 4;
+  return c < wave ? (count < wave ? count : wave) : c;
+}
+
+}  // namespace
+
+extern "C" size_t hqc_mixed_host_workspace_bytes(int64_t count, const hqc_item_t* items_host, int64_t chunk) {
+  if (count <= 0 || !items_host) return 0;
+  if (chunk <= 0) chunk = default_mixed_chunk(count);
+  std::vector<MixedChunk> cs;
+  if (mixed_chunks(count, items_host, INT64_MAX / 4, INT64_MAX / 4, chunk, &cs) != HQC_OK) return 0;
+  int64_t mw = 0, mm = 0;
+  for (const auto& c : cs) {
+    mw = c.words > mw ? c.words : mw;
+    mm = c.mbytes > mm ? c.mbytes : mm;
+  }
+  return 2 * mixed_slot(chunk, mw, mm).total;
+}
+
+extern "C" int hqc_decrypt_mixed_host(int64_t count, const hqc_item_t* items_host, const uint64_t* arena_host,
+                                      int64_t arena_words, const hqc_keyset_t* const keys[3], uint8_t* m_host,
+                                      int64_t m_bytes, int64_t chunk, void* workspace, size_t workspace_bytes,
+                                      void* stream) {
+  if (count < 0) return hfail(HQC_EINVAL, "count must be >= 0");
+  if (count == 0) return HQC_OK;
+  if (!items_host || !arena_host || !keys || !m_host || !workspace) return hfail(HQC_EINVAL, "NULL argument");
+  if ((uintptr_t)workspace % 16) return hfail(HQC_EINVAL, "workspace must be 16-byte aligned");
+  for (int li = 0; li < 3; li++)
+    if (keys[li] && keys[li]->level != (li == 0 ? 1 : li == 1 ? 3 : 5))
+      return hfail(HQC_EINVAL, "keys[%d] registered for another level", li);
+  if (chunk <= 0) chunk = default_mixed_chunk(count);
+  std::vector<MixedChunk> cs;
+  int rc = mixed_chunks(count, items_host, arena_words, m_bytes, chunk, &cs);
+  if (rc != HQC_OK) return rc;
+  int64_t mw = 0, mm = 0;
+  for (const auto& c : cs) {
+    mw = c.words > mw ? c.words : mw;
+    mm = c.mbytes > mm ? c.mbytes : mm;
+  }
+  const MixedSlot M = mixed_slot(chunk, mw, mm);
+  if (2 * M.total > workspace_bytes)
+    return hfail(HQC_ENOMEM, "workspace has %zu bytes, needs %zu", workspace_bytes, 2 * M.total);
+  // the generic driver's slot layout carries only sizes here
+  SlotLayout L{};
+  L.total = M.total;
+  auto parts = [&](const Slot& s, uint64_t** w, hqc::MixedItem** raw, hqc::MixedItem** grouped, uint8_t** m) {
+    char* b = reinterpret_cast<char*>(s.u);  // slot base
+    *w = reinterpret_cast<uint64_t*>(b);
+    *raw = reinterpret_cast<hqc::MixedItem*>(b + M.words);
+    *grouped = reinterpret_cast<hqc::MixedItem*>(b + M.words + M.items);
+    *m = reinterpret_cast<uint8_t*>(b + M.words + M.items + M.grouped);
+  };
+  auto chunk_of = [&](int64_t first) -> const MixedChunk& { return cs[(size_t)(first / chunk)]; };
+  auto up = [&](int64_t first, int64_t, const Slot& s, cudaStream_t st) {
+    const MixedChunk& c = chunk_of(first);
+    uint64_t* w;
+    hqc::MixedItem *raw, *grouped;
+    uint8_t* m;
+    parts(s, &w, &raw, &grouped, &m);
+    cudaError_t e = h2d(w, arena_host + c.base, (size_t)c.words * 8, st);
+    if (e == cudaSuccess) e = h2d(raw, items_host + c.first, (size_t)c.n * sizeof(hqc::MixedItem), st);
+    return e;
+  };
+  auto comp = [&](int64_t first, int64_t, const Slot& s, cudaStream_t st) {
+    const MixedChunk& c = chunk_of(first);
+    uint64_t* w;
+    hqc::MixedItem *raw, *grouped;
+    uint8_t* m;
+    parts(s, &w, &raw, &grouped, &m);
+    const int64_t s1 = c.cnt[0], s2 = c.cnt[0] + c.cnt[1];
+    // m bytes no valid item writes come back as zero
+    cudaError_t e = cudaMemsetAsync(m, 0, (size_t)c.mbytes, st);
+    if (e != cudaSuccess) return e;
+    k_group_items<<<1, kGroupThreads, 0, st>>>(raw, c.n, 0, s1, s2, grouped);
+    e = cudaGetLastError();
+    const int64_t start[3] = {0, s1, s2};
+    for (int li = 0; li < 3 && e == cudaSuccess; li++) {
+      if (c.cnt[li] == 0 || !keys[li]) continue;
+      hqc::MixedArgs a;
+      a.count = c.cnt[li];
+      a.items = grouped + start[li];
+      a.arena = w - c.base;  // record offsets are absolute in the host arena
+      a.arena_words = c.base + c.words;
+      for (int k = 0; k < 3; k++) {
+        a.keys[k] = keys[k] ? keys[k]->d_table : nullptr;
+        a.nkeys[k] = keys[k] ? keys[k]->nkeys : 0;
+      }
+      a.m = m - c.mbase;
+      a.m_bytes = c.mbase + c.mbytes;
+      e = hqc::launch_items(li == 0 ? 1 : li == 1 ? 3 : 5, a, 0, st, hqc::LaunchCfg{});
+    }
+    return e;
+  };
+  auto down = [&](int64_t first, int64_t, const Slot& s, cudaStream_t st) {
+    const MixedChunk& c = chunk_of(first);
+    uint64_t* w;
+    hqc::MixedItem *raw, *grouped;
+    uint8_t* m;
+    parts(s, &w, &raw, &grouped, &m);
+    return cudaMemcpyAsync(m_host + c.mbase, m, (size_t)c.mbytes, cudaMemcpyDeviceToHost, st);
+  };
+  return run_pipeline(count, chunk, workspace, L, stream, up, comp, down);
 }

@@ -141,3 +141,22 @@ def test_kem_host_pipeline_argument_checks():
     assert lib.hqc_kem_decaps_host(1, 4, N, N, N, N, N, N, N, N, N, N, 0, N, 0, N) == -1
     assert b"NULL" in lib.hqc_last_error()
     assert lib.hqc_kem_decaps_host(4, 4, N, N, N, N, N, N, N, N, N, N, 0, N, 0, N) == -1
+
+
+def test_mixed_host_pipeline_order_checks_on_the_host():
+    lib = hqc.load()
+    items = np.zeros(4, dtype=hqc.ITEM_DTYPE)
+    P1 = hqc.hqc_get_params(1)
+    row = P1.W_u_pitch + P1.W_v
+    for i in range(4):
+        items[i] = (1, 0, i * row, i * row + P1.W_u_pitch, i * P1.k)
+    import torch
+    t = torch.from_numpy(items.view(np.uint8).copy())
+    b = hqc.hqc_mixed_host_workspace_bytes(t, chunk=2)
+    assert b >= 2 * (2 * row * 8 + 2 * 2 * 32 + 2 * P1.k)
+    bad = items.copy()
+    bad[[1, 2]] = bad[[2, 1]]
+    assert hqc.hqc_mixed_host_workspace_bytes(torch.from_numpy(bad.view(np.uint8).copy()), chunk=2) == 0
+    N = None
+    assert lib.hqc_decrypt_mixed_host(0, N, N, 0, N, N, 0, 0, N, 0, N) == 0
+    assert lib.hqc_decrypt_mixed_host(3, N, N, 0, N, N, 0, 0, N, 0, N) == -1

@@ -285,3 +285,52 @@ def test_host_pipelined_matches_oracle(hqc, level):
     with pytest.raises(hqc.HqcError):
         hqc.hqc_decrypt_host_keyed(level, u_h, v_h, keys, k_h, chunk=64, workspace=short)
     keys.free()
+
+
+def test_mixed_from_host_buffers(hqc):
+    """Chunked mixed-level decryption from pinned host buffers: chunks that
+    split levels unevenly, a ragged last chunk, an item skipped for its key
+    (its m bytes come back zero), and a batch out of arena order refused."""
+    parts = {}
+    for lvl, cnt in ((1, 40), (3, 35), (5, 25)):
+        parts[lvl] = honest(lvl, 8, cnt, first_ct=21000, tag=13)
+    order = synth.shuffle(np.arange(100, dtype=np.int32), tag=14)
+    seq = [(1, i) for i in range(40)] + [(3, i) for i in range(35)] + [(5, i) for i in range(25)]
+    seq = [seq[j] for j in order]
+    items = np.zeros(len(seq), dtype=hqc.ITEM_DTYPE)
+    arena, m_off, words, want = [], 0, 0, []
+    for idx, (lvl, i) in enumerate(seq):
+        wl = parts[lvl]
+        items[idx] = (lvl, wl.key_idx[i], words, words + wl.P.W_u_pitch, m_off)
+        arena.append(wl.u[i]); arena.append(wl.v[i])
+        words += wl.P.W_u_pitch + wl.P.W_v
+        m_off += wl.P.k
+        want.append(wl.m[i])
+    want = np.concatenate(want)
+    arena_h = torch.from_numpy(np.concatenate(arena).view(np.int64)).pin_memory()
+    keys = [hqc.Keyset(l, parts[l].y) for l in (1, 3, 5)]
+    items_h = torch.from_numpy(items.view(np.uint8).copy()).pin_memory()
+    for chunk in (1, 7, 33, 100, 0):
+        m_h = torch.full((m_off,), 0xAA, dtype=torch.uint8).pin_memory()
+        hqc.hqc_decrypt_mixed_host(items_h, arena_h, keys, m_h, chunk=chunk)
+        torch.cuda.current_stream().synchronize()
+        assert (m_h.numpy() == want).all(), chunk
+    items2 = items.copy()
+    items2[5]["key"] = 10 ** 6
+    m_h = torch.full((m_off,), 0xAA, dtype=torch.uint8).pin_memory()
+    hqc.hqc_decrypt_mixed_host(torch.from_numpy(items2.view(np.uint8).copy()).pin_memory(), arena_h, keys, m_h,
+                               chunk=16)
+    torch.cuda.current_stream().synchronize()
+    g = m_h.numpy()
+    s5, k5 = int(items2[5]["m_off"]), parts[seq[5][0]].P.k
+    assert (g[s5:s5 + k5] == 0).all()
+    g[s5:s5 + k5] = want[s5:s5 + k5]
+    assert (g == want).all()
+    swapped = items.copy()
+    swapped[[3, 4]] = swapped[[4, 3]]
+    ws = torch.empty(1 << 24, dtype=torch.uint8, device="cuda")
+    with pytest.raises(hqc.HqcError):
+        hqc.hqc_decrypt_mixed_host(torch.from_numpy(swapped.view(np.uint8).copy()), arena_h, keys,
+                                   torch.zeros(m_off, dtype=torch.uint8), chunk=16, workspace=ws)
+    for k in keys:
+        k.free()
