@@ -18,7 +18,7 @@
  *                    RM(1,7) inner code; byte-parallel RM decoder
  *   Sec. III-D       RS syndromes S_i = sum_j c_j alpha^{i j}, i = 1..2*delta
  *
- * Readings where the paper is silent (they are listed in the design doc too):
+ * Readings where the paper is silent (the CUDA path follows the same list):
  *   A1 decrypt uses v - u*y (the paper prints u*s; y is the secret operand
  *      that cancels h: v - u*y = mG + x*r2 - r1*y + e).
  *   A2 v holds only the first n1*n2 bits; u*y is truncated the same way.
