@@ -119,13 +119,14 @@ def test_decaps_accept_and_reject_match_oracle(hqc, level):
     keys.free()
 
 
-def test_kem_full_size_roundtrip_sampled(hqc):
-    """65,536 HQC-1 items under 256 keys: every decapsulated K equals the
-    encapsulated one (a property at any size), and sampled items match the
-    oracle byte for byte."""
-    level, count, nkeys = 1, 65536, 256
+@pytest.mark.parametrize("level,count,nkeys", [(1, 65536, 256), (3, 32768, 128), (5, 32768, 128)])
+def test_kem_full_size_roundtrip_sampled(hqc, level, count, nkeys):
+    """The bench sizes (65,536 HQC-1 items under 256 keys, 32,768 HQC-3 and
+    HQC-5 items under 128): every decapsulated K equals the encapsulated one
+    (a property at any size), and sampled items match the oracle byte for
+    byte."""
     P = oracle.params(level)
-    sk, pk = _keys(level, nkeys, tag=900)
+    sk, pk = _keys(level, nkeys, tag=900 + level)
     h, x, y, s = hqc.hqc_kem_keygen(level, cu8(sk), cu8(pk))
     sigma = cu8(rows(nkeys, P.k, 902))
     kidx = cu32(synth.key_assignment(count, nkeys, tag=903))
@@ -135,7 +136,7 @@ def test_kem_full_size_roundtrip_sampled(hqc):
     keys = hqc.Keyset(level, y.cpu().numpy().view(np.uint32))
     Kd, ok = hqc.hqc_kem_decaps(level, keys, h, s, sigma, kidx, u, v, salt)
     assert bool(ok.all().item()) and bool((Kd == K).all().item())
-    idx = [0, 1, 4095, 31337, 65535]
+    idx = [0, 1, 4095, count // 2 + 7, count - 1]
     hh, ss, yy = host_u64(h), host_u64(s), y.cpu().numpy().view(np.uint32)
     ki = kidx.cpu().numpy()[idx]
     ou, ov, oK = oracle.kem_encaps(level, hh, ss, ki, m.cpu().numpy()[idx], salt.cpu().numpy()[idx])

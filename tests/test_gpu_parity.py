@@ -334,3 +334,29 @@ def test_mixed_from_host_buffers(hqc):
                                    torch.zeros(m_off, dtype=torch.uint8), chunk=16, workspace=ws)
     for k in keys:
         k.free()
+
+
+
+def test_host_pipelined_full_size_sampled(hqc):
+    """65,536 HQC-1 ciphertexts from pinned host buffers with the library's
+    own chunking (whole waves, two slots): every m equals the device path's,
+    and sampled items equal the oracle."""
+    level, count, nkeys = 1, 65536, 256
+    P = oracle.params(level)
+    S = synth.Shape.of(P)
+    h, x, y = synth.keys(S, nkeys, first=300)
+    s = oracle.keygen(level, h, x, y)
+    m, r1, r2, e = synth.ciphertext_randomness(S, count, first=400000)
+    kidx = synth.key_assignment(count, nkeys, tag=31)
+    hd, sd = u64(h), u64(s)
+    u_d, v_d = hqc.hqc_encrypt_batch(level, hd, sd, dev(kidx.astype(np.int32)), dev(m), i32(r1), i32(r2), i32(e))
+    keys = hqc.Keyset(level, y)
+    u_h, v_h = u_d.cpu().pin_memory(), v_d.cpu().pin_memory()
+    k_h = torch.from_numpy(kidx.astype(np.int32)).pin_memory()
+    m_h = hqc.hqc_decrypt_host_keyed(level, u_h, v_h, keys, k_h)
+    torch.cuda.current_stream().synchronize()
+    assert (m_h.numpy() == m).all()
+    idx = [0, 9727, 9728, 40000, count - 1]
+    want = oracle.decrypt(level, u_h.numpy()[idx].view(np.uint64), v_h.numpy()[idx].view(np.uint64), y[kidx[idx]])
+    assert (m_h.numpy()[idx] == want).all()
+    keys.free()
