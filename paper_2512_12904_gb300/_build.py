@@ -1,7 +1,8 @@
 """Build the CUDA library (libhqc_gb300.so) in-tree with nvcc for sm_103a.
 
-Three translation units are compiled in parallel and linked into one
-shared library with a plain C ABI (include/hqc_gb300.h).
+The translation units are compiled in parallel and linked into one shared
+library with a plain C ABI (include/hqc_gb300.h); the on-chip peak
+microbenchmarks go into a second one (libhqc_peaks.so).
 """
 from __future__ import annotations
 
@@ -18,7 +19,7 @@ LIB = os.path.join(BUILD, "libhqc_gb300.so")
 PEAKS_LIB = os.path.join(BUILD, "libhqc_peaks.so")
 SOURCES = ["hqc_decrypt.cu", "hqc_encrypt.cu", "hqc_abi.cu", "hqc_noalloc.cu", "hqc_plan.cu", "hqc_serve.cu", "hqc_host.cu", "hqc_kem.cu"]
 PEAKS_SOURCES = ["hqc_peaks.cu"]
-HEADERS = ["hqc_params.cuh", "hqc_device.cuh", "hqc_internal.h"]
+HEADERS = ["hqc_params.cuh", "hqc_device.cuh", "hqc_internal.h", "hqc_keccak.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]
 
