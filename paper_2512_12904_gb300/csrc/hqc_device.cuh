@@ -40,22 +40,44 @@ __device__ __forceinline__ uint32_t gf_xtime(uint32_t a) {
   return ((a << 1) ^ (0x11Du & (0u - (a >> 7)))) & 0xFFu;
 }
 
-// Fill both tables; called by every thread of the block, then __syncthreads.
-__device__ inline void gf_tables_init(uint8_t* smem, int tid, int nthreads) {
-  uint8_t* ex = smem;
-  uint16_t* lg = reinterpret_cast<uint16_t*>(smem + GF_EXP_BYTES);
-  for (int e = tid; e < 512; e += nthreads) {
-    uint32_t v = 0;
-    if (e < 511) {
-      v = 1;
-      const int ee = e % 255;
-      for (int i = 0; i < ee; i++) v = gf_xtime(v);
+// The two tables packed as the 32-bit words one lane's column holds:
+// exp4[q] = exp[4q .. 4q+3] as bytes, log2[p] = log[2p], log[2p+1] as
+// halfwords.  Computed at compile time (GF(2^8) mod x^8+x^4+x^3+x^2+1,
+// alpha = x) into constant memory; a block copies each word into all 32
+// lane columns.
+struct GfPacked {
+  uint32_t exp4[128];
+  uint32_t log2[128];
+  __host__ __device__ constexpr GfPacked() : exp4(), log2() {
+    uint32_t ex[512] = {};
+    uint32_t lg[256] = {};
+    uint32_t x = 1;
+    for (int e = 0; e < 255; e++) {
+      ex[e] = x;
+      ex[e + 255] = x;
+      lg[x] = (uint32_t)e;
+      x = ((x << 1) ^ ((x >> 7) ? 0x11Du : 0u)) & 0xFFu;
     }
-    for (int l = 0; l < 32; l++) ex[((e & ~3) << 5) + (l << 2) + (e & 3)] = (uint8_t)v;
-    if (e < 255)
-      for (int l = 0; l < 32; l++) lg[((v & ~1u) << 5) + (l << 1) + (v & 1u)] = (uint16_t)e;
+    ex[510] = ex[0];
+    ex[511] = 0;
+    lg[0] = GF_LOG_ZERO;
+    for (int q = 0; q < 128; q++)
+      exp4[q] = ex[4 * q] | ex[4 * q + 1] << 8 | ex[4 * q + 2] << 16 | ex[4 * q + 3] << 24;
+    for (int p = 0; p < 128; p++) log2[p] = lg[2 * p] | lg[2 * p + 1] << 16;
   }
-  if (tid < 32) lg[(tid << 1)] = (uint16_t)GF_LOG_ZERO;  // log 0 in every replica
+};
+static __constant__ GfPacked c_gf_packed = GfPacked();
+
+// Fill both tables; called by every thread of the block, then
+// __syncthreads.  Word w of either table belongs to lane w mod 32 and holds
+// packed word w / 32 (a warp reads one constant word: a broadcast).
+__device__ inline void gf_tables_init(uint8_t* smem, int tid, int nthreads) {
+  uint32_t* ex32 = reinterpret_cast<uint32_t*>(smem);
+  uint32_t* lg32 = reinterpret_cast<uint32_t*>(smem + GF_EXP_BYTES);
+  for (int w = tid; w < 128 * 32; w += nthreads) {
+    ex32[w] = c_gf_packed.exp4[w >> 5];
+    lg32[w] = c_gf_packed.log2[w >> 5];
+  }
 }
 
 struct GF {
