@@ -375,6 +375,21 @@ static cudaError_t team_level(const DecArgs& a, cudaStream_t st, const LaunchCfg
   if (ctas) *ctas = c;
   if (grid) *grid = g;
   if (!launch || a.count == 0) return cudaSuccess;
+  // less than one wave: fewer warps per block so the batch spreads over
+  // every SM instead of filling a few
+  if (cfg.warps_per_cta == 0 && a.count < (int64_t)g * nw) {
+    const int64_t sms = g / c;
+    int small = (int)((a.count + sms - 1) / sms);
+    small = (small + 1) & ~1;
+    if (small < 2) small = 2;
+    if (small < nw) {
+      LaunchCfg sc;
+      sc.warps_per_cta = small;
+      e = shape_for(k_decrypt_team<LEVEL, KEYED>, TeamBound<LEVEL>::threads, (size_t)Team<Level<LEVEL>>::WORDS * 2,
+                    sc, &nw, &c, &g, &sm, true);
+      if (e != cudaSuccess) return e;
+    }
+  }
   const int64_t need = (a.count + nw - 1) / nw;  // nw / 2 teams, two ciphertexts each
   if (need < g) g = (int)need;
   k_decrypt_team<LEVEL, KEYED><<<g, nw * 32, sm, st>>>(a);
@@ -394,7 +409,22 @@ static cudaError_t fused_level(const DecArgs& a, cudaStream_t st, const LaunchCf
   if (ctas) *ctas = c;
   if (grid) *grid = g;
   if (!launch || a.count == 0) return cudaSuccess;
-  const int64_t need = (a.count + (int64_t)nw * FusedGroup<LEVEL>::G - 1) / ((int64_t)nw * FusedGroup<LEVEL>::G);
+  constexpr int G = FusedGroup<LEVEL>::G;
+  // less than one wave: fewer warps per block so the batch spreads over
+  // every SM instead of filling a few
+  if (cfg.warps_per_cta == 0 && a.count < (int64_t)g * nw * G) {
+    const int64_t sms = g / c;
+    int small = (int)((a.count + sms * G - 1) / (sms * G));
+    if (small < 1) small = 1;
+    if (small < nw) {
+      LaunchCfg sc;
+      sc.warps_per_cta = small;
+      e = shape_for(k_decrypt_fused<LEVEL, KEYED>, FusedBound<LEVEL>::threads, (size_t)fused_words<LEVEL>() * 4, sc,
+                    &nw, &c, &g, &sm);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  const int64_t need = (a.count + (int64_t)nw * G - 1) / ((int64_t)nw * G);
   if (need < g) g = (int)need;
   k_decrypt_fused<LEVEL, KEYED><<<g, nw * 32, sm, st>>>(a);
   return cudaGetLastError();

@@ -109,8 +109,36 @@ int pick_chunk(const hqc_params_t& p, int64_t count, int64_t chunk, size_t works
 // The double-buffered pipeline.  upload(first, n, slot, copy_stream),
 // compute(first, n, slot, compute_stream) and download(first, n, slot,
 // compute_stream) enqueue one chunk's work and return a CUDA status.
+// Chunk schedule: `sizes` (each at most the slot's capacity) covering the
+// batch in order.
+std::vector<int64_t> uniform_chunks(int64_t count, int64_t chunk) {
+  std::vector<int64_t> v;
+  for (int64_t f = 0; f < count; f += chunk) v.push_back(count - f < chunk ? count - f : chunk);
+  return v;
+}
+
+// Full chunks, then the remainder split so that the last chunk is about a
+// quarter chunk: the pipeline's tail (the last chunk's kernels and copy
+// back, which nothing overlaps) stays short.
+std::vector<int64_t> tapered_chunks(int64_t count, int64_t chunk) {
+  std::vector<int64_t> v;
+  const int64_t q = chunk / 4 > 0 ? chunk / 4 : 1;
+  int64_t left = count;
+  while (left > chunk + q) {
+    v.push_back(chunk);
+    left -= chunk;
+  }
+  if (left > q) {
+    v.push_back(left - q);
+    v.push_back(q);
+  } else if (left > 0) {
+    v.push_back(left);
+  }
+  return v;
+}
+
 template <class Up, class Comp, class Down>
-int run_pipeline(int64_t count, int64_t chunk, void* workspace, const SlotLayout& L, void* stream, Up upload,
+int run_pipeline(const std::vector<int64_t>& sizes, void* workspace, const SlotLayout& L, void* stream, Up upload,
                  Comp compute, Down download) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -134,10 +162,11 @@ int run_pipeline(int64_t count, int64_t chunk, void* workspace, const SlotLayout
   e = cudaEventRecord(start, us);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, start, 0);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(ks, start, 0);
-  const int64_t nchunks = (count + chunk - 1) / chunk;
-  for (int64_t c = 0; c < nchunks && e == cudaSuccess; c++) {
+  const int64_t nchunks = (int64_t)sizes.size();
+  int64_t first = 0;
+  for (int64_t c = 0; c < nchunks && e == cudaSuccess; first += sizes[(size_t)c], c++) {
     const int s = (int)(c & 1);
-    const int64_t first = c * chunk, n = (count - first) < chunk ? (count - first) : chunk;
+    const int64_t n = sizes[(size_t)c];
     const Slot slot = slot_at(workspace, L, s);
     // the slot is free once the chunk that last used it was processed and copied out
     if (c >= 2) e = cudaStreamWaitEvent(cs, done[s], 0);
@@ -183,6 +212,7 @@ extern "C" int hqc_decrypt_host_keyed(int level, int64_t count, const uint64_t* 
     return hfail(HQC_EINVAL, "NULL argument");
   if (keys->level != level) return hfail(HQC_EINVAL, "keys registered for another level");
   if ((uintptr_t)workspace % 16) return hfail(HQC_EINVAL, "workspace must be 16-byte aligned");
+  const bool tapered = chunk <= 0;
   int rc = pick_chunk(p, count, chunk, workspace_bytes, false, &chunk);
   if (rc != HQC_OK) return rc;
   const SlotLayout L = layout(p, chunk, false);
@@ -207,7 +237,8 @@ extern "C" int hqc_decrypt_host_keyed(int level, int64_t count, const uint64_t* 
   auto down = [&](int64_t first, int64_t n, const Slot& s, cudaStream_t st) {
     return cudaMemcpyAsync(m_host + first * p.k, s.out, (size_t)n * p.k, cudaMemcpyDeviceToHost, st);
   };
-  return run_pipeline(count, chunk, workspace, L, stream, up, comp, down);
+  return run_pipeline(tapered ? tapered_chunks(count, chunk) : uniform_chunks(count, chunk), workspace, L, stream, up,
+                      comp, down);
 }
 
 extern "C" size_t hqc_kem_host_workspace_bytes(int level, int64_t chunk) {
@@ -253,7 +284,7 @@ extern "C" int hqc_kem_decaps_host(int level, int64_t count, const hqc_keyset_t*
       e = cudaMemcpyAsync(ok_host + first, sl.ok, (size_t)n * 4, cudaMemcpyDeviceToHost, st);
     return e;
   };
-  const int rc = run_pipeline(count, chunk, workspace, L, stream, up, comp, down);
+  const int rc = run_pipeline(uniform_chunks(count, chunk), workspace, L, stream, up, comp, down);
   if (rc_kem != HQC_OK) {
     hqc::set_last_error(kem_err);
     return rc_kem;
@@ -449,5 +480,5 @@ extern "C" int hqc_decrypt_mixed_host(int64_t count, const hqc_item_t* items_hos
     parts(s, &w, &raw, &grouped, &m);
     return cudaMemcpyAsync(m_host + c.mbase, m, (size_t)c.mbytes, cudaMemcpyDeviceToHost, st);
   };
-  return run_pipeline(count, chunk, workspace, L, stream, up, comp, down);
+  return run_pipeline(uniform_chunks(count, chunk), workspace, L, stream, up, comp, down);
 }
