@@ -491,6 +491,21 @@ static cudaError_t items_team_level(const MixedArgs& a, int grid, cudaStream_t s
   if (ctas) *ctas = c;
   if (full_grid) *full_grid = g;
   if (!launch || a.count == 0) return cudaSuccess;
+  // a full grid for less than one wave: fewer warps per block so the items
+  // spread over every SM
+  if (grid <= 0 && tc.warps_per_cta == 0 && a.count < (int64_t)g * nw) {
+    const int64_t sms = g / c;
+    int small = (int)((a.count + sms - 1) / sms);
+    small = (small + 1) & ~1;
+    if (small < 2) small = 2;
+    if (small < nw) {
+      LaunchCfg sc;
+      sc.warps_per_cta = small;
+      e = shape_for(k_decrypt_items_team<LEVEL>, TeamBound<LEVEL>::threads, (size_t)Team<Level<LEVEL>>::WORDS * 2,
+                    sc, &nw, &c, &g, &sm, true);
+      if (e != cudaSuccess) return e;
+    }
+  }
   if (grid <= 0 || grid > g) grid = g;
   const int64_t need = (a.count + nw - 1) / nw;
   if (need < grid) grid = (int)need;
@@ -511,8 +526,23 @@ static cudaError_t items_level(const MixedArgs& a, int grid, cudaStream_t st, co
   if (ctas) *ctas = c;
   if (full_grid) *full_grid = g;
   if (!launch || a.count == 0) return cudaSuccess;
+  constexpr int G = FusedGroup<LEVEL>::G;
+  // a full grid for less than one wave: fewer warps per block so the items
+  // spread over every SM
+  if (grid <= 0 && cfg.warps_per_cta == 0 && a.count < (int64_t)g * nw * G) {
+    const int64_t sms = g / c;
+    int small = (int)((a.count + sms * G - 1) / (sms * G));
+    if (small < 1) small = 1;
+    if (small < nw) {
+      LaunchCfg sc;
+      sc.warps_per_cta = small;
+      e = shape_for(k_decrypt_items<LEVEL>, FusedBound<LEVEL>::threads, (size_t)fused_words<LEVEL>() * 4, sc, &nw, &c,
+                    &g, &sm);
+      if (e != cudaSuccess) return e;
+    }
+  }
   if (grid <= 0 || grid > g) grid = g;
-  const int64_t need = (a.count + (int64_t)nw * FusedGroup<LEVEL>::G - 1) / ((int64_t)nw * FusedGroup<LEVEL>::G);
+  const int64_t need = (a.count + (int64_t)nw * G - 1) / ((int64_t)nw * G);
   if (need < grid) grid = (int)need;
   k_decrypt_items<LEVEL><<<grid, nw * 32, sm, st>>>(a);
   return cudaGetLastError();
