@@ -310,6 +310,8 @@ static cudaError_t encrypt_level(int64_t count, const uint64_t* h, const uint64_
   int wpb = (int)((optin - ENC_GF_BYTES) / per_warp);
   if (wpb > EncBound<LEVEL>::threads / 32) wpb = EncBound<LEVEL>::threads / 32;
   if (wpb < 1) return cudaErrorInvalidConfiguration;
+  // fewer items than one wave: fewer warps per block, so every SM gets work
+  if (count < (int64_t)sms * wpb) wpb = (int)((count + sms - 1) / sms);
   const size_t sm = ENC_GF_BYTES + (size_t)wpb * per_warp;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (err != cudaSuccess) return err;
