@@ -150,7 +150,7 @@ int hqc_decrypt_host_keyed(int level, int64_t count, const uint64_t* u_host, con
                            void* workspace, size_t workspace_bytes, void* stream);
 
 /* ---------------------------------------------------------------------
- * KEM (Sec. II-B: SHAKE-based sampling, domain-separated G and K, the HHK
+ * KEM (Sec. II-A: SHAKE-based sampling, domain-separated G and K, the HHK
  * transform with implicit rejection; Algorithms 1-3).  The paper names
  * these functions but not their inputs; this library's reading:
  *   theta   = SHAKE256(m || salt || 0x03)[0:32]          (G)

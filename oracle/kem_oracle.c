@@ -2,7 +2,7 @@
  * kem_oracle.c -- TEST INFRASTRUCTURE, NOT PART OF THE PRODUCT PATH.
  *
  * Plain CPU restatement of the pieces around HQC.PKE that the KEM needs
- * (Sec. II-B: SHAKE as the sampler's PRNG, the domain-separated functions
+ * (Sec. II-A: SHAKE as the sampler's PRNG, the domain-separated functions
  * G, H, K, and the HHK transform with implicit rejection; Algorithms 1-3;
  * the batched Keccak of Sec. III-C).  Linked into the same test library as
  * hqc_oracle.c and used only by tests/, the smoke check and bench.py's CPU

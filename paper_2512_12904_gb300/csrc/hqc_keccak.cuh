@@ -1,5 +1,5 @@
 // Keccak-f[1600] and SHAKE256 for one message per thread (FIPS 202), the
-// PRNG and hash behind HQC's sampler and its G and K functions (Sec. II-B),
+// PRNG and hash behind HQC's sampler and its G and K functions (Sec. II-A),
 // batched as the paper batches its Keccak calls (Sec. III-C).
 //
 // State: 25 lanes a[x + 5 y] of 64 bits, held in registers.  The round

@@ -1,4 +1,4 @@
-// HQC.KEM around the PKE kernels (Sec. II-B: SHAKE-based sampling, the
+// HQC.KEM around the PKE kernels (Sec. II-A: SHAKE-based sampling, the
 // domain-separated G and K functions, HHK with implicit rejection;
 // Algorithms 1-3), one message per thread for every SHAKE256 call:
 //
