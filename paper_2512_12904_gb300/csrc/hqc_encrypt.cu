@@ -161,6 +161,55 @@ __device__ __forceinline__ uint32_t rm_codeword_word(uint32_t B, int t) {
   return w;
 }
 
+// RS systematic encoding of the k-byte row m by the division register (one
+// warp; lane owns parity coefficient c = lane + 32 x, lgc its generator
+// log), written as the codeword (parity || message) to cw.
+template <class LV>
+__device__ __forceinline__ void enc_rs_encode(const uint8_t* __restrict__ mrow, const uint32_t (&lgc)[cdiv(LV::NR, 32)],
+                                              const uint8_t* gex, const uint16_t* glg, int lane, uint8_t* cw) {
+  constexpr int NR = LV::NR, k = LV::k, NX = cdiv(NR, 32);
+  uint32_t par[NX];
+#pragma unroll
+  for (int x = 0; x < NX; x++) par[x] = 0;
+  for (int i = k - 1; i >= 0; i--) {
+    const uint32_t top = __shfl_sync(FULL_MASK, par[(NR - 1) / 32], (NR - 1) % 32);
+    const uint32_t lfb = glg[(uint32_t)mrow[i] ^ top];
+    uint32_t nxt[NX];
+#pragma unroll
+    for (int x = 0; x < NX; x++) {
+      const uint32_t up = __shfl_up_sync(FULL_MASK, par[x], 1);
+      const uint32_t carry = x > 0 ? __shfl_sync(FULL_MASK, par[x > 0 ? x - 1 : 0], 31) : 0u;
+      const int c = lane + 32 * x;
+      const uint32_t prev = lane == 0 ? carry : up;
+      nxt[x] = c < NR ? (prev ^ (uint32_t)gex[min(lgc[x] + lfb, GF_LOG_ZERO)]) : 0u;
+    }
+#pragma unroll
+    for (int x = 0; x < NX; x++) par[x] = nxt[x];
+  }
+#pragma unroll
+  for (int x = 0; x < NX; x++) {
+    const int c = lane + 32 * x;
+    if (c < NR) cw[c] = (uint8_t)par[x];
+  }
+  for (int i = lane; i < k; i += 32) cw[NR + i] = mrow[i];
+}
+
+// Duplicated RM(1,7) encoding of every codeword byte (at u2 + W_v32), added
+// into the truncated product in u2; NT threads, tid in [0, NT).
+template <class LV, int NT>
+__device__ __forceinline__ void enc_rm_encode(uint32_t* u2, int tid) {
+  const uint8_t* cw = reinterpret_cast<const uint8_t*>(u2 + LV::W_v32);
+  for (int j = tid; j < LV::n1; j += NT) {
+    const uint32_t B = cw[j];
+#pragma unroll
+    for (int t = 0; t < 4; t++) {
+      const uint32_t cwt = rm_codeword_word(B, t);
+#pragma unroll
+      for (int rcp = 0; rcp < LV::mult; rcp++) u2[j * (LV::n2 / 32) + 4 * rcp + t] ^= cwt;
+    }
+  }
+}
+
 // Persistent: each warp encrypts items it, it + (warps in the grid), ...
 // CMP: instead of storing (u, v), compare them with (u_in, v_in) on the n
 // and n1 n2 bits (padding of u_in ignored) and store ok[item] = 1 on a match
@@ -229,45 +278,9 @@ __global__ void __launch_bounds__(EncBound<LEVEL>::threads, 1) k_encrypt(int64_t
     }
     xor_support_bits<LV::we, LV::n1 * LV::n2>(u2, e + it * LV::we, lane);
 
-    // RS systematic encoding by the division register; lane owns parity
-    // coefficient c = lane + 32 x
-    uint32_t par[NX];
-#pragma unroll
-    for (int x = 0; x < NX; x++) par[x] = 0;
-    const uint8_t* mrow = m + it * k;
-    for (int i = k - 1; i >= 0; i--) {
-      const uint32_t top = __shfl_sync(FULL_MASK, par[(NR - 1) / 32], (NR - 1) % 32);
-      const uint32_t lfb = glg[(uint32_t)mrow[i] ^ top];
-      uint32_t nxt[NX];
-#pragma unroll
-      for (int x = 0; x < NX; x++) {
-        const uint32_t up = __shfl_up_sync(FULL_MASK, par[x], 1);
-        const uint32_t carry = x > 0 ? __shfl_sync(FULL_MASK, par[x > 0 ? x - 1 : 0], 31) : 0u;
-        const int c = lane + 32 * x;
-        const uint32_t prev = lane == 0 ? carry : up;
-        nxt[x] = c < NR ? (prev ^ (uint32_t)gex[min(lgc[x] + lfb, GF_LOG_ZERO)]) : 0u;
-      }
-#pragma unroll
-      for (int x = 0; x < NX; x++) par[x] = nxt[x];
-    }
-    uint8_t* cw = reinterpret_cast<uint8_t*>(u2 + LV::W_v32);
-#pragma unroll
-    for (int x = 0; x < NX; x++) {
-      const int c = lane + 32 * x;
-      if (c < NR) cw[c] = (uint8_t)par[x];
-    }
-    for (int i = lane; i < k; i += 32) cw[NR + i] = mrow[i];
+    enc_rs_encode<LV>(m + it * k, lgc, gex, glg, lane, reinterpret_cast<uint8_t*>(u2 + LV::W_v32));
     __syncwarp();
-    // duplicated RM(1,7) encoding of every symbol, added into the product
-    for (int j = lane; j < n1; j += 32) {
-      const uint32_t B = cw[j];
-#pragma unroll
-      for (int t = 0; t < 4; t++) {
-        const uint32_t cwt = rm_codeword_word(B, t);
-#pragma unroll
-        for (int rcp = 0; rcp < LV::mult; rcp++) u2[j * (LV::n2 / 32) + 4 * rcp + t] ^= cwt;
-      }
-    }
+    enc_rm_encode<LV, 32>(u2, lane);
     __syncwarp();
     if constexpr (CMP) {
       const uint32_t* vi = reinterpret_cast<const uint32_t*>(v_in + it * LV::W_v);
@@ -278,6 +291,106 @@ __global__ void __launch_bounds__(EncBound<LEVEL>::threads, 1) k_encrypt(int64_t
       store_row<LV::W_v, LV::W_v32>(v + it * LV::W_v, u2, lane);
     }
     __syncwarp();
+  }
+}
+
+// Two-warp teams (HQC-5): the team's warps share one doubled operand and
+// each computes half of both products' words (strips of ETeam::WPT2 words
+// over 64 lanes), so a block holds twice the items in shared memory.  The
+// RS encoder runs on the team's first warp; members synchronise with a
+// 64-thread named barrier.
+template <class LV>
+struct ETeam {
+  static constexpr int WPT2 = odd_at_least(cdiv(cmax(LV::N32, LV::W_v32), 64));
+  static constexpr int U2W = round_up(cmax(cdiv(2 * LV::n, 32), 64 * WPT2 + (LV::n >> 5) + 1), 4);
+  static constexpr int WORDS = U2W + LV::WP_R + 4;  // u2, supports, the team's compare flag
+  static_assert(LV::W_v32 + cdiv(LV::n1, 4) <= U2W, "codeword bytes fit after the product");
+};
+template <int LEVEL> struct EncTeamBound { static constexpr int threads = 896; };
+
+template <int LEVEL, bool CMP, bool VALID>
+__global__ void __launch_bounds__(EncTeamBound<LEVEL>::threads, 1)
+    k_encrypt_team(int64_t count, const uint64_t* __restrict__ h, const uint64_t* __restrict__ s, int64_t nkeys,
+                   const int32_t* __restrict__ key_idx, const uint8_t* __restrict__ m,
+                   const uint32_t* __restrict__ r1, const uint32_t* __restrict__ r2, const uint32_t* __restrict__ e,
+                   uint64_t* __restrict__ u, uint64_t* __restrict__ v, const uint64_t* __restrict__ u_in,
+                   const uint64_t* __restrict__ v_in, uint32_t* __restrict__ ok) {
+  using LV = Level<LEVEL>;
+  using T = ETeam<LV>;
+  constexpr int NR = LV::NR, NX = cdiv(NR, 32), WPT = T::WPT2, RB = LV::n & 31;
+  extern __shared__ __align__(16) uint8_t smem[];
+  enc_gf_init(smem, threadIdx.x);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int team = warp >> 1, wt = warp & 1, tid = wt * 32 + lane, nteams = blockDim.x >> 6;
+  const uint8_t* gex = smem;
+  const uint16_t* glg = reinterpret_cast<const uint16_t*>(smem + 512);
+  uint32_t* u2 = reinterpret_cast<uint32_t*>(smem + ENC_GF_BYTES) + team * T::WORDS;
+  uint32_t* sup = u2 + T::U2W;
+  uint32_t* flag = sup + LV::WP_R;
+  const TeamSync sync{(uint32_t)(1 + team)};
+  uint32_t lgc[NX];
+#pragma unroll
+  for (int x = 0; x < NX; x++) lgc[x] = rs_gen_log_select<NR>(lane + 32 * x, std::make_integer_sequence<int, NR>{});
+  for (int64_t it = (int64_t)blockIdx.x * nteams + team; it < count; it += (int64_t)gridDim.x * nteams) {
+    const uint32_t ki = (uint32_t)key_idx[it];
+    const int64_t key = ki < (uint64_t)nkeys ? (int64_t)ki : 0;
+    if (tid == 0) *flag = 0u;
+    // u = r1 + h * r2
+    load_supports<LV::n, LV::wr, 64>(sup, r2 + it * LV::wr, tid);
+    build_doubled<LV::n, LV::W_u_pitch, T::U2W, 64, TeamSync>(u2, h + key * LV::W_u_pitch, tid, sync);
+    uint32_t acc[WPT];
+    rot_xor_product<WPT, LV::wr, !VALID>(u2, sup, tid, acc);
+    sync();
+#pragma unroll
+    for (int kk = 0; kk < WPT; kk++) {
+      const int i = tid * WPT + kk;
+      if (i < LV::N32) u2[i] = (RB && i == LV::N32 - 1) ? (acc[kk] & ((1u << RB) - 1u)) : acc[kk];
+    }
+    sync();
+    if (wt == 0) xor_support_bits<LV::wr, LV::n>(u2, r1 + it * LV::wr, lane);
+    sync();
+    uint32_t diff = 0;
+    if constexpr (CMP) {
+      const uint32_t* ui = reinterpret_cast<const uint32_t*>(u_in + it * LV::W_u_pitch);
+      for (int i = tid; i < LV::N32; i += 64) {
+        uint32_t x = __ldg(ui + i);
+        if (RB && i == LV::N32 - 1) x &= (1u << RB) - 1u;
+        diff |= x ^ u2[i];
+      }
+    } else {
+      uint32_t* d32 = reinterpret_cast<uint32_t*>(u + it * LV::W_u_pitch);
+      for (int i = tid; i < 2 * LV::W_u_pitch; i += 64) d32[i] = i < LV::N32 ? u2[i] : 0u;
+    }
+    sync();
+    // s * r2, truncated to n1*n2 bits, plus e
+    build_doubled<LV::n, LV::W_u_pitch, T::U2W, 64, TeamSync>(u2, s + key * LV::W_u_pitch, tid, sync);
+    rot_xor_product<WPT, LV::wr, !VALID>(u2, sup, tid, acc);
+    sync();
+#pragma unroll
+    for (int kk = 0; kk < WPT; kk++) {
+      const int i = tid * WPT + kk;
+      if (i < LV::W_v32) u2[i] = acc[kk];
+    }
+    sync();
+    if (wt == 0) {
+      xor_support_bits<LV::we, LV::n1 * LV::n2>(u2, e + it * LV::we, lane);
+      enc_rs_encode<LV>(m + it * LV::k, lgc, gex, glg, lane, reinterpret_cast<uint8_t*>(u2 + LV::W_v32));
+    }
+    sync();
+    enc_rm_encode<LV, 64>(u2, tid);
+    sync();
+    if constexpr (CMP) {
+      const uint32_t* vi = reinterpret_cast<const uint32_t*>(v_in + it * LV::W_v);
+      for (int i = tid; i < LV::W_v32; i += 64) diff |= __ldg(vi + i) ^ u2[i];
+      if (__any_sync(FULL_MASK, diff != 0u) && lane == 0) atomicOr(flag, 1u);
+      sync();
+      if (tid == 0) ok[it] = *flag ? 0u : 1u;
+    } else {
+      uint32_t* d32 = reinterpret_cast<uint32_t*>(v + it * LV::W_v);
+      for (int i = tid; i < 2 * LV::W_v; i += 64) d32[i] = u2[i];
+    }
+    sync();
   }
 }
 
@@ -295,12 +408,47 @@ static cudaError_t keygen_level(int64_t nkeys, const uint64_t* h, const uint32_t
 }
 
 template <int LEVEL, bool CMP, bool VALID>
+static cudaError_t encrypt_team_level(int64_t count, const uint64_t* h, const uint64_t* s, int64_t nkeys,
+                                      const int32_t* ki, const uint8_t* m, const uint32_t* r1, const uint32_t* r2,
+                                      const uint32_t* e, uint64_t* u, uint64_t* v, const uint64_t* u_in,
+                                      const uint64_t* v_in, uint32_t* ok, cudaStream_t st) {
+  using T = ETeam<Level<LEVEL>>;
+  auto kern = k_encrypt_team<LEVEL, CMP, VALID>;
+  int dev = 0, sms = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  constexpr size_t per_team = (size_t)T::WORDS * 4;
+  int teams = (int)((optin - ENC_GF_BYTES) / per_team);
+  if (teams > EncTeamBound<LEVEL>::threads / 64) teams = EncTeamBound<LEVEL>::threads / 64;
+  if (teams > 15) teams = 15;  // named barriers 1..15
+  if (teams < 1) return cudaErrorInvalidConfiguration;
+  if (count < (int64_t)sms * teams) teams = (int)((count + sms - 1) / sms);
+  const size_t sm = ENC_GF_BYTES + (size_t)teams * per_team;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (err != cudaSuccess) return err;
+  int occ = 0;
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, teams * 64, sm);
+  if (err != cudaSuccess) return err;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  int64_t grid = (int64_t)sms * occ;
+  const int64_t need = (count + teams - 1) / teams;
+  if (need < grid) grid = need;
+  kern<<<(unsigned)grid, teams * 64, sm, st>>>(count, h, s, nkeys, ki, m, r1, r2, e, u, v, u_in, v_in, ok);
+  return cudaGetLastError();
+}
+
+template <int LEVEL> struct EncUseTeam { static constexpr bool value = LEVEL == 5; };
+
+template <int LEVEL, bool CMP, bool VALID>
 static cudaError_t encrypt_level(int64_t count, const uint64_t* h, const uint64_t* s, int64_t nkeys, const int32_t* ki,
                                  const uint8_t* m, const uint32_t* r1, const uint32_t* r2, const uint32_t* e,
                                  uint64_t* u, uint64_t* v, const uint64_t* u_in, const uint64_t* v_in, uint32_t* ok,
                                  cudaStream_t st) {
   using LV = Level<LEVEL>;
   if (count == 0) return cudaSuccess;
+  if constexpr (EncUseTeam<LEVEL>::value)
+    return encrypt_team_level<LEVEL, CMP, VALID>(count, h, s, nkeys, ki, m, r1, r2, e, u, v, u_in, v_in, ok, st);
   auto kern = k_encrypt<LEVEL, CMP, VALID>;
   int dev = 0, sms = 0, optin = 0;
   cudaGetDevice(&dev);
