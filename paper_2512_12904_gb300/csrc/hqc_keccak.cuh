@@ -130,16 +130,4 @@ __device__ __forceinline__ void shake256_absorb(uint64_t (&a)[25], int len, Word
   }
 }
 
-// Contribution to message word q of a segment of 64-bit little-endian words
-// seg[0..nwords) placed at byte offset `off` of the message (zero outside).
-template <class SegFn>
-__device__ __forceinline__ uint64_t segment_word(int q, int off, int nwords, SegFn seg) {
-  const int a = off >> 3, r = off & 7;
-  const int i = q - a;
-  if (r == 0) return (i >= 0 && i < nwords) ? seg(i) : 0ull;
-  const uint64_t lo = (i >= 0 && i < nwords) ? seg(i) << (8 * r) : 0ull;
-  const uint64_t hi = (i >= 1 && i - 1 < nwords) ? seg(i - 1) >> (64 - 8 * r) : 0ull;
-  return lo | hi;
-}
-
 }  // namespace hqc
