@@ -40,16 +40,15 @@ __host__ __device__ constexpr int fused_words() { return fused_warp_words<Level<
 // Fused persistent kernel, one level.  Warp w takes groups of G consecutive
 // ciphertexts w, w + (all warps), ...
 // ---------------------------------------------------------------------------
-template <int LEVEL, bool KEYED>
+template <int LEVEL, bool KEYED, int G = FusedGroup<LEVEL>::G>
 __global__ void __launch_bounds__(FusedBound<LEVEL>::threads, 1) k_decrypt_fused(DecArgs a) {
   using LV = Level<LEVEL>;
-  constexpr int G = FusedGroup<LEVEL>::G;
   extern __shared__ __align__(16) uint8_t smem[];
   gf_tables_init(smem, threadIdx.x, blockDim.x);
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const GF gf(smem, lane);
-  uint32_t* ws = reinterpret_cast<uint32_t*>(smem + GF_TABLE_BYTES) + warp * fused_words<LEVEL>();
+  uint32_t* ws = reinterpret_cast<uint32_t*>(smem + GF_TABLE_BYTES) + warp * fused_warp_words<LV, G>();
   const int64_t ngroups = (a.count + G - 1) / G;
   for (int64_t q = (int64_t)blockIdx.x * nw + warp; q < ngroups; q += (int64_t)gridDim.x * nw) {
     auto rows = [&](int g, const uint64_t*& u, const uint64_t*& v, const uint32_t*& y, uint8_t*& m) {
@@ -410,6 +409,20 @@ static cudaError_t fused_level(const DecArgs& a, cudaStream_t st, const LaunchCf
   if (grid) *grid = g;
   if (!launch || a.count == 0) return cudaSuccess;
   constexpr int G = FusedGroup<LEVEL>::G;
+  // at most one group per warp even when spread over every SM: one
+  // ciphertext per warp (G = 1) halves each warp's serial chain
+  if (G > 1 && cfg.warps_per_cta == 0 && a.count <= (int64_t)(g / c) * nw) {
+    const int64_t sms = g / c;
+    LaunchCfg sc;
+    sc.warps_per_cta = (int)((a.count + sms - 1) / sms);
+    e = shape_for(k_decrypt_fused<LEVEL, KEYED, 1>, FusedBound<LEVEL>::threads,
+                  (size_t)fused_warp_words<Level<LEVEL>, 1>() * 4, sc, &nw, &c, &g, &sm);
+    if (e != cudaSuccess) return e;
+    const int64_t need1 = (a.count + nw - 1) / nw;
+    if (need1 < g) g = (int)need1;
+    k_decrypt_fused<LEVEL, KEYED, 1><<<g, nw * 32, sm, st>>>(a);
+    return cudaGetLastError();
+  }
   // less than one wave: fewer warps per block so the batch spreads over
   // every SM instead of filling a few
   if (cfg.warps_per_cta == 0 && a.count < (int64_t)g * nw * G) {
