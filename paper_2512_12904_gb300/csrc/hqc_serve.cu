@@ -50,6 +50,8 @@ struct Slot {
   int64_t words_cap = 0, m_cap = 0;
   bool busy = false;
   int64_t first = 0, last = 0;       // requests [first, last)
+  bool dense = false;                // every request in [first, last) runs: m is one contiguous range
+  int64_t m_first = 0, m_bytes = 0;  // that range of the ring's m layout
 };
 
 // Batches of at most this many requests run as one mixed-kernel launch
@@ -163,16 +165,27 @@ extern "C" int hqc_serve_run(const hqc_serve_cfg_t* cfg, const hqc_keyset_t* con
       }
       const int64_t tc = now_ns();
       t_last = tc;
-      int64_t mpos = 0;
-      for (int64_t i = s.first; i < s.last; i++) {
-        if (status[i] != HQC_STATUS_RUNNING) continue;
-        const int64_t j = rslot(i);
-        const int64_t mb = req_m(j);
-        if (m_out) std::memcpy(m_out + ring->m_off[j], s.h_m + mpos, (size_t)mb);
-        mpos += mb;
-        latency_ns[i] = tc - t0 - arrival_ns[i];
-        status[i] = HQC_STATUS_DONE;
-        done++;
+      if (s.dense) {
+        // the batch's m bytes are one range of the ring's m layout
+        if (m_out) std::memcpy(m_out + s.m_first, s.h_m, (size_t)s.m_bytes);
+        const int64_t lat0 = tc - t0;
+        for (int64_t i = s.first; i < s.last; i++) {
+          latency_ns[i] = lat0 - arrival_ns[i];
+          status[i] = HQC_STATUS_DONE;
+        }
+        done += s.last - s.first;
+      } else {
+        int64_t mpos = 0;
+        for (int64_t i = s.first; i < s.last; i++) {
+          if (status[i] != HQC_STATUS_RUNNING) continue;
+          const int64_t j = rslot(i);
+          const int64_t mb = req_m(j);
+          if (m_out) std::memcpy(m_out + ring->m_off[j], s.h_m + mpos, (size_t)mb);
+          mpos += mb;
+          latency_ns[i] = tc - t0 - arrival_ns[i];
+          status[i] = HQC_STATUS_DONE;
+          done++;
+        }
       }
       s.busy = false;
     }
@@ -183,13 +196,17 @@ extern "C" int hqc_serve_run(const hqc_serve_cfg_t* cfg, const hqc_keyset_t* con
       // contiguous run of requests from head that fits this slot; the copy
       // range starts at the first admitted request (base)
       int64_t i = head, words = 0, mbytes = 0, n = 0, base = -1, prev = -1;
+      bool dense = true;  // no request skipped between the first admitted and the last
+      int64_t j_next = rslot(head);
       for (auto& l : lists) l.clear();
       while (i < arrived && n < max_items) {
+        const int64_t j = j_next;
+        j_next = j + 1 == ring->period ? 0 : j + 1;
         if (status[i] != HQC_STATUS_QUEUED) {
+          if (n > 0) dense = false;
           i++;
           continue;
         }
-        const int64_t j = rslot(i);
         if (n > 0 && j <= prev) break;  // the ring wrapped: next batch
         const int64_t b = base >= 0 ? base : j;
         const int64_t span = ring->word_off[j + 1] - ring->word_off[b];  // ring words up to this request
@@ -225,6 +242,12 @@ extern "C" int hqc_serve_run(const hqc_serve_cfg_t* cfg, const hqc_keyset_t* con
       }
       s.first = head;
       s.last = i;
+      // requests before the first admitted one (already answered) are not
+      // part of the range; trailing skipped ones would have cleared dense
+      while (s.first < i && status[s.first] != HQC_STATUS_RUNNING) s.first++;
+      s.dense = dense;
+      s.m_first = ring->m_off[rslot(s.first)];
+      s.m_bytes = mbytes;
       head = i;
       // the m bytes of the batch are laid out in admission order; the item
       // lists are grouped by level
