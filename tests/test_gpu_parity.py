@@ -360,3 +360,33 @@ def test_host_pipelined_full_size_sampled(hqc):
     want = oracle.decrypt(level, u_h.numpy()[idx].view(np.uint64), v_h.numpy()[idx].view(np.uint64), y[kidx[idx]])
     assert (m_h.numpy()[idx] == want).all()
     keys.free()
+
+
+def test_large_batch_2_20_hqc1(hqc):
+    """2^20 HQC-1 ciphertexts (4.6 GB of u and v) in one keyed launch: 64-bit
+    row arithmetic and many waves of the persistent grid; every m checked on
+    the device, sampled items against the oracle."""
+    level, count, nkeys = 1, 1 << 20, 64
+    P = oracle.params(level)
+    S = synth.Shape.of(P)
+    h, x, y = synth.keys(S, nkeys, first=500)
+    s = oracle.keygen(level, h, x, y)
+    chunk = 1 << 17
+    keys = hqc.Keyset(level, y)
+    hd, sd = u64(h), u64(s)
+    u_d = torch.empty((count, P.W_u_pitch), dtype=torch.int64, device="cuda")
+    v_d = torch.empty((count, P.W_v), dtype=torch.int64, device="cuda")
+    m_d = torch.empty((count, P.k), dtype=torch.uint8, device="cuda")
+    kidx = synth.key_assignment(count, nkeys, tag=41)
+    k_d = dev(kidx.astype(np.int32))
+    for c0 in range(0, count, chunk):
+        m, r1, r2, e = synth.ciphertext_randomness(S, chunk, first=1_000_000 + c0)
+        m_d[c0:c0 + chunk] = dev(m)
+        hqc.hqc_encrypt_batch(level, hd, sd, k_d[c0:c0 + chunk], m_d[c0:c0 + chunk], i32(r1), i32(r2), i32(e),
+                              u_out=u_d[c0:c0 + chunk], v_out=v_d[c0:c0 + chunk])
+    got = hqc.hqc_decrypt_batch_keyed(level, u_d, v_d, keys, k_d)
+    assert bool((got == m_d).all().item())
+    idx = [0, 123457, count // 2, count - 1]
+    want = oracle.decrypt(level, host(u_d[idx]).view(np.uint64), host(v_d[idx]).view(np.uint64), y[kidx[idx]])
+    assert (host(got[idx]) == want).all()
+    keys.free()
