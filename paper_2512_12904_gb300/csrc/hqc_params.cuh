@@ -52,6 +52,10 @@ template <int LEVEL> struct Level : LevelConst<LEVEL> {
   // output words of the truncated product per lane (odd -> a warp's
   // strided shared-memory reads hit 32 distinct banks)
   static constexpr int WPT = odd_at_least(cdiv(W_v32, 32));
+  // decryption's split of the W_v32 product words: 32 strips of WPTM (odd,
+  // at most W_v32 / 32 words) and TAIL < 32 words shared by lane groups
+  static constexpr int WPTM = ((W_v32 / 32) & 1) ? W_v32 / 32 : W_v32 / 32 - 1;
+  static constexpr int TAIL = W_v32 - 32 * WPTM;
   // highest u2 word a lane may read: 32*WPT - 1 + (n >> 5) + 1
   static constexpr int U2W = round_up(cmax(cdiv(2 * C::n, 32), 32 * WPT + (C::n >> 5) + 1), 4);
   static constexpr int WP = round_up(2 * C::w, 4);    // two words per support entry
