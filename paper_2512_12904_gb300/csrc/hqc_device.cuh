@@ -575,20 +575,22 @@ __device__ __forceinline__ void rs_decode_seg(const GF& gf, uint32_t* rs, const 
 // S1-S7 of one ciphertext by one warp: product, XOR with v, RM decode; the
 // n1 RM bytes go to r_out.  ws: U2W + WP words owned by this warp.
 // ---------------------------------------------------------------------------
-// Words [32 WPTM, W_v32) of the truncated product (LV::TAIL of them, at
-// most 16): lane l takes word 32 WPTM + (l mod TP) over the entries t = l / TP
-// (mod 32 / TP), TP = TAIL rounded up to a power of two; shuffles then XOR
-// the lane groups' partial sums, so lane l returns word 32 WPTM + (l mod TP).
-// Trip counts depend only on the public weight.
-template <class LV, bool MASKED>
+// Words [32 WPTM, 32 WPTM + TAIL) of the product (TAIL at most 16), the
+// ones past the 32 strips of WPTM words: lane l takes word 32 WPTM + (l mod
+// TP) over the entries t = l / TP (mod 32 / TP) of the W-entry support, TP =
+// TAIL rounded up to a power of two; shuffles then XOR the lane groups'
+// partial sums, so lane l returns word 32 WPTM + (l mod TP).  Trip counts
+// depend only on the public weight.
+template <int WPTM, int TAIL, int W, bool MASKED>
 __device__ __forceinline__ uint32_t product_tail(const uint32_t* u2, const uint32_t* sup, int lane) {
-  constexpr int TP = LV::TAIL <= 1 ? 1 : LV::TAIL <= 2 ? 2 : LV::TAIL <= 4 ? 4 : LV::TAIL <= 8 ? 8 : 16;
+  static_assert(TAIL > 0 && TAIL <= 16, "tail of 1..16 words");
+  constexpr int TP = TAIL <= 1 ? 1 : TAIL <= 2 ? 2 : TAIL <= 4 ? 4 : TAIL <= 8 ? 8 : 16;
   constexpr int NG = 32 / TP;
   const int grp = lane / TP;
-  const char* base = reinterpret_cast<const char*>(u2 + 32 * LV::WPTM + (lane & (TP - 1)));
+  const char* base = reinterpret_cast<const char*>(u2 + 32 * WPTM + (lane & (TP - 1)));
   uint32_t acc = 0;
 #pragma unroll 2
-  for (int t = grp; t < LV::w; t += NG) {
+  for (int t = grp; t < W; t += NG) {
     const uint2 e = *reinterpret_cast<const uint2*>(sup + 2 * t);
     const uint32_t* a = reinterpret_cast<const uint32_t*>(base + e.x);
     const uint32_t f = __funnelshift_r(a[0], a[1], e.y);
@@ -614,7 +616,7 @@ __device__ __forceinline__ void product_rm_one(uint32_t* ws, int lane, const uin
   uint32_t acc[WPT];
   rot_xor_product<WPT, LV::w, MASKED>(u2, sup, lane, acc);
   uint32_t tail = 0;
-  if constexpr (SPLIT) tail = product_tail<LV, MASKED>(u2, sup, lane);
+  if constexpr (SPLIT) tail = product_tail<WPT, LV::TAIL, LV::w, MASKED>(u2, sup, lane);
   // S4: w = v + t, truncated (only the first n1*n2 bits were computed)
   const uint32_t* v32 = reinterpret_cast<const uint32_t*>(vrow);
 #pragma unroll

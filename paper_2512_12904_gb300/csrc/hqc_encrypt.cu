@@ -95,21 +95,53 @@ __device__ __forceinline__ uint32_t rs_gen_log_select(int c, std::integer_sequen
 
 // Product of the dense row `dense` by the support `supp` (w entries, may
 // be invalid -> masked) over the full n bits, left in u2[0, N32) with the
-// bits >= n of the last word cleared.
-template <class LV, int W, int WPT, int U2W, bool MASKED = true>
+// bits >= n of the last word cleared.  A short tail past 32 odd strips
+// (HQC-1: 17-word strips and 9 tail words, HQC-3: 35 and 1) is computed
+// by lane groups instead of widening every strip.
+template <class LV, int W, bool MASKED = true>
 __device__ __forceinline__ void full_product_to_smem(uint32_t* u2, uint32_t* sup, const uint64_t* dense,
                                                      const uint32_t* supp, int lane) {
   constexpr int N32 = LV::N32, R = LV::n & 31;
+  constexpr uint32_t LAST = R ? (1u << R) - 1u : ~0u;
+  constexpr bool SPLIT = LV::TAIL_FULL > 0 && LV::TAIL_FULL <= 16;
+  constexpr int WPT = SPLIT ? LV::WPTM_FULL : LV::WPT_FULL;
   load_supports<LV::n, W>(sup, supp, lane);
-  build_doubled<LV::n, LV::W_u_pitch, U2W>(u2, dense, lane);
+  build_doubled<LV::n, LV::W_u_pitch, LV::U2W_FULL>(u2, dense, lane);
   uint32_t acc[WPT];
   rot_xor_product<WPT, W, MASKED>(u2, sup, lane, acc);
+  uint32_t tail = 0;
+  if constexpr (SPLIT) tail = product_tail<WPT, LV::TAIL_FULL, W, MASKED>(u2, sup, lane);
   __syncwarp();
 #pragma unroll
   for (int k = 0; k < WPT; k++) {
     const int i = lane * WPT + k;
-    if (i < N32) u2[i] = (R && i == N32 - 1) ? (acc[k] & ((1u << R) - 1u)) : acc[k];
+    if (i < N32) u2[i] = i == N32 - 1 ? (acc[k] & LAST) : acc[k];
   }
+  if constexpr (SPLIT) {
+    const int i = 32 * WPT + lane;
+    if (lane < LV::TAIL_FULL) u2[i] = i == N32 - 1 ? (tail & LAST) : tail;
+  }
+  __syncwarp();
+}
+
+// The W_v32 words of the product truncated to n1 n2 bits, left in
+// u2[0, W_v32); the same strip and tail split as decryption's product.
+template <class LV, int W, bool MASKED>
+__device__ __forceinline__ void truncated_product_to_smem(uint32_t* u2, const uint32_t* sup, int lane) {
+  constexpr bool SPLIT = LV::TAIL > 0 && LV::TAIL <= 16;
+  constexpr int WPT = SPLIT ? LV::WPTM : LV::WPT;
+  uint32_t acc[WPT];
+  rot_xor_product<WPT, W, MASKED>(u2, sup, lane, acc);
+  uint32_t tail = 0;
+  if constexpr (SPLIT) tail = product_tail<WPT, LV::TAIL, W, MASKED>(u2, sup, lane);
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < WPT; k++) {
+    const int i = lane * WPT + k;
+    if (i < LV::W_v32) u2[i] = acc[k];
+  }
+  if constexpr (SPLIT)
+    if (lane < LV::TAIL) u2[32 * WPT + lane] = tail;
   __syncwarp();
 }
 
@@ -140,7 +172,7 @@ __global__ void __launch_bounds__(ENC_THREADS) k_keygen(int64_t nkeys, const uin
   if (it >= nkeys) return;
   uint32_t* u2 = reinterpret_cast<uint32_t*>(smem) + warp * WARP_W;
   uint32_t* sup = u2 + LV::U2W_FULL;
-  full_product_to_smem<LV, LV::w, LV::WPT_FULL, LV::U2W_FULL>(u2, sup, h + it * LV::W_u_pitch, y + it * LV::w, lane);
+  full_product_to_smem<LV, LV::w>(u2, sup, h + it * LV::W_u_pitch, y + it * LV::w, lane);
   xor_support_bits<LV::w, LV::n>(u2, x + it * LV::w, lane);
   store_row<LV::W_u_pitch, LV::N32>(s + it * LV::W_u_pitch, u2, lane);
 }
@@ -246,7 +278,7 @@ __global__ void __launch_bounds__(EncBound<LEVEL>::threads, 1) k_encrypt(int64_t
     const int64_t key = ki < (uint64_t)nkeys ? (int64_t)ki : 0;
 
     // u = r1 + h * r2
-    full_product_to_smem<LV, LV::wr, LV::WPT_FULL, LV::U2W_FULL, !VALID>(u2, sup, h + key * LV::W_u_pitch,
+    full_product_to_smem<LV, LV::wr, !VALID>(u2, sup, h + key * LV::W_u_pitch,
                                                                         r2 + it * LV::wr, lane);
     xor_support_bits<LV::wr, LV::n>(u2, r1 + it * LV::wr, lane);
     uint32_t diff = 0;
@@ -265,17 +297,7 @@ __global__ void __launch_bounds__(EncBound<LEVEL>::threads, 1) k_encrypt(int64_t
 
     // s * r2, truncated to n1*n2 bits, plus e
     build_doubled<LV::n, LV::W_u_pitch, LV::U2W_FULL>(u2, s + key * LV::W_u_pitch, lane);
-    {
-      uint32_t acc[LV::WPT];
-      rot_xor_product<LV::WPT, LV::wr, !VALID>(u2, sup, lane, acc);
-      __syncwarp();
-#pragma unroll
-      for (int kk = 0; kk < LV::WPT; kk++) {
-        const int i = lane * LV::WPT + kk;
-        if (i < LV::W_v32) u2[i] = acc[kk];
-      }
-      __syncwarp();
-    }
+    truncated_product_to_smem<LV, LV::wr, !VALID>(u2, sup, lane);
     xor_support_bits<LV::we, LV::n1 * LV::n2>(u2, e + it * LV::we, lane);
 
     enc_rs_encode<LV>(m + it * k, lgc, gex, glg, lane, reinterpret_cast<uint8_t*>(u2 + LV::W_v32));
