@@ -338,7 +338,13 @@ int hqc_plan_destroy(hqc_plan_t* plan);
  * Outputs per request: status[i] (HQC_STATUS_*) and latency_ns[i] =
  * completion time - arrival time (-1 unless DONE).  The call allocates the
  * budget at start and frees it before returning; it returns when every
- * request is answered. */
+ * request is answered.
+ * A batch still incomplete stall_ms after its launch ends the call with
+ * HQC_ETIMEOUT: the batches in flight are then waited for, again at most
+ * stall_ms plus one second, and their buffers freed only if they finished
+ * (a batch that never finishes keeps its device and pinned memory).
+ * Requests not answered by then keep status QUEUED or RUNNING, and stats
+ * counts what completed before the stall. */
 #define HQC_STATUS_DONE 0
 #define HQC_STATUS_QUEUED 1
 #define HQC_STATUS_RUNNING 2
@@ -351,6 +357,7 @@ typedef struct hqc_serve_cfg_s {
   int64_t budget_bytes;   /* device memory for request data, split over the streams */
   int64_t max_queue;      /* waiting requests at most */
   int32_t warps_per_cta;  /* launch shape of the per-level kernels (0 = default) */
+  int32_t stall_ms;       /* per-batch completion limit in ms (0 = 10,000; < 0 is an error) */
 } hqc_serve_cfg_t;
 typedef struct hqc_serve_ring_s {
   int64_t period;

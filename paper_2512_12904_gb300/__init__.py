@@ -26,12 +26,16 @@ __all__ = [
     "SERVE_STATUS", "hqc_decrypt_host_keyed", "hqc_host_workspace_bytes", "hqc_shake256_batch",
     "hqc_kem_keygen", "hqc_kem_workspace_bytes", "hqc_kem_encaps", "hqc_kem_decaps",
     "hqc_kem_host_workspace_bytes", "hqc_kem_decaps_host", "hqc_mixed_host_workspace_bytes",
-    "hqc_decrypt_mixed_host",
+    "hqc_decrypt_mixed_host", "HQC_OK", "HQC_EINVAL", "HQC_ENOMEM", "HQC_ECUDA", "HQC_ETIMEOUT", "HQC_EBUSY",
+    "HQC_EINTERNAL",
 ]
 
 LEVELS = (1, 3, 5)
 _lock = threading.Lock()
 _lib = None
+
+
+HQC_OK, HQC_EINVAL, HQC_ENOMEM, HQC_ECUDA, HQC_ETIMEOUT, HQC_EBUSY, HQC_EINTERNAL = 0, -1, -2, -3, -4, -5, -6
 
 
 class HqcError(RuntimeError):
@@ -472,7 +476,7 @@ def hqc_plan_create_mixed(items, arena, keys, m_arena, autotune=True, stream=Non
 
 class _ServeCfg(ctypes.Structure):
     _fields_ = [("streams", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("budget_bytes", ctypes.c_int64),
-                ("max_queue", ctypes.c_int64), ("warps_per_cta", ctypes.c_int32)]
+                ("max_queue", ctypes.c_int64), ("warps_per_cta", ctypes.c_int32), ("stall_ms", ctypes.c_int32)]
 
 
 class _ServeRing(ctypes.Structure):
@@ -491,11 +495,14 @@ SERVE_STATUS = {0: "done", 1: "queued", 2: "running", 3: "rejected", 4: "invalid
 
 
 def hqc_serve_run(keys, ring_level, ring_key, ring_word_off, ring_words, ring_m_off, arrival_ns, streams=4,
-                  max_batch=8192, budget_bytes=256 << 20, max_queue=1 << 20, warps_per_cta=0, want_m=True):
+                  max_batch=8192, budget_bytes=256 << 20, max_queue=1 << 20, warps_per_cta=0, want_m=True,
+                  stall_ms=0):
     """Run the continuous-batching loop over a request trace (hqc_serve_run).
 
     ring_words must be a PINNED uint64/int64 CPU tensor; the other ring
-    arrays are numpy.  Returns (status, latency_ns, m_out or None, stats)."""
+    arrays are numpy.  Returns (status, latency_ns, m_out or None, stats).
+    A batch incomplete stall_ms after its launch (0: 10 s) raises HqcError
+    with code HQC_ETIMEOUT."""
     torch = _torch()
     if not isinstance(ring_words, torch.Tensor) or ring_words.is_cuda or not ring_words.is_pinned():
         raise ValueError("ring_words must be a pinned CPU tensor")
@@ -513,16 +520,20 @@ def hqc_serve_run(keys, ring_level, ring_key, ring_word_off, ring_words, ring_m_
     status = np.zeros(cnt, np.int32)
     lat = np.zeros(cnt, np.int64)
     m_out = np.zeros(int(moff[-1]), np.uint8) if want_m else None
-    cfg = _ServeCfg(streams, max_batch, budget_bytes, max_queue, warps_per_cta)
+    cfg = _ServeCfg(streams, max_batch, budget_bytes, max_queue, warps_per_cta, stall_ms)
     ring = _ServeRing(period, lvl.ctypes.data_as(ctypes.c_void_p), key.ctypes.data_as(ctypes.c_void_p),
                       woff.ctypes.data_as(ctypes.c_void_p), ctypes.c_void_p(ring_words.data_ptr()),
                       moff.ctypes.data_as(ctypes.c_void_p))
     karr = (ctypes.c_void_p * 3)(*[(k.handle if k is not None else None) for k in keys])
     st = _ServeStats()
-    _check(load().hqc_serve_run(ctypes.byref(cfg), karr, ctypes.byref(ring), cnt, arr.ctypes.data_as(ctypes.c_void_p),
-                                status.ctypes.data_as(ctypes.c_void_p), lat.ctypes.data_as(ctypes.c_void_p),
-                                m_out.ctypes.data_as(ctypes.c_void_p) if want_m else None, ctypes.byref(st)))
+    rc = load().hqc_serve_run(ctypes.byref(cfg), karr, ctypes.byref(ring), cnt, arr.ctypes.data_as(ctypes.c_void_p),
+                              status.ctypes.data_as(ctypes.c_void_p), lat.ctypes.data_as(ctypes.c_void_p),
+                              m_out.ctypes.data_as(ctypes.c_void_p) if want_m else None, ctypes.byref(st))
     stats = {f: getattr(st, f) for f, _ in _ServeStats._fields_}
+    if rc != 0:
+        err = HqcError(rc, load().hqc_last_error().decode(errors="replace"))
+        err.partial = (status, lat, m_out, stats)  # what was answered before the error
+        raise err
     return status, lat, m_out, stats
 
 

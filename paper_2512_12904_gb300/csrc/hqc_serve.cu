@@ -21,6 +21,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 #include "../../include/hqc_gb300.h"
@@ -49,6 +50,7 @@ struct Slot {
   uint8_t* h_m = nullptr;            // pinned
   int64_t words_cap = 0, m_cap = 0;
   bool busy = false;
+  int64_t t_launch = 0;              // host time the batch was issued
   int64_t first = 0, last = 0;       // requests [first, last)
   bool dense = false;                // every request in [first, last) runs: m is one contiguous range
   int64_t m_first = 0, m_bytes = 0;  // that range of the ring's m layout
@@ -69,8 +71,10 @@ extern "C" int hqc_serve_run(const hqc_serve_cfg_t* cfg, const hqc_keyset_t* con
                              const hqc_serve_ring_t* ring, int64_t count, const int64_t* arrival_ns,
                              int32_t* status, int64_t* latency_ns, uint8_t* m_out, hqc_serve_stats_t* stats) {
   if (!cfg || !keys || !ring || !arrival_ns || !status || !latency_ns) return sfail(HQC_EINVAL, "NULL argument");
-  if (cfg->streams < 1 || cfg->streams > 16 || cfg->max_batch < 1 || cfg->budget_bytes <= 0 || cfg->max_queue < 1)
-    return sfail(HQC_EINVAL, "streams in [1, 16], max_batch >= 1, budget_bytes > 0, max_queue >= 1");
+  if (cfg->streams < 1 || cfg->streams > 16 || cfg->max_batch < 1 || cfg->budget_bytes <= 0 || cfg->max_queue < 1 ||
+      cfg->stall_ms < 0)
+    return sfail(HQC_EINVAL, "streams in [1, 16], max_batch >= 1, budget_bytes > 0, max_queue >= 1, stall_ms >= 0");
+  const int64_t stall_ns = (int64_t)(cfg->stall_ms ? cfg->stall_ms : 10000) * 1000000;
   if (ring->period < 1 || !ring->level || !ring->key || !ring->word_off || !ring->words || !ring->m_off)
     return sfail(HQC_EINVAL, "ring is incomplete");
   if (count < 0) return sfail(HQC_EINVAL, "count must be >= 0");
@@ -138,6 +142,34 @@ extern "C" int hqc_serve_run(const hqc_serve_cfg_t* cfg, const hqc_keyset_t* con
   for (int64_t i = 0; i < count; i++) status[i] = -1, latency_ns[i] = -1;
 
   std::vector<hqc::MixedItem> lists[3];
+  auto fill_stats = [&]() {
+    if (!stats) return;
+    stats->completed = done;
+    stats->rejected_queue = rej_queue;
+    stats->rejected_invalid = rej_invalid;
+    stats->rejected_size = rej_size;
+    stats->batches = batches;
+    stats->mean_batch = batches ? (double)batch_items / (double)batches : 0.0;
+    stats->wall_ns = t_last - t0;
+    stats->items_per_slot = max_items;
+  };
+  // a batch past its limit: wait a bounded time for everything in flight,
+  // free the buffers if it all finished, and report the stall
+  auto stalled = [&](const Slot& late) {
+    const int64_t n_late = late.last - late.first;
+    const int64_t until = now_ns() + stall_ns + 1000000000;
+    bool drained = true;
+    for (auto& s : slots) {
+      if (!s.busy) continue;
+      cudaError_t q;
+      while ((q = cudaEventQuery(s.ev)) == cudaErrorNotReady && now_ns() < until) std::this_thread::yield();
+      if (q == cudaErrorNotReady) drained = false;
+    }
+    if (drained) cleanup();
+    fill_stats();
+    return sfail(HQC_ETIMEOUT, "a batch of %lld requests did not complete within %lld ms%s", (long long)n_late,
+                 (long long)(stall_ns / 1000000), drained ? "" : "; its buffers are still held");
+  };
   while (done + rej_queue + rej_invalid + rej_size < count) {
     const int64_t now = now_ns() - t0;
     // arrivals; invalid requests are answered at once, overflow is rejected
@@ -158,7 +190,10 @@ extern "C" int hqc_serve_run(const hqc_serve_cfg_t* cfg, const hqc_keyset_t* con
     for (auto& s : slots) {
       if (!s.busy) continue;
       e = cudaEventQuery(s.ev);
-      if (e == cudaErrorNotReady) continue;
+      if (e == cudaErrorNotReady) {
+        if (now_ns() - s.t_launch > stall_ns) return stalled(s);
+        continue;
+      }
       if (e != cudaSuccess) {
         cleanup();
         return sfail(HQC_ECUDA, "batch failed: %s", cudaGetErrorString(e));
@@ -303,20 +338,12 @@ extern "C" int hqc_serve_run(const hqc_serve_cfg_t* cfg, const hqc_keyset_t* con
         return sfail(HQC_ECUDA, "batch launch: %s", cudaGetErrorString(e));
       }
       s.busy = true;
+      s.t_launch = now_ns();
       batches++;
       batch_items += n;
     }
   }
   cleanup();
-  if (stats) {
-    stats->completed = done;
-    stats->rejected_queue = rej_queue;
-    stats->rejected_invalid = rej_invalid;
-    stats->rejected_size = rej_size;
-    stats->batches = batches;
-    stats->mean_batch = batches ? (double)batch_items / (double)batches : 0.0;
-    stats->wall_ns = t_last - t0;
-    stats->items_per_slot = max_items;
-  }
+  fill_stats();
   return HQC_OK;
 }

@@ -160,3 +160,27 @@ def test_mixed_host_pipeline_order_checks_on_the_host():
     N = None
     assert lib.hqc_decrypt_mixed_host(0, N, N, 0, N, N, 0, 0, N, 0, N) == 0
     assert lib.hqc_decrypt_mixed_host(3, N, N, 0, N, N, 0, 0, N, 0, N) == -1
+
+
+def test_serving_argument_checks_without_a_gpu():
+    """hqc_serve_run rejects a bad configuration (including a negative stall
+    limit) before it touches the device."""
+    lib = hqc.load()
+    one32 = np.zeros(2, np.int32)
+    one64 = np.zeros(2, np.int64)
+    ring = hqc._ServeRing(1, one32.ctypes.data_as(ctypes.c_void_p), one32.ctypes.data_as(ctypes.c_void_p),
+                          one64.ctypes.data_as(ctypes.c_void_p), one64.ctypes.data_as(ctypes.c_void_p),
+                          one64.ctypes.data_as(ctypes.c_void_p))
+    karr = (ctypes.c_void_p * 3)(None, None, None)
+    st, lat = np.zeros(1, np.int32), np.zeros(1, np.int64)
+
+    def call(cfg):
+        return lib.hqc_serve_run(ctypes.byref(cfg), karr, ctypes.byref(ring), 1,
+                                 one64.ctypes.data_as(ctypes.c_void_p), st.ctypes.data_as(ctypes.c_void_p),
+                                 lat.ctypes.data_as(ctypes.c_void_p), None, None)
+
+    assert ctypes.sizeof(hqc._ServeCfg) == 32
+    assert call(hqc._ServeCfg(1, 1, 1 << 20, 1, 0, -1)) == hqc.HQC_EINVAL
+    assert b"stall_ms" in lib.hqc_last_error()
+    assert call(hqc._ServeCfg(0, 1, 1 << 20, 1, 0, 0)) == hqc.HQC_EINVAL
+    assert call(hqc._ServeCfg(1, 1, 0, 1, 0, 0)) == hqc.HQC_EINVAL

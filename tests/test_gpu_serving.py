@@ -105,3 +105,33 @@ def test_queue_limit_rejects_and_the_admitted_decrypt(hqc):
     for i in np.nonzero(st == 0)[0]:
         j = i % 200
         assert (m[R["m_off"][j]:R["m_off"][j + 1]] == R["want"][R["m_off"][j]:R["m_off"][j + 1]]).all()
+
+
+def test_a_batch_past_its_stall_limit_ends_the_call_with_a_timeout(hqc):
+    """A batch still incomplete stall_ms after its launch ends the call with
+    HQC_ETIMEOUT; the batch in flight is waited for and freed, its requests
+    are reported as still running, and the library keeps working.  A slow
+    batch stands in for a stuck one: 32,768 HQC-5 requests in one batch
+    need more than 1 ms for the upload of their 472 MB alone at the host
+    link's rate, and about as long again to decrypt."""
+    P = hqc.hqc_get_params(5)
+    n, per = 32768, P.W_u_pitch + P.W_v
+    wl = honest(5, 1, 1, first_ct=99000, tag=93)
+    keys = [None, None, hqc.Keyset(5, wl.y)]
+    words = torch.from_numpy(synth.words(n * per, tag=94).view(np.int64)).pin_memory()
+    level = np.full(n, 5, np.int32)
+    key = np.zeros(n, np.int32)
+    woff = np.arange(n + 1, dtype=np.int64) * per
+    moff = np.arange(n + 1, dtype=np.int64) * P.k
+    with pytest.raises(hqc.HqcError) as info:
+        hqc.hqc_serve_run(keys, level, key, woff, words, moff, np.zeros(n, np.int64), streams=1, max_batch=n,
+                          budget_bytes=512 << 20, stall_ms=1)
+    err = info.value
+    assert err.code == hqc.HQC_ETIMEOUT and "did not complete" in str(err)
+    st, lat, _, stats = err.partial
+    assert (st == 2).all() and (lat == -1).all() and stats["completed"] == 0 and stats["batches"] == 1
+    keys[2].free()
+    # the same library and device serve a normal trace afterwards
+    R = make_ring(hqc, 40, tag=5)
+    st2, _, m2, stats2 = run(hqc, R, np.zeros(40, np.int64), streams=2)
+    assert (st2 == 0).all() and (m2 == R["want"]).all() and stats2["completed"] == 40
