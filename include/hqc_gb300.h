@@ -248,7 +248,10 @@ int hqc_decrypt_debug(int level, int64_t count, const uint64_t* u, const uint64_
  * is absent).  An item whose level, key or offsets fall outside these
  * arrays is skipped and its m bytes are left untouched.  workspace: at
  * least hqc_mixed_workspace_bytes() bytes of device memory (a work
- * counter, zeroed on the stream by this call). */
+ * counter, zeroed on the stream by this call).  With the default launch
+ * shape, batches of at most 512 items run the latency form: a team of four
+ * warps per item, one item per team, so the slowest item's chain is split
+ * over 128 lanes. */
 typedef struct hqc_item_s {
   int32_t level;
   int32_t key;

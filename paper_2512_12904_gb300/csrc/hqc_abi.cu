@@ -268,6 +268,9 @@ int hqc_decrypt_mixed(int64_t count, const hqc_item_t* items, const uint64_t* ar
   }
   a.m = m_arena;
   a.m_bytes = m_bytes;
+  // a small batch with the default shape: one team of warps per item
+  if (count <= hqc::MIXED_LATENCY_MAX && g_cfg[0].warps_per_cta == 0 && g_cfg[0].ctas_per_sm == 0)
+    return launch_result(hqc::launch_mixed_latency(a, (cudaStream_t)stream), "mixed decrypt launch");
   a.counter = static_cast<uint32_t*>(workspace);
   cudaError_t e = cudaMemsetAsync(workspace, 0, sizeof(uint32_t), (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "zeroing the work counter");

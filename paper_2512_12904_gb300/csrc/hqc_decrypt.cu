@@ -167,6 +167,54 @@ __global__ void __launch_bounds__(MIXED_MAX_THREADS, 1) k_decrypt_mixed(MixedArg
 }
 
 // ---------------------------------------------------------------------------
+// Latency form of the mixed kernel: a team of LAT_TEAM warps decodes one
+// item of any level at a time, splitting the product strips and the RM
+// blocks over the team; the first warp runs the Reed-Solomon stage.  One
+// team per block, so a small batch spreads over every SM.  In a batch that
+// fits one wave the slowest item sets the time, and its chain is shorter.
+// ---------------------------------------------------------------------------
+constexpr int LAT_TEAM = 4;
+template <int T>
+__host__ __device__ constexpr int lat_team_words() {
+  return cmax(Team<Level<1>, T, 1>::WORDS, cmax(Team<Level<3>, T, 1>::WORDS, Team<Level<5>, T, 1>::WORDS));
+}
+
+template <class LV, int T>
+__device__ __forceinline__ void mixed_item_team(const GF& gf, uint32_t* ws, int wt, int lane, const TeamSync& sync,
+                                                const MixedArgs& a, const MixedItem& it) {
+  const int li = LV::level == 1 ? 0 : LV::level == 3 ? 1 : 2;
+  const bool ok = (uint32_t)it.key < (uint64_t)a.nkeys[li] && it.u_off >= 0 && (it.u_off & 1) == 0 &&
+                  it.u_off + LV::W_u_pitch <= a.arena_words && it.v_off >= 0 &&
+                  it.v_off + LV::W_v <= a.arena_words && it.m_off >= 0 && it.m_off + LV::k <= a.m_bytes;
+  if (!ok) return;  // the same item for the whole team: all its warps leave together
+  auto rows = [&](int g, const uint64_t*& u, const uint64_t*& v, const uint32_t*& y, uint8_t*& m) {
+    u = a.arena + it.u_off;
+    v = a.arena + it.v_off;
+    y = a.keys[li] + (int64_t)it.key * LV::w;
+    m = a.m + it.m_off;
+    return g == 0;
+  };
+  decrypt_team<LV, false, T, 1>(gf, ws, wt, lane, sync, rows);
+}
+
+template <int T>
+__global__ void __launch_bounds__(32 * T, 4) k_decrypt_mixed_team(MixedArgs a) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  gf_tables_init(smem, threadIdx.x, blockDim.x);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wt = threadIdx.x >> 5;
+  const GF gf(smem, lane);
+  uint32_t* ws = reinterpret_cast<uint32_t*>(smem + GF_TABLE_BYTES);
+  const TeamSync sync{1u, 32u * T};
+  for (int64_t it = blockIdx.x; it < a.count; it += gridDim.x) {
+    const MixedItem item = a.items[it];
+    if (item.level == 1) mixed_item_team<Level<1>, T>(gf, ws, wt, lane, sync, a, item);
+    else if (item.level == 3) mixed_item_team<Level<3>, T>(gf, ws, wt, lane, sync, a, item);
+    else if (item.level == 5) mixed_item_team<Level<5>, T>(gf, ws, wt, lane, sync, a, item);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Persistent kernel over the items of ONE level taken from a mixed list
 // (the item list was partitioned by level beforehand).  Static stride:
 // every item of a level costs the same.  Used by the level-partitioned
@@ -487,6 +535,17 @@ cudaError_t launch_mixed(const MixedArgs& a, cudaStream_t st, const LaunchCfg& c
   const int64_t need = (a.count + nw - 1) / nw;
   if (need < g) g = (int)need;
   k_decrypt_mixed<<<g, nw * 32, sm, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mixed_latency(const MixedArgs& a, cudaStream_t st) {
+  if (a.count == 0) return cudaSuccess;
+  if (a.count > MIXED_LATENCY_MAX) return cudaErrorInvalidValue;
+  constexpr int T = LAT_TEAM;
+  const size_t sm = GF_TABLE_BYTES + (size_t)lat_team_words<T>() * 4;
+  cudaError_t e = cudaFuncSetAttribute(k_decrypt_mixed_team<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_decrypt_mixed_team<T><<<(unsigned)a.count, 32 * T, sm, st>>>(a);
   return cudaGetLastError();
 }
 

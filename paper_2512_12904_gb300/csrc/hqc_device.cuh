@@ -688,40 +688,45 @@ __device__ __forceinline__ void decrypt_one(const GF& gf, uint32_t* ws, int lane
 }
 
 // ---------------------------------------------------------------------------
-// Two-warp teams.  Both warps of a team share one doubled operand: each
-// computes half of the product's output words (strips of WPT2 words), the
-// RM blocks spread over the team's 32 lane pairs, and the two warps decode
-// the Reed-Solomon stage of the team's two ciphertexts at the same time.
-// Half the shared memory per warp, so twice the warps fit on an SM (HQC-3
-// and HQC-5 are limited by shared memory, not registers).
-// Members synchronise with a named barrier of 64 threads.
+// Teams of T warps.  The warps of a team share one doubled operand: each
+// lane computes a strip of WPT2 of the product's output words over the
+// team's 32 T lanes, the RM blocks spread over its 16 T lane pairs, and
+// warp i < NI decodes the Reed-Solomon stage of the team's i-th ciphertext
+// of the turn.  With T = 2, NI = 2 (throughput, HQC-5) a warp needs half
+// the shared memory, so twice the warps fit on an SM; with NI = 1 (latency)
+// one ciphertext's serial chain is split over the team.
+// Members synchronise with a named barrier of 32 T threads.
 // ---------------------------------------------------------------------------
 struct TeamSync {
   uint32_t id;
-  __device__ __forceinline__ void operator()() const { asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory"); }
+  uint32_t threads = 64;
+  __device__ __forceinline__ void operator()() const {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+  }
 };
 
-template <class LV>
+template <class LV, int T = 2, int NI = 2>
 struct Team {
-  static constexpr int WPT2 = odd_at_least(cdiv(LV::W_v32, 64));
-  static constexpr int U2W = round_up(cmax(cdiv(2 * LV::n, 32), 64 * WPT2 + (LV::n >> 5) + 1), 4);
+  static constexpr int WPT2 = odd_at_least(cdiv(LV::W_v32, 32 * T));
+  static constexpr int U2W = round_up(cmax(cdiv(2 * LV::n, 32), 32 * T * WPT2 + (LV::n >> 5) + 1), 4);
   static constexpr int RB = cdiv(LV::n1, 4) * 4;  // bytes per stored RM word
-  static constexpr int WORDS = round_up(U2W + LV::WP + 2 * (RB / 4), 4);  // shared words per team
-  static_assert(2 * RS_SCRATCH <= U2W, "two RS scratches fit in u2");
+  static constexpr int WORDS = round_up(U2W + LV::WP + NI * (RB / 4), 4);  // shared words per team
+  static_assert(NI >= 1 && NI <= T, "one RS word per warp at most");
+  static_assert(NI * RS_SCRATCH <= U2W, "the RS scratches fit in u2");
   static_assert(U2W % 4 == 0 && LV::WP % 4 == 0 && WORDS % 4 == 0, "16-byte alignment");
 };
 
-// S1-S7 of one ciphertext by a team (tid in [0, 64)).
-template <class LV, bool MASKED>
+// S1-S7 of one ciphertext by a team (tid in [0, 32 T)).
+template <class LV, bool MASKED, int T = 2>
 __device__ __forceinline__ void product_rm_team(uint32_t* ws, int tid, const TeamSync& sync,
                                                 const uint64_t* __restrict__ urow, const uint64_t* __restrict__ vrow,
                                                 const uint32_t* __restrict__ yrow, uint8_t* r_out) {
-  using T = Team<LV>;
-  constexpr int WPT = T::WPT2, W_v32 = LV::W_v32;
+  using TT = Team<LV, T>;
+  constexpr int WPT = TT::WPT2, W_v32 = LV::W_v32;
   uint32_t* u2 = ws;
-  uint32_t* sup = ws + T::U2W;
-  load_supports<LV::n, LV::w, 64>(sup, yrow, tid);
-  build_doubled<LV::n, LV::W_u_pitch, T::U2W, 64>(u2, urow, tid, sync);
+  uint32_t* sup = ws + TT::U2W;
+  load_supports<LV::n, LV::w, 32 * T>(sup, yrow, tid);
+  build_doubled<LV::n, LV::W_u_pitch, TT::U2W, 32 * T>(u2, urow, tid, sync);
   uint32_t acc[WPT];
   rot_xor_product<WPT, LV::w, MASKED>(u2, sup, tid, acc);
   const uint32_t* v32 = reinterpret_cast<const uint32_t*>(vrow);
@@ -737,27 +742,29 @@ __device__ __forceinline__ void product_rm_team(uint32_t* ws, int tid, const Tea
     if (i < W_v32) u2[i] = acc[k];
   }
   sync();
-  rm_decode_warp<LV, 32>(u2, r_out, tid);
+  rm_decode_warp<LV, 16 * T>(u2, r_out, tid);
   sync();
 }
 
-// Two ciphertexts per turn: product and RM of each by the whole team, then
-// warp wt of the team runs the RS stage of ciphertext wt.
-template <class LV, bool MASKED, class Rows>
+// NI ciphertexts per turn: product and RM of each by the whole team, then
+// warp wt < NI of the team runs the RS stage of ciphertext wt.
+template <class LV, bool MASKED, int T = 2, int NI = 2, class Rows>
 __device__ __forceinline__ void decrypt_team(const GF& gf, uint32_t* ws, int wt, int lane, const TeamSync& sync,
                                              const Rows& rows) {
-  using T = Team<LV>;
+  using TT = Team<LV, T, NI>;
   const int tid = (wt << 5) | lane;
-  uint8_t* rbuf = reinterpret_cast<uint8_t*>(ws + T::U2W + LV::WP);
+  uint8_t* rbuf = reinterpret_cast<uint8_t*>(ws + TT::U2W + LV::WP);
   const uint64_t* u;
   const uint64_t* v;
   const uint32_t* y;
   uint8_t* m;
 #pragma unroll 1
-  for (int g = 0; g < 2; g++)
-    if (rows(g, u, v, y, m)) product_rm_team<LV, MASKED>(ws, tid, sync, u, v, y, rbuf + g * T::RB);
-  const bool act = rows(wt, u, v, y, m);
-  rs_decode_seg<LV, 32, false>(gf, ws + wt * RS_SCRATCH, rbuf + wt * T::RB, lane, act, m, nullptr);
+  for (int g = 0; g < NI; g++)
+    if (rows(g, u, v, y, m)) product_rm_team<LV, MASKED, T>(ws, tid, sync, u, v, y, rbuf + g * TT::RB);
+  if (wt < NI) {
+    const bool act = rows(wt, u, v, y, m);
+    rs_decode_seg<LV, 32, false>(gf, ws + wt * RS_SCRATCH, rbuf + wt * TT::RB, lane, act, m, nullptr);
+  }
   sync();  // the RS scratch lives in u2: the next turn rebuilds it
 }
 

@@ -73,6 +73,10 @@ cudaError_t launch_fused(int level, bool keyed, const DecArgs& a, cudaStream_t s
 cudaError_t launch_staged(int level, bool keyed, const DecArgs& a, uint64_t* w_ws, uint8_t* r_ws, cudaStream_t st);
 cudaError_t launch_debug(int level, const DecArgs& a, const DebugArgs& d, cudaStream_t st);
 cudaError_t launch_mixed(const MixedArgs& a, cudaStream_t st, const LaunchCfg& cfg);
+// Latency form of the mixed kernel: a team of warps per item, one item per
+// team at a time, for batches of at most MIXED_LATENCY_MAX items.
+constexpr int64_t MIXED_LATENCY_MAX = 512;
+cudaError_t launch_mixed_latency(const MixedArgs& a, cudaStream_t st);
 cudaError_t fused_occupancy(int level, bool keyed, const LaunchCfg& cfg, int* warps, int* ctas_per_sm, int* grid);
 // Ciphertexts one full wave of the persistent fused grid decrypts at once.
 cudaError_t fused_wave(int level, bool keyed, const LaunchCfg& cfg, int64_t* items);

@@ -58,7 +58,7 @@ struct Slot {
 
 // Batches of at most this many requests run as one mixed-kernel launch
 // (lowest latency); larger ones as one persistent kernel per level.
-constexpr int64_t kSmallBatch = 512;
+constexpr int64_t kSmallBatch = hqc::MIXED_LATENCY_MAX;
 
 inline int64_t now_ns() {
   return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
@@ -298,8 +298,9 @@ extern "C" int hqc_serve_run(const hqc_serve_cfg_t* cfg, const hqc_keyset_t* con
         e = cudaMemcpyAsync(s.d_items, s.h_items, (size_t)nitems * sizeof(hqc::MixedItem), cudaMemcpyHostToDevice,
                             s.st);
       if (nitems <= kSmallBatch && e == cudaSuccess) {
-        // a small batch: one launch of the mixed kernel on small blocks, so
-        // its items spread over many SMs and finish together
+        // a small batch: one launch of the latency form of the mixed kernel
+        // (a team of warps per item), so its items spread over every SM and
+        // the slowest one's chain is split over its team
         hqc::MixedArgs a;
         a.count = nitems;
         a.items = s.d_items;
@@ -311,9 +312,7 @@ extern "C" int hqc_serve_run(const hqc_serve_cfg_t* cfg, const hqc_keyset_t* con
         }
         a.m = s.d_m;
         a.m_bytes = mbytes;
-        hqc::LaunchCfg small;
-        small.warps_per_cta = 4;
-        e = hqc::launch_mixed(a, s.st, small);
+        e = hqc::launch_mixed_latency(a, s.st);
         for (auto& l : lists) l.clear();
       }
       for (int li = 0; li < 3 && e == cudaSuccess; li++) {
