@@ -174,6 +174,7 @@ __global__ void __launch_bounds__(MIXED_MAX_THREADS, 1) k_decrypt_mixed(MixedArg
 // fits one wave the slowest item sets the time, and its chain is shorter.
 // ---------------------------------------------------------------------------
 constexpr int LAT_TEAM = 4;
+constexpr int64_t MAX_LATENCY_GRID = 65535;
 template <int T>
 __host__ __device__ constexpr int lat_team_words() {
   return cmax(Team<Level<1>, T, 1>::WORDS, cmax(Team<Level<3>, T, 1>::WORDS, Team<Level<5>, T, 1>::WORDS));
@@ -211,6 +212,35 @@ __global__ void __launch_bounds__(32 * T, 4) k_decrypt_mixed_team(MixedArgs a) {
     if (item.level == 1) mixed_item_team<Level<1>, T>(gf, ws, wt, lane, sync, a, item);
     else if (item.level == 3) mixed_item_team<Level<3>, T>(gf, ws, wt, lane, sync, a, item);
     else if (item.level == 5) mixed_item_team<Level<5>, T>(gf, ws, wt, lane, sync, a, item);
+  }
+}
+
+// The same latency form for a batch of one level (literal or keyed
+// supports): block b decodes ciphertexts b, b + grid, ... with its team.
+template <int LEVEL, bool KEYED, int T>
+__global__ void __launch_bounds__(32 * T, 4) k_decrypt_latency(DecArgs a) {
+  using LV = Level<LEVEL>;
+  extern __shared__ __align__(16) uint8_t smem[];
+  gf_tables_init(smem, threadIdx.x, blockDim.x);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wt = threadIdx.x >> 5;
+  const GF gf(smem, lane);
+  uint32_t* ws = reinterpret_cast<uint32_t*>(smem + GF_TABLE_BYTES);
+  const TeamSync sync{1u, 32u * T};
+  for (int64_t it = blockIdx.x; it < a.count; it += gridDim.x) {
+    auto rows = [&](int g, const uint64_t*& u, const uint64_t*& v, const uint32_t*& y, uint8_t*& m) {
+      if (KEYED) {
+        const uint32_t ki = (uint32_t)__ldg(a.key_idx + it);
+        y = a.y + (ki < (uint64_t)a.nkeys ? (int64_t)ki : 0) * LV::w;  // out-of-range index -> key 0
+      } else {
+        y = a.y + it * LV::w;
+      }
+      u = a.u + it * LV::W_u_pitch;
+      v = a.v + it * LV::W_v;
+      m = a.m + it * LV::k;
+      return g == 0;
+    };
+    decrypt_team<LV, !KEYED, T, 1>(gf, ws, wt, lane, sync, rows);
   }
 }
 
@@ -410,6 +440,20 @@ static cudaError_t shape_for(KernelT kern, int max_threads, size_t per_warp, con
   return cudaSuccess;
 }
 
+// Largest batch that runs the latency form (one four-warp team per
+// ciphertext) under the default launch shape.
+template <int LEVEL> struct FusedLatencyMax { static constexpr int64_t count = 512; };
+
+template <int LEVEL, bool KEYED>
+static cudaError_t launch_latency(const DecArgs& a, cudaStream_t st) {
+  constexpr int T = LAT_TEAM;
+  constexpr size_t sm = GF_TABLE_BYTES + (size_t)Team<Level<LEVEL>, T, 1>::WORDS * 4;
+  static_assert(sm <= 48 * 1024, "fits the default dynamic shared memory limit");
+  const int64_t grid = a.count < MAX_LATENCY_GRID ? a.count : MAX_LATENCY_GRID;
+  k_decrypt_latency<LEVEL, KEYED, T><<<(unsigned)grid, 32 * T, sm, st>>>(a);
+  return cudaGetLastError();
+}
+
 template <int LEVEL, bool KEYED>
 static cudaError_t team_level(const DecArgs& a, cudaStream_t st, const LaunchCfg& cfg, bool launch, int* warps,
                               int* ctas, int* grid) {
@@ -446,6 +490,10 @@ static cudaError_t team_level(const DecArgs& a, cudaStream_t st, const LaunchCfg
 template <int LEVEL, bool KEYED>
 static cudaError_t fused_level(const DecArgs& a, cudaStream_t st, const LaunchCfg& cfg, bool launch, int* warps,
                                int* ctas, int* grid) {
+  // a small batch with the default shape: a team of warps per ciphertext
+  if (launch && a.count > 0 && cfg.warps_per_cta == 0 && cfg.ctas_per_sm == 0 &&
+      a.count <= FusedLatencyMax<LEVEL>::count)
+    return launch_latency<LEVEL, KEYED>(a, st);
   if (UseTeam<LEVEL>::value) return team_level<LEVEL, KEYED>(a, st, cfg, launch, warps, ctas, grid);
   int nw = 0, c = 0, g = 0;
   size_t sm = 0;
@@ -542,9 +590,8 @@ cudaError_t launch_mixed_latency(const MixedArgs& a, cudaStream_t st) {
   if (a.count == 0) return cudaSuccess;
   if (a.count > MIXED_LATENCY_MAX) return cudaErrorInvalidValue;
   constexpr int T = LAT_TEAM;
-  const size_t sm = GF_TABLE_BYTES + (size_t)lat_team_words<T>() * 4;
-  cudaError_t e = cudaFuncSetAttribute(k_decrypt_mixed_team<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
+  constexpr size_t sm = GF_TABLE_BYTES + (size_t)lat_team_words<T>() * 4;
+  static_assert(sm <= 48 * 1024, "fits the default dynamic shared memory limit");
   k_decrypt_mixed_team<T><<<(unsigned)a.count, 32 * T, sm, st>>>(a);
   return cudaGetLastError();
 }

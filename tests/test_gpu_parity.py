@@ -75,14 +75,25 @@ def test_debug_path_every_intermediate(hqc, level):
     assert (host(got["m"])[-20:] == wl.m).all()
 
 
+# launch shapes of the single-level path: the default picks the latency form
+# (a four-warp team per ciphertext) for batches of at most 512; an explicit
+# shape runs the persistent fused kernel
+SHAPES = ((0, 0), (4, 0))
+
+
 @pytest.mark.parametrize("level", LEVELS)
-def test_fused_literal_matches_oracle(hqc, level):
+@pytest.mark.parametrize("shape", SHAPES)
+def test_fused_literal_matches_oracle(hqc, level, shape):
     P, u, v, y = adversarial(level, tag=10 + level)
     wl = honest(level, 5, 37, first_ct=900, tag=4)
     u = np.concatenate([u, with_garbage_padding(P, wl.u, tag=5)]); v = np.concatenate([v, wl.v])
     y = np.concatenate([y, wl.y_rows])
     want = oracle.decrypt(level, u, v, y)
-    got = host(hqc.hqc_decrypt_batch(level, u64(u), u64(v), i32(y)))
+    hqc.hqc_set_launch_config(level, *shape)
+    try:
+        got = host(hqc.hqc_decrypt_batch(level, u64(u), u64(v), i32(y)))
+    finally:
+        hqc.hqc_set_launch_config(level, 0, 0)
     assert (got == want).all()
     assert (got[-37:] == wl.m).all()
 
@@ -104,13 +115,35 @@ def test_fused_keyed_and_staged_match_oracle(hqc, level):
 
 
 @pytest.mark.parametrize("level", LEVELS)
-def test_ragged_counts(hqc, level):
+@pytest.mark.parametrize("shape", SHAPES)
+def test_ragged_counts(hqc, level, shape):
     wl = honest(level, 3, 41, first_ct=3000, tag=6)
-    for cnt in (1, 2, 31, 33, 41):
-        got = host(hqc.hqc_decrypt_batch(level, u64(wl.u[:cnt]), u64(wl.v[:cnt]), i32(wl.y_rows[:cnt])))
-        assert (got == wl.m[:cnt]).all(), cnt
-    empty = hqc.hqc_decrypt_batch(level, u64(wl.u[:0]), u64(wl.v[:0]), i32(wl.y_rows[:0]))
-    assert empty.shape == (0, wl.P.k)
+    hqc.hqc_set_launch_config(level, *shape)
+    try:
+        for cnt in (1, 2, 31, 33, 41):
+            got = host(hqc.hqc_decrypt_batch(level, u64(wl.u[:cnt]), u64(wl.v[:cnt]), i32(wl.y_rows[:cnt])))
+            assert (got == wl.m[:cnt]).all(), cnt
+        empty = hqc.hqc_decrypt_batch(level, u64(wl.u[:0]), u64(wl.v[:0]), i32(wl.y_rows[:0]))
+        assert empty.shape == (0, wl.P.k)
+    finally:
+        hqc.hqc_set_launch_config(level, 0, 0)
+
+
+@pytest.mark.parametrize("level", LEVELS)
+def test_latency_form_at_its_limit_and_past_it(hqc, level):
+    """Batches of 512 (the latency form's limit, one team per ciphertext)
+    and 513 (the persistent fused kernel) both match the oracle's messages,
+    keyed with an out-of-range key index in each (read as key 0)."""
+    wl = honest(level, 4, 513, first_ct=12000, tag=13)
+    keys = hqc.Keyset(level, wl.y)
+    kidx = wl.key_idx.astype(np.int32).copy()
+    want = wl.m.copy()
+    kidx[7] = 10 ** 6
+    want[7] = oracle.decrypt(level, wl.u[7:8], wl.v[7:8], wl.y[0:1])[0]
+    for cnt in (512, 513):
+        got = host(hqc.hqc_decrypt_batch_keyed(level, u64(wl.u[:cnt]), u64(wl.v[:cnt]), keys, dev(kidx[:cnt])))
+        assert (got == want[:cnt]).all(), cnt
+    keys.free()
 
 
 @pytest.mark.parametrize("level", LEVELS)
