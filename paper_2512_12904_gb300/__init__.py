@@ -9,6 +9,7 @@ without the compiled library or a CUDA device the calls raise.
 from __future__ import annotations
 
 import ctypes
+import functools
 import os
 import threading
 from dataclasses import dataclass
@@ -171,7 +172,10 @@ class Params:
     W_v: int
 
 
+@functools.lru_cache(maxsize=None)
 def hqc_get_params(level: int) -> Params:
+    """Table I parameters and derived sizes (constant per level, so cached;
+    a bad level raises every time)."""
     p = _Params()
     _check(load().hqc_get_params(level, ctypes.byref(p)))
     return Params(*(int(getattr(p, f)) for f, _ in _Params._fields_))

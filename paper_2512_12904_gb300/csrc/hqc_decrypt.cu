@@ -9,7 +9,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <type_traits>
+#include <utility>
 
 #include "hqc_device.cuh"
 #include "hqc_internal.h"
@@ -400,6 +404,10 @@ template <int LEVEL>
   return (size_t)GF_TABLE_BYTES + (size_t)warps * fused_words<LEVEL>() * 4;
 }
 
+static std::mutex g_shape_mu;
+static std::map<std::pair<const void*, int>, size_t> g_shape_attr;
+static std::map<std::tuple<const void*, int, int, size_t>, int> g_shape_occ;
+
 static int device_props(int* sms, int* smem_optin) {
   int dev = 0;
   cudaGetDevice(&dev);
@@ -414,7 +422,7 @@ template <class KernelT>
 static cudaError_t shape_for(KernelT kern, int max_threads, size_t per_warp, const LaunchCfg& cfg, int* warps,
                              int* ctas, int* grid, size_t* smem_bytes, bool teams = false) {
   int sms = 0, optin = 0;
-  device_props(&sms, &optin);
+  const int dev = device_props(&sms, &optin);
   int nw = cfg.warps_per_cta;
   if (nw <= 0) {
     nw = (int)((optin - GF_TABLE_BYTES) / per_warp);
@@ -425,11 +433,29 @@ static cudaError_t shape_for(KernelT kern, int max_threads, size_t per_warp, con
   if (nw > max_threads / 32 || (teams && nw > 30)) return cudaErrorInvalidValue;
   const size_t sm = GF_TABLE_BYTES + (size_t)nw * per_warp;
   if (sm > (size_t)optin) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
+  // the shared-memory attribute only grows, and occupancies are looked up
+  // once per (kernel, device, warps, bytes): repeated launches of small
+  // batches pay no runtime queries
+  const void* kp = reinterpret_cast<const void*>(kern);
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, nw * 32, sm);
-  if (e != cudaSuccess) return e;
+  {
+    std::lock_guard<std::mutex> lock(g_shape_mu);
+    size_t& attr = g_shape_attr[{kp, dev}];
+    if (sm > attr) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+      attr = sm;
+    }
+    const auto key = std::make_tuple(kp, dev, nw, sm);
+    const auto hit = g_shape_occ.find(key);
+    if (hit != g_shape_occ.end()) {
+      occ = hit->second;
+    } else {
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, nw * 32, sm);
+      if (e != cudaSuccess) return e;
+      g_shape_occ[key] = occ;
+    }
+  }
   if (occ < 1) return cudaErrorInvalidConfiguration;
   int c = cfg.ctas_per_sm > 0 ? cfg.ctas_per_sm : occ;
   if (c > occ) c = occ;

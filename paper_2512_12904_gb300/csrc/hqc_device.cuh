@@ -484,8 +484,17 @@ __device__ __forceinline__ void rs_decode_seg(const GF& gf, uint32_t* rs, const 
       llam[x] = gf.log(lam[x]);
       part ^= gf.mul_l(llam[x], logS[rr - c]);
     }
+    if constexpr (SEG == 32) {
+      part = __reduce_xor_sync(FULL_MASK, part);  // one warp-wide reduction
+    } else if constexpr (SEG == 16) {
+      // two warp-wide reductions, each over one half's partial sums
+      const uint32_t lo = __reduce_xor_sync(FULL_MASK, lane < 16 ? part : 0u);
+      const uint32_t hi = __reduce_xor_sync(FULL_MASK, lane < 16 ? 0u : part);
+      part = lane < 16 ? lo : hi;
+    } else {
 #pragma unroll
-    for (int o = SEG / 2; o > 0; o >>= 1) part ^= __shfl_xor_sync(FULL_MASK, part, o, SEG);
+      for (int o = SEG / 2; o > 0; o >>= 1) part ^= __shfl_xor_sync(FULL_MASK, part, o, SEG);
+    }
     const uint32_t d = part;
     const uint32_t ld = gf.log(d);
     const uint32_t lcoef = sel(d == 0, GF_LOG_ZERO, sel(ld >= lb, ld - lb, ld + 255u - lb));
