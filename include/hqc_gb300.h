@@ -26,8 +26,11 @@
  *     results are ready when the stream reaches the call.
  *   - No entry point allocates device memory, except hqc_keys_register.
  *   - HQC.PKE.Decrypt has no failure output, so m_out is always written.
- *   - Every kernel has data-independent control flow and lane-replicated
- *     GF(2^8) tables (bank-conflict-free for any secret index).
+ *   - Every kernel has data-independent control flow, and no shared-memory
+ *     access pattern depends on secret data: GF(2^8) lookups go through
+ *     lane-replicated (decoder) or per-lane (encoder) tables, every lane of
+ *     a product load reads at the same support entry's offset, and sparse
+ *     vectors are added one entry per step by a single lane.
  *   - Return value: HQC_OK or a negative HQC_E* code; hqc_last_error()
  *     gives a message for the calling thread's last error.
  */

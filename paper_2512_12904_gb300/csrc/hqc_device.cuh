@@ -174,7 +174,12 @@ __device__ __forceinline__ void load_supports(uint32_t* sup, const uint32_t* __r
 // Word i of x^p u is the 32-bit window of u2 at bit 32 i + n - p: two
 // neighbouring u2 words joined by one funnel shift.  The lane's strip of
 // WPT + 1 u2 words is read once per support entry; WPT odd keeps the
-// warp's reads on 32 distinct banks for every rotation.
+// warp's reads on 32 distinct banks for every rotation.  Every lane of a
+// load works on the same support entry, so its 32 addresses are one fixed
+// pattern shifted by that entry's offset: one wavefront whatever the
+// secret positions.  (Lanes working on different entries at once, e.g. to
+// share out a few leftover words, would collide in banks depending on the
+// positions, so the strips cover the product with odd WPT and no tail.)
 // ---------------------------------------------------------------------------
 template <int WPT, int W, bool MASKED>
 __device__ __forceinline__ void rot_xor_product(const uint32_t* u2, const uint32_t* sup, int lane,
@@ -584,48 +589,17 @@ __device__ __forceinline__ void rs_decode_seg(const GF& gf, uint32_t* rs, const 
 // S1-S7 of one ciphertext by one warp: product, XOR with v, RM decode; the
 // n1 RM bytes go to r_out.  ws: U2W + WP words owned by this warp.
 // ---------------------------------------------------------------------------
-// Words [32 WPTM, 32 WPTM + TAIL) of the product (TAIL at most 16), the
-// ones past the 32 strips of WPTM words: lane l takes word 32 WPTM + (l mod
-// TP) over the entries t = l / TP (mod 32 / TP) of the W-entry support, TP =
-// TAIL rounded up to a power of two; shuffles then XOR the lane groups'
-// partial sums, so lane l returns word 32 WPTM + (l mod TP).  Trip counts
-// depend only on the public weight.
-template <int WPTM, int TAIL, int W, bool MASKED>
-__device__ __forceinline__ uint32_t product_tail(const uint32_t* u2, const uint32_t* sup, int lane) {
-  static_assert(TAIL > 0 && TAIL <= 16, "tail of 1..16 words");
-  constexpr int TP = TAIL <= 1 ? 1 : TAIL <= 2 ? 2 : TAIL <= 4 ? 4 : TAIL <= 8 ? 8 : 16;
-  constexpr int NG = 32 / TP;
-  const int grp = lane / TP;
-  const char* base = reinterpret_cast<const char*>(u2 + 32 * WPTM + (lane & (TP - 1)));
-  uint32_t acc = 0;
-#pragma unroll 2
-  for (int t = grp; t < W; t += NG) {
-    const uint2 e = *reinterpret_cast<const uint2*>(sup + 2 * t);
-    const uint32_t* a = reinterpret_cast<const uint32_t*>(base + e.x);
-    const uint32_t f = __funnelshift_r(a[0], a[1], e.y);
-    acc ^= MASKED ? (f & (uint32_t)((int32_t)e.y >> 31)) : f;
-  }
-#pragma unroll
-  for (int o = TP; o < 32; o <<= 1) acc ^= __shfl_xor_sync(FULL_MASK, acc, o);
-  return acc;
-}
-
 template <class LV, bool MASKED>
 __device__ __forceinline__ void product_rm_one(uint32_t* ws, int lane, const uint64_t* __restrict__ urow,
                                                const uint64_t* __restrict__ vrow, const uint32_t* __restrict__ yrow,
                                                uint8_t* r_out) {
-  // a short tail (HQC-1: 17-word strips and 8 tail words instead of 19-word
-  // strips over 608 words) saves the strips' unused words
-  constexpr bool SPLIT = LV::TAIL > 0 && LV::TAIL <= 16;
-  constexpr int WPT = SPLIT ? LV::WPTM : LV::WPT, W_v32 = LV::W_v32;
+  constexpr int WPT = LV::WPT, W_v32 = LV::W_v32;
   uint32_t* u2 = ws;
   uint32_t* sup = ws + LV::U2W;
   load_supports<LV::n, LV::w>(sup, yrow, lane);
   build_doubled<LV::n, LV::W_u_pitch, LV::U2W>(u2, urow, lane);
   uint32_t acc[WPT];
   rot_xor_product<WPT, LV::w, MASKED>(u2, sup, lane, acc);
-  uint32_t tail = 0;
-  if constexpr (SPLIT) tail = product_tail<WPT, LV::TAIL, LV::w, MASKED>(u2, sup, lane);
   // S4: w = v + t, truncated (only the first n1*n2 bits were computed)
   const uint32_t* v32 = reinterpret_cast<const uint32_t*>(vrow);
 #pragma unroll
@@ -633,16 +607,12 @@ __device__ __forceinline__ void product_rm_one(uint32_t* ws, int lane, const uin
     const int i = lane * WPT + k;
     if (i < W_v32) acc[k] ^= __ldcs(v32 + i);
   }
-  if constexpr (SPLIT)
-    if (lane < LV::TAIL) tail ^= __ldcs(v32 + 32 * WPT + lane);
   __syncwarp();
 #pragma unroll
   for (int k = 0; k < WPT; k++) {
     const int i = lane * WPT + k;
     if (i < W_v32) u2[i] = acc[k];
   }
-  if constexpr (SPLIT)
-    if (lane < LV::TAIL) u2[32 * WPT + lane] = tail;
   __syncwarp();
   rm_decode_warp<LV>(u2, r_out, lane);
   __syncwarp();

@@ -20,29 +20,14 @@ template <> struct EncBound<1> { static constexpr int threads = 1024; };
 template <> struct EncBound<3> { static constexpr int threads = 704; };
 template <> struct EncBound<5> { static constexpr int threads = 448; };
 
-// Compact GF(2^8) tables for the RS encoder: exp[0..511] (exp[511] = 0,
-// exp[e] = alpha^(e mod 255) below) and log[0..255] (log 0 = 511), one copy
-// per block.  The encoder's lookups are few, so bank conflicts between
-// lanes cost little, and the 32 KB lane-replicated tables of the decoder
-// would halve the warps a block can hold.
-constexpr int ENC_GF_BYTES = 512 + 512;
-
-__device__ inline void enc_gf_init(uint8_t* smem, int tid) {
-  uint8_t* ex = smem;
-  uint16_t* lg = reinterpret_cast<uint16_t*>(smem + 512);
-  if (tid == 0) {
-    uint32_t x = 1;
-    for (int e = 0; e < 255; e++) {
-      ex[e] = (uint8_t)x;
-      ex[e + 255] = (uint8_t)x;
-      lg[x] = (uint16_t)e;
-      x = gf_xtime(x);
-    }
-    ex[510] = ex[0];  // e = 510 = 2 * 255: alpha^0
-    ex[511] = 0;
-    lg[0] = (uint16_t)GF_LOG_ZERO;
-  }
-}
+// Products of the RS generator's coefficients by a byte, in shared memory
+// for the encoder: lane l of a warp owns coefficients c = l + 32 x, and
+// g_c * b = T[x][0][b & 15] ^ T[x][1][b >> 4] with T[x][h][j] = g_c *
+// (j << 4 h).  Entry (x, h, j) of lane l sits at byte ((2 x + h) 16 + j) 32
+// + l: the warp looks up one j (the feedback byte is the same for every
+// lane), its 32 bytes fill 8 words in 8 different banks, so the access
+// pattern does not depend on the (secret) byte.  NX <= 2: 2 KB per block.
+constexpr int ENC_GF_BYTES = 2 * 1024;
 
 // RS generator g(x) = prod_{i=1}^{2 delta} (x - alpha^i) over GF(2^8) mod
 // x^8 + x^4 + x^3 + x^2 + 1, alpha = x, computed at compile time; the
@@ -81,75 +66,87 @@ struct RsGenLog {
   }
 };
 template <int NR, int C>
-struct RsGenLogAt {
-  static constexpr uint32_t value = RsGenLog<NR>().lg[C];
+struct RsGenAt {
+  static constexpr uint32_t lg = RsGenLog<NR>().lg[C];
+  static constexpr uint32_t value = lg == 511u ? 0u : ce_gf_pow_alpha((int)lg);
 };
-// log g_c for a lane's runtime c, as a chain of selects between
+// g_c for a runtime c (0 past the degree NR), as a chain of selects between
 // compile-time immediates (no table in memory)
 template <int NR, int... C>
-__device__ __forceinline__ uint32_t rs_gen_log_select(int c, std::integer_sequence<int, C...>) {
-  uint32_t v = 511u;
-  ((v = (c == C) ? RsGenLogAt<NR, C>::value : v), ...);
+__device__ __forceinline__ uint32_t rs_gen_select(int c, std::integer_sequence<int, C...>) {
+  uint32_t v = 0u;
+  ((v = (c == C) ? RsGenAt<NR, C>::value : v), ...);
   return v;
+}
+
+// Fill the encoder's product tables (all threads of the block, then
+// __syncthreads).  Only the NR parity coefficients c < NR are used.
+template <class LV>
+__device__ inline void enc_tab_init(uint8_t* tab, int tid, int nthreads) {
+  constexpr int NX = cdiv(LV::NR, 32);
+  static_assert(NX <= 2, "two coefficient columns per lane at most");
+  for (int i = tid; i < NX * 1024; i += nthreads) {
+    const int l = i & 31, j = (i >> 5) & 15, h = (i >> 9) & 1, x = i >> 10;
+    const uint32_t g = rs_gen_select<LV::NR>(l + 32 * x, std::make_integer_sequence<int, LV::NR>{});
+    tab[i] = (uint8_t)ce_gf_mul(g, h ? (uint32_t)j << 4 : (uint32_t)j);
+  }
 }
 
 // Product of the dense row `dense` by the support `supp` (w entries, may
 // be invalid -> masked) over the full n bits, left in u2[0, N32) with the
-// bits >= n of the last word cleared.  A short tail past 32 odd strips
-// (HQC-1: 17-word strips and 9 tail words, HQC-3: 35 and 1) is computed
-// by lane groups instead of widening every strip.
+// bits >= n of the last word cleared.
 template <class LV, int W, bool MASKED = true>
 __device__ __forceinline__ void full_product_to_smem(uint32_t* u2, uint32_t* sup, const uint64_t* dense,
                                                      const uint32_t* supp, int lane) {
-  constexpr int N32 = LV::N32, R = LV::n & 31;
+  constexpr int N32 = LV::N32, R = LV::n & 31, WPT = LV::WPT_FULL;
   constexpr uint32_t LAST = R ? (1u << R) - 1u : ~0u;
-  constexpr bool SPLIT = LV::TAIL_FULL > 0 && LV::TAIL_FULL <= 16;
-  constexpr int WPT = SPLIT ? LV::WPTM_FULL : LV::WPT_FULL;
   load_supports<LV::n, W>(sup, supp, lane);
   build_doubled<LV::n, LV::W_u_pitch, LV::U2W_FULL>(u2, dense, lane);
   uint32_t acc[WPT];
   rot_xor_product<WPT, W, MASKED>(u2, sup, lane, acc);
-  uint32_t tail = 0;
-  if constexpr (SPLIT) tail = product_tail<WPT, LV::TAIL_FULL, W, MASKED>(u2, sup, lane);
   __syncwarp();
 #pragma unroll
   for (int k = 0; k < WPT; k++) {
     const int i = lane * WPT + k;
     if (i < N32) u2[i] = i == N32 - 1 ? (acc[k] & LAST) : acc[k];
   }
-  if constexpr (SPLIT) {
-    const int i = 32 * WPT + lane;
-    if (lane < LV::TAIL_FULL) u2[i] = i == N32 - 1 ? (tail & LAST) : tail;
-  }
   __syncwarp();
 }
 
 // The W_v32 words of the product truncated to n1 n2 bits, left in
-// u2[0, W_v32); the same strip and tail split as decryption's product.
+// u2[0, W_v32).
 template <class LV, int W, bool MASKED>
 __device__ __forceinline__ void truncated_product_to_smem(uint32_t* u2, const uint32_t* sup, int lane) {
-  constexpr bool SPLIT = LV::TAIL > 0 && LV::TAIL <= 16;
-  constexpr int WPT = SPLIT ? LV::WPTM : LV::WPT;
+  constexpr int WPT = LV::WPT;
   uint32_t acc[WPT];
   rot_xor_product<WPT, W, MASKED>(u2, sup, lane, acc);
-  uint32_t tail = 0;
-  if constexpr (SPLIT) tail = product_tail<WPT, LV::TAIL, W, MASKED>(u2, sup, lane);
   __syncwarp();
 #pragma unroll
   for (int k = 0; k < WPT; k++) {
     const int i = lane * WPT + k;
     if (i < LV::W_v32) u2[i] = acc[k];
   }
-  if constexpr (SPLIT)
-    if (lane < LV::TAIL) u2[32 * WPT + lane] = tail;
   __syncwarp();
 }
 
+// XOR the bits of a W-entry support into out (NBITS bits).  Lanes writing
+// at once would collide in banks according to the secret positions, so the
+// entries are applied one per step by lane 0 alone, with one shared load
+// and one store every step; an entry at or past NBITS adds 0 to word 0.
+// The accesses and their timing do not depend on the positions.
 template <int W, int NBITS>
 __device__ __forceinline__ void xor_support_bits(uint32_t* out, const uint32_t* supp, int lane) {
-  for (int t = lane; t < W; t += 32) {
-    const uint32_t p = __ldg(supp + t);
-    if (p < (uint32_t)NBITS) atomicXor(out + (p >> 5), 1u << (p & 31));
+  constexpr int NJ = cdiv(W, 32);
+  uint32_t pj[NJ];
+#pragma unroll
+  for (int j = 0; j < NJ; j++) pj[j] = lane + 32 * j < W ? __ldg(supp + lane + 32 * j) : 0u;
+#pragma unroll
+  for (int t = 0; t < W; t++) {
+    const uint32_t p = __shfl_sync(FULL_MASK, pj[t >> 5], t & 31);
+    const bool ok = p < (uint32_t)NBITS;
+    const uint32_t q = sel(ok, p >> 5, 0u);
+    const uint32_t bit = sel(ok, 1u << (p & 31), 0u);
+    if (lane == 0) out[q] ^= bit;
   }
   __syncwarp();
 }
@@ -194,18 +191,20 @@ __device__ __forceinline__ uint32_t rm_codeword_word(uint32_t B, int t) {
 }
 
 // RS systematic encoding of the k-byte row m by the division register (one
-// warp; lane owns parity coefficient c = lane + 32 x, lgc its generator
-// log), written as the codeword (parity || message) to cw.
+// warp; lane owns parity coefficient c = lane + 32 x, tab the block's
+// product tables), written as the codeword (parity || message) to cw.
 template <class LV>
-__device__ __forceinline__ void enc_rs_encode(const uint8_t* __restrict__ mrow, const uint32_t (&lgc)[cdiv(LV::NR, 32)],
-                                              const uint8_t* gex, const uint16_t* glg, int lane, uint8_t* cw) {
+__device__ __forceinline__ void enc_rs_encode(const uint8_t* __restrict__ mrow, const uint8_t* tab, int lane,
+                                              uint8_t* cw) {
   constexpr int NR = LV::NR, k = LV::k, NX = cdiv(NR, 32);
   uint32_t par[NX];
 #pragma unroll
   for (int x = 0; x < NX; x++) par[x] = 0;
+  const uint8_t* tl = tab + lane;
   for (int i = k - 1; i >= 0; i--) {
     const uint32_t top = __shfl_sync(FULL_MASK, par[(NR - 1) / 32], (NR - 1) % 32);
-    const uint32_t lfb = glg[(uint32_t)mrow[i] ^ top];
+    const uint32_t fb = (uint32_t)mrow[i] ^ top;  // the feedback byte, the same in every lane
+    const uint32_t lo = (fb & 15u) << 5, hi = 512u + ((fb >> 4) << 5);
     uint32_t nxt[NX];
 #pragma unroll
     for (int x = 0; x < NX; x++) {
@@ -213,7 +212,8 @@ __device__ __forceinline__ void enc_rs_encode(const uint8_t* __restrict__ mrow, 
       const uint32_t carry = x > 0 ? __shfl_sync(FULL_MASK, par[x > 0 ? x - 1 : 0], 31) : 0u;
       const int c = lane + 32 * x;
       const uint32_t prev = lane == 0 ? carry : up;
-      nxt[x] = c < NR ? (prev ^ (uint32_t)gex[min(lgc[x] + lfb, GF_LOG_ZERO)]) : 0u;
+      const uint32_t gfb = (uint32_t)tl[1024 * x + lo] ^ (uint32_t)tl[1024 * x + hi];  // g_c * fb
+      nxt[x] = c < NR ? (prev ^ gfb) : 0u;
     }
 #pragma unroll
     for (int x = 0; x < NX; x++) par[x] = nxt[x];
@@ -258,21 +258,14 @@ __global__ void __launch_bounds__(EncBound<LEVEL>::threads, 1) k_encrypt(int64_t
                                                         const uint64_t* __restrict__ u_in,
                                                         const uint64_t* __restrict__ v_in, uint32_t* __restrict__ ok) {
   using LV = Level<LEVEL>;
-  constexpr int NR = LV::NR, n1 = LV::n1, k = LV::k;
+  constexpr int k = LV::k;
   constexpr int WARP_W = LV::U2W_FULL + LV::WP_R;
-  constexpr int NX = cdiv(NR, 32);
   extern __shared__ __align__(16) uint8_t smem[];
-  enc_gf_init(smem, threadIdx.x);
+  enc_tab_init<LV>(smem, threadIdx.x, blockDim.x);
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const uint8_t* gex = smem;
-  const uint16_t* glg = reinterpret_cast<const uint16_t*>(smem + 512);
   uint32_t* u2 = reinterpret_cast<uint32_t*>(smem + ENC_GF_BYTES) + warp * WARP_W;
   uint32_t* sup = u2 + LV::U2W_FULL;
-  // log g_c of the parity coefficients c = lane + 32 x this lane owns
-  uint32_t lgc[NX];
-#pragma unroll
-  for (int x = 0; x < NX; x++) lgc[x] = rs_gen_log_select<NR>(lane + 32 * x, std::make_integer_sequence<int, NR>{});
   for (int64_t it = (int64_t)blockIdx.x * nw + warp; it < count; it += (int64_t)gridDim.x * nw) {
     const uint32_t ki = (uint32_t)key_idx[it];
     const int64_t key = ki < (uint64_t)nkeys ? (int64_t)ki : 0;
@@ -300,7 +293,7 @@ __global__ void __launch_bounds__(EncBound<LEVEL>::threads, 1) k_encrypt(int64_t
     truncated_product_to_smem<LV, LV::wr, !VALID>(u2, sup, lane);
     xor_support_bits<LV::we, LV::n1 * LV::n2>(u2, e + it * LV::we, lane);
 
-    enc_rs_encode<LV>(m + it * k, lgc, gex, glg, lane, reinterpret_cast<uint8_t*>(u2 + LV::W_v32));
+    enc_rs_encode<LV>(m + it * k, smem, lane, reinterpret_cast<uint8_t*>(u2 + LV::W_v32));
     __syncwarp();
     enc_rm_encode<LV, 32>(u2, lane);
     __syncwarp();
@@ -339,21 +332,16 @@ __global__ void __launch_bounds__(EncTeamBound<LEVEL>::threads, 1)
                    const uint64_t* __restrict__ v_in, uint32_t* __restrict__ ok) {
   using LV = Level<LEVEL>;
   using T = ETeam<LV>;
-  constexpr int NR = LV::NR, NX = cdiv(NR, 32), WPT = T::WPT2, RB = LV::n & 31;
+  constexpr int WPT = T::WPT2, RB = LV::n & 31;
   extern __shared__ __align__(16) uint8_t smem[];
-  enc_gf_init(smem, threadIdx.x);
+  enc_tab_init<LV>(smem, threadIdx.x, blockDim.x);
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int team = warp >> 1, wt = warp & 1, tid = wt * 32 + lane, nteams = blockDim.x >> 6;
-  const uint8_t* gex = smem;
-  const uint16_t* glg = reinterpret_cast<const uint16_t*>(smem + 512);
   uint32_t* u2 = reinterpret_cast<uint32_t*>(smem + ENC_GF_BYTES) + team * T::WORDS;
   uint32_t* sup = u2 + T::U2W;
   uint32_t* flag = sup + LV::WP_R;
   const TeamSync sync{(uint32_t)(1 + team)};
-  uint32_t lgc[NX];
-#pragma unroll
-  for (int x = 0; x < NX; x++) lgc[x] = rs_gen_log_select<NR>(lane + 32 * x, std::make_integer_sequence<int, NR>{});
   for (int64_t it = (int64_t)blockIdx.x * nteams + team; it < count; it += (int64_t)gridDim.x * nteams) {
     const uint32_t ki = (uint32_t)key_idx[it];
     const int64_t key = ki < (uint64_t)nkeys ? (int64_t)ki : 0;
@@ -397,7 +385,7 @@ __global__ void __launch_bounds__(EncTeamBound<LEVEL>::threads, 1)
     sync();
     if (wt == 0) {
       xor_support_bits<LV::we, LV::n1 * LV::n2>(u2, e + it * LV::we, lane);
-      enc_rs_encode<LV>(m + it * LV::k, lgc, gex, glg, lane, reinterpret_cast<uint8_t*>(u2 + LV::W_v32));
+      enc_rs_encode<LV>(m + it * LV::k, smem, lane, reinterpret_cast<uint8_t*>(u2 + LV::W_v32));
     }
     sync();
     enc_rm_encode<LV, 64>(u2, tid);
@@ -405,7 +393,9 @@ __global__ void __launch_bounds__(EncTeamBound<LEVEL>::threads, 1)
     if constexpr (CMP) {
       const uint32_t* vi = reinterpret_cast<const uint32_t*>(v_in + it * LV::W_v);
       for (int i = tid; i < LV::W_v32; i += 64) diff |= __ldg(vi + i) ^ u2[i];
-      if (__any_sync(FULL_MASK, diff != 0u) && lane == 0) atomicOr(flag, 1u);
+      // every warp adds its result, 0 or 1: no branch on the comparison
+      const uint32_t differs = __any_sync(FULL_MASK, diff != 0u) ? 1u : 0u;
+      if (lane == 0) atomicOr(flag, differs);
       sync();
       if (tid == 0) ok[it] = *flag ? 0u : 1u;
     } else {

@@ -24,7 +24,6 @@ template <> struct LevelConst<5> {
 
 __host__ __device__ constexpr int cdiv(int a, int b) { return (a + b - 1) / b; }
 __host__ __device__ constexpr int odd_at_least(int x) { return x | 1; }
-__host__ __device__ constexpr int odd_at_most(int x) { return (x & 1) ? x : x - 1; }
 __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 __host__ __device__ constexpr int round_up(int a, int b) { return cdiv(a, b) * b; }
 
@@ -53,10 +52,6 @@ template <int LEVEL> struct Level : LevelConst<LEVEL> {
   // output words of the truncated product per lane (odd -> a warp's
   // strided shared-memory reads hit 32 distinct banks)
   static constexpr int WPT = odd_at_least(cdiv(W_v32, 32));
-  // decryption's split of the W_v32 product words: 32 strips of WPTM (odd,
-  // at most W_v32 / 32 words) and TAIL < 32 words shared by lane groups
-  static constexpr int WPTM = odd_at_most(W_v32 / 32);
-  static constexpr int TAIL = W_v32 - 32 * WPTM;
   // highest u2 word a lane may read: 32*WPT - 1 + (n >> 5) + 1
   static constexpr int U2W = round_up(cmax(cdiv(2 * C::n, 32), 32 * WPT + (C::n >> 5) + 1), 4);
   static constexpr int WP = round_up(2 * C::w, 4);    // two words per support entry
@@ -64,9 +59,6 @@ template <int LEVEL> struct Level : LevelConst<LEVEL> {
   // full-length (n-bit) product used by key generation and encryption
   static constexpr int WPT_FULL = odd_at_least(cdiv(N32, 32));
   static constexpr int U2W_FULL = round_up(cmax(cdiv(2 * C::n, 32), 32 * WPT_FULL + (C::n >> 5) + 1), 4);
-  // the same split of the N32 words of the full-length product
-  static constexpr int WPTM_FULL = odd_at_most(N32 / 32);
-  static constexpr int TAIL_FULL = N32 - 32 * WPTM_FULL;
   static constexpr int WP_R = round_up(2 * C::wr, 4);
   static_assert(C::n1 * n2 % 64 == 0, "v is a whole number of words");
   static_assert(C::n1 - C::k == NR, "RS code has n1 - k = 2 delta");
