@@ -199,14 +199,21 @@ def test_mixed_levels_one_launch(hqc):
         m_off += wl.P.k
     arena = np.concatenate(arena)
     keys = [hqc.Keyset(l, parts[l].y) for l in (1, 3, 5)]
-    m_arena = torch.full((m_off,), 0xAA, dtype=torch.uint8, device="cuda")
-    hqc.hqc_decrypt_mixed(dev(items.view(np.uint8)), u64(arena), keys, m_arena)
-    got = host(m_arena)
-    pos = 0
-    for lvl, i in seq:
-        k = parts[lvl].P.k
-        assert (got[pos: pos + k] == parts[lvl].m[i]).all()
-        pos += k
+    # the default shape runs this 100-item batch in the latency form (a team
+    # per item); an explicit shape runs the one-warp-per-item mixed kernel
+    for shape in SHAPES:
+        hqc.hqc_set_launch_config(0, *shape)
+        try:
+            m_arena = torch.full((m_off,), 0xAA, dtype=torch.uint8, device="cuda")
+            hqc.hqc_decrypt_mixed(dev(items.view(np.uint8)), u64(arena), keys, m_arena)
+            got = host(m_arena)
+        finally:
+            hqc.hqc_set_launch_config(0, 0, 0)
+        pos = 0
+        for lvl, i in seq:
+            k = parts[lvl].P.k
+            assert (got[pos: pos + k] == parts[lvl].m[i]).all(), shape
+            pos += k
     # an item with an out-of-range key is skipped, the rest still decrypt
     items2 = items.copy()
     items2[0]["key"] = 10 ** 6
