@@ -77,7 +77,9 @@ const char* hqc_last_error(void);
  * (Algorithm 2): y is [count][w] uint32 positions of the secret y of each
  * ciphertext.  Entries >= n contribute nothing; repeated entries cancel
  * (the product is a XOR of rotations, Eq. 1).  u [count][W_u_pitch],
- * v [count][W_v], m_out [count][k].  One persistent fused kernel. */
+ * v [count][W_v], m_out [count][k].  One persistent fused kernel; with the
+ * default launch shape, a batch of at most 512 runs the latency form
+ * instead (one block of four warps per ciphertext, same results). */
 int hqc_decrypt_batch(int level, int64_t count, const uint64_t* u, const uint64_t* v, const uint32_t* y,
                       uint8_t* m_out, void* stream);
 
