@@ -147,3 +147,25 @@ def test_decaps_accepts_honest_and_rejects_implicitly(level):
     assert not oks.any()
     _, okk = oracle.kem_decaps(level, h, s, y, sigma, (kidx + 1) % 3, u, v, salt)
     assert not okk.any()
+
+
+def test_fixed_weight_full_size_marginals_are_uniform():
+    """At full size (HQC-1, w_e = 75 of n = 17,669) every position is in the
+    support with probability w / n: over 3,000 supports drawn from seeded
+    32-bit words, the counts in 32 equal bins pass a chi-square test, and
+    both ends of [0, n) occur (an off-by-one in pos_i = i + floor(R_i (n - i)
+    / 2^32) would lose n - 1 or shift mass between the bins)."""
+    from scipy.stats import chi2
+    P = oracle.params(1)
+    n, w, trials = P.n, P.we, 3000
+    counts = np.zeros(n, np.int64)
+    for idx in range(trials):
+        R = synth.words(w, tag=93, index=idx).astype(np.uint32)
+        counts[oracle.fixed_weight(n, w, R)] += 1
+    assert counts.sum() == trials * w
+    assert counts[0] > 0 and counts[n - 1] > 0
+    edges = np.linspace(0, n, 33).astype(np.int64)
+    observed = np.array([counts[a:b].sum() for a, b in zip(edges[:-1], edges[1:])], np.float64)
+    expected = trials * w * np.diff(edges) / n
+    stat = float(((observed - expected) ** 2 / expected).sum())
+    assert chi2.sf(stat, df=31) > 1e-4, stat
