@@ -121,6 +121,25 @@ def test_eq1_matches_schoolbook(n):
         assert (got == _schoolbook(n, a1, a2)).all()
 
 
+@pytest.mark.parametrize("level", [1, 3, 5])
+def test_eq1_matches_schoolbook_at_full_size(level):
+    """Eq. 1 at the full ring length (n = 17,669 / 35,851 / 57,637),
+    w entries against a dense convolution over GF(2) folded mod x^n - 1:
+    the word boundaries and the wrap at n are exercised where they are
+    used."""
+    P = oracle.params(level)
+    n = P.n
+    a2 = (synth.words(n, tag=300 + level) & 1).astype(np.uint8)
+    supp = synth.support(n, P.w, tag=301 + level, index=0)
+    a1 = np.zeros(n, np.uint8)
+    a1[supp] = 1
+    full = np.convolve(a1.astype(np.int64), a2.astype(np.int64)) & 1
+    want = full[:n].copy()
+    want[: full.size - n] ^= full[n:]
+    got = oracle.ring_mul_sparse_bits(n, a2, supp)
+    assert (got == want.astype(np.uint8)).all()
+
+
 @pytest.mark.parametrize("n", range(2, 13))
 def test_eq1_exhaustive_small_n(n):
     # every a2 in GF(2)^n against every single rotation and a fixed pair
