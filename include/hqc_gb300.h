@@ -122,9 +122,14 @@ int hqc_decrypt_batch_staged(int level, int64_t count, const uint64_t* u, const 
  *     (8 W_v + n1): 7443 (HQC-1), 3698 (HQC-3), 2301 (HQC-5) per call.  A
  *     larger count returns HQC_EINVAL (message in hqc_last_error) and
  *     launches nothing.
+ *   - Device: the call works on the CURRENT device (cudaSetDevice); u, v,
+ *     the keys, m_out and the stream must belong to it.
  *   - First call on a device: it looks up the array's device address with
  *     cudaGetSymbolAddress once (per device, that device current), so make
- *     that first call outside any stream capture.
+ *     that first call outside any stream capture.  The address is cached
+ *     for the life of the process; do not call this entry point again
+ *     after cudaDeviceReset in the same process (the cached address would
+ *     point into the destroyed context).
  *   - Sharing: every call on a device uses the same array, and each call
  *     overwrites all of the part it reads before reading it (nothing needs
  *     to start at zero).  Calls whose work overlaps on the GPU -- two

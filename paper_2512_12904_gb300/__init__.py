@@ -304,10 +304,14 @@ def hqc_decrypt_batch_staged_noalloc(level, u, v, y=None, keys: Keyset = None, k
     else:
         y = y.view(torch.int32) if y.dtype == torch.uint32 else y
         yp = _dev_ptr(y, torch.int32, (cnt, P.w), "y")
-    _check(load().hqc_decrypt_batch_staged_noalloc(level, cnt, _dev_ptr(u, torch.int64, (cnt, P.W_u_pitch), "u"),
-                                                   _dev_ptr(v, torch.int64, (cnt, P.W_v), "v"), yp, kp, ip,
-                                                   _dev_ptr(m_out, torch.uint8, (cnt, P.k), "m_out"),
-                                                   _stream(stream)))
+    # the library resolves its compiled-in scratch on the current device:
+    # make that the device the tensors live on
+    with torch.cuda.device(u.device):
+        _check(load().hqc_decrypt_batch_staged_noalloc(level, cnt,
+                                                       _dev_ptr(u, torch.int64, (cnt, P.W_u_pitch), "u"),
+                                                       _dev_ptr(v, torch.int64, (cnt, P.W_v), "v"), yp, kp, ip,
+                                                       _dev_ptr(m_out, torch.uint8, (cnt, P.k), "m_out"),
+                                                       _stream(stream)))
     return m_out
 
 

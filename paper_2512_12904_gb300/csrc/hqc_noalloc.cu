@@ -31,7 +31,10 @@ void* g_dev_ptr[kMaxDevices] = {nullptr};
 
 // Device address of the scratch on the current device.  In host code the
 // array's name is only a host-side stand-in, so the address has to come
-// from the runtime, once per device, with that device current.
+// from the runtime, once per device, with that device current.  The cache
+// lives as long as the process: after cudaDeviceReset (which destroys the
+// context that held the array) the cached address is stale.  Unsafe to call
+// after cudaDeviceReset in the same process.
 cudaError_t scratch_on_current_device(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -46,6 +49,19 @@ cudaError_t scratch_on_current_device(void** out) {
   }
   *out = g_dev_ptr[dev];
   return cudaSuccess;
+}
+
+// Largest count whose per-stage workspace (the same formula the
+// allocating entry point checks against) fits the compiled-in array: the
+// closed-form estimate, stepped down until hqc_staged_workspace_bytes
+// agrees, so the limit follows any change to the workspace layout.
+int64_t noalloc_max_count(int level) {
+  hqc_params_t p;
+  if (hqc_get_params(level, &p) != HQC_OK) return 0;
+  const size_t per_ct = (size_t)p.W_v * 8 + (size_t)p.n1;
+  int64_t c = (int64_t)(HQC_NOALLOC_SCRATCH_BYTES / per_ct) + 1;
+  while (c > 0 && hqc_staged_workspace_bytes(level, c) > (size_t)HQC_NOALLOC_SCRATCH_BYTES) c--;
+  return c;
 }
 
 // Record the message for hqc_last_error() and return the code.
@@ -68,9 +84,7 @@ extern "C" int hqc_decrypt_batch_staged_noalloc(int level, int64_t count, const 
   if (hqc_get_params(level, &p) != HQC_OK) return nfail(HQC_EINVAL, "level must be 1, 3 or 5 (got %d)", level);
   if (count < 0) return nfail(HQC_EINVAL, "count must be >= 0");
   if (count == 0) return HQC_OK;
-  // scratch layout: w [count][W_v] words, then r [count][n1] bytes
-  const size_t per_ct = (size_t)p.W_v * 8 + (size_t)p.n1;
-  const int64_t max_count = (int64_t)((HQC_NOALLOC_SCRATCH_BYTES - 16) / per_ct);
+  const int64_t max_count = noalloc_max_count(level);
   if (count > max_count)
     return nfail(HQC_EINVAL,
                  "count %lld exceeds the static scratch: %d bytes hold at most %lld HQC-%d ciphertexts per call",

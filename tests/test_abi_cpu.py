@@ -184,3 +184,19 @@ def test_serving_argument_checks_without_a_gpu():
     assert b"stall_ms" in lib.hqc_last_error()
     assert call(hqc._ServeCfg(0, 1, 1 << 20, 1, 0, 0)) == hqc.HQC_EINVAL
     assert call(hqc._ServeCfg(1, 1, 0, 1, 0, 0)) == hqc.HQC_EINVAL
+
+
+@pytest.mark.parametrize("level,limit", [(1, 7443), (3, 3698), (5, 2301)])
+def test_noalloc_limit_is_the_largest_count_whose_workspace_fits(level, limit):
+    """The allocation-free entry point's count limit and the per-stage
+    workspace formula agree: the limit's workspace fits the compiled-in
+    array and one more ciphertext's does not.  Counts beyond the limit are
+    refused on the host, before any launch."""
+    lib = hqc.load()
+    scratch = 16 << 20
+    assert lib.hqc_staged_workspace_bytes(level, limit) <= scratch < lib.hqc_staged_workspace_bytes(level, limit + 1)
+    p16 = ctypes.c_void_p(16)
+    rc = lib.hqc_decrypt_batch_staged_noalloc(level, limit + 1, p16, p16, p16, None, None, p16, None)
+    assert rc == -1
+    msg = lib.hqc_last_error()
+    assert b"exceeds the static scratch" in msg and str(limit).encode() in msg
