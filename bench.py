@@ -67,6 +67,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU-baseline duration")
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="trace length per offered load (serving)")
+    ap.add_argument("--configs", choices=["auto", "all", "none"], default="auto",
+                    help="also measure every other benchmark configuration (auto: with the default workload at N=1)")
     return ap.parse_args()
 
 
@@ -177,36 +179,20 @@ def make_workload(hqc, level, count, nkeys, rank, device):
     return P, keys, u_d, v_d, k_d, m_d, y, kidx
 
 
-def timed_steps(fn, steps, stream, dist, clocks_idx=None):
-    """Run fn() `steps` times between barriers; return (total_ms, per-step ms list, clocks)."""
-    import torch
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
-    dist.barrier()
-    torch.cuda.synchronize()
-    clk = Clocks(clocks_idx) if clocks_idx is not None else None
-    with torch.cuda.stream(stream):
-        evs[0].record(stream)
-        for i in range(steps):
-            fn()
-            evs[i + 1].record(stream)
-    torch.cuda.synchronize()
-    dist.barrier()
-    clocks = clk.stop() if clk else None
-    per = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
-    return evs[0].elapsed_time(evs[-1]), per, clocks
-
-
 def pct(xs, q):
     s = sorted(xs)
     return s[min(len(s) - 1, int(round(q / 100.0 * (len(s) - 1))))]
 
 
 def load_peaks():
+    """On-chip peaks measured once in this run (libhqc_peaks.so)."""
     from paper_2512_12904_gb300 import _build
     lib = ctypes.CDLL(_build.PEAKS_LIB)
-    lib.hqc_peak_smem_read_bytes_per_s.restype = ctypes.c_double
-    lib.hqc_peak_int_ops_per_s.restype = ctypes.c_double
-    return lib.hqc_peak_smem_read_bytes_per_s(), lib.hqc_peak_int_ops_per_s()
+    for f in ("hqc_peak_smem_read_bytes_per_s", "hqc_peak_int_ops_per_s", "hqc_peak_int_issue_ops_per_s"):
+        getattr(lib, f).restype = ctypes.c_double
+    return {"smem_bytes_per_s": lib.hqc_peak_smem_read_bytes_per_s(),
+            "alu_ops_per_s": lib.hqc_peak_int_ops_per_s(),
+            "issue_ops_per_s": lib.hqc_peak_int_issue_ops_per_s()}
 
 
 def measured_peaks_file():
@@ -353,19 +339,262 @@ def run_reference_kem(args):
 # ---------------------------------------------------------------------------
 # the GPU arm
 # ---------------------------------------------------------------------------
-def run_mixed(args):
+class Ctx:
+    """What every GPU measurement of one bench process shares: the rank's
+    device, the library, the on-chip peaks measured once in this run, and an
+    L2 flush buffer for workloads smaller than L2."""
+
+    def __init__(self, args):
+        import torch
+        import paper_2512_12904_gb300 as hqc
+        self.args = args
+        self.dist = Dist(args.gpus)
+        self.device = torch.device("cuda", self.dist.local)
+        torch.cuda.set_device(self.device)
+        hqc.load()
+        self.hqc = hqc
+        self.peaks = load_peaks()
+        self.hbm_peak = measured_peaks_file().get("hbm_gbs")
+        self._flush = None
+
+    def flush_l2(self):
+        """Overwrite a buffer twice the size of L2 (on the current stream)."""
+        import torch
+        if self._flush is None:
+            self._flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=self.device)
+        self._flush.fill_(0x5A5A5A5A)
+
+    def roofline(self, smem_b, int_ops, hbm_b, seconds, kernel, traffic=None):
+        """Roofline of a measured launch: algorithmic work ÷ its time against
+        the peaks measured in this run (ALU pipe, ALU+FMA issue, shared
+        memory) and MEASURED_PEAKS.json's HBM bandwidth."""
+        smem_peak = self.peaks["smem_bytes_per_s"] / 1e9
+        alu_peak = self.peaks["alu_ops_per_s"] / 1e9
+        issue_peak = self.peaks["issue_ops_per_s"] / 1e9
+        smem_ach = smem_b / seconds / 1e9
+        int_ach = int_ops / seconds / 1e9
+        hbm_ach = hbm_b / seconds / 1e9
+        blocks = {
+            "smem": {"bound": "smem", "achieved": smem_ach, "peak": smem_peak, "unit": "GB/s",
+                     "frac": smem_ach / smem_peak if smem_peak else None, "traffic": None,
+                     "peak_source": "measured in this run: conflict-free 32-bit shared-memory loads, all SMs"},
+            "alu": {"bound": "alu", "achieved": int_ach, "peak": alu_peak, "unit": "Gop/s",
+                    "frac": int_ach / alu_peak if alu_peak else None,
+                    "peak_source": "measured in this run: 32-bit funnel-shift + XOR issue rate, all SMs "
+                                   "(the integer ALU pipe alone)",
+                    "issue": {"peak": issue_peak, "frac": int_ach / issue_peak if issue_peak else None,
+                              "peak_source": "measured in this run: half funnel-shift/XOR (ALU pipe), half "
+                                             "IMAD (FMA pipe), all SMs: the integer issue ceiling of both pipes"}},
+            "hbm": {"bound": "hbm", "achieved": hbm_ach, "peak": self.hbm_peak, "unit": "GB/s",
+                    "frac": hbm_ach / self.hbm_peak if self.hbm_peak else None,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if self.hbm_peak else "absent"},
+        }
+        primary = max(("smem", "alu"), key=lambda k: blocks[k]["frac"] or 0)
+        roof = dict(blocks[primary])
+        roof["kernel"] = kernel
+        roof["traffic"] = traffic
+        roof["others"] = {k: v for k, v in blocks.items() if k != primary}
+        return roof
+
+
+def timed_steps(fn, steps, stream, dist, clocks_idx=None, flush=None):
+    """Run fn() `steps` times between barriers; return (total_ms, per-step ms
+    list, clocks).  With flush, flush() runs between steps outside the
+    events, and total_ms is the sum of the steps' own times."""
+    import torch
+    dist.barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(clocks_idx) if clocks_idx is not None else None
+    with torch.cuda.stream(stream):
+        if flush is None:
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+            evs[0].record(stream)
+            for i in range(steps):
+                fn()
+                evs[i + 1].record(stream)
+        else:
+            pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                     for _ in range(steps)]
+            for a, b in pairs:
+                flush()
+                a.record(stream)
+                fn()
+                b.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clocks = clk.stop() if clk else None
+    if flush is None:
+        per = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
+        return evs[0].elapsed_time(evs[-1]), per, clocks
+    per = [a.elapsed_time(b) for a, b in pairs]
+    return sum(per), per, clocks
+
+
+def warm(fn, n, stream):
+    import torch
+    with torch.cuda.stream(stream):
+        for _ in range(n):
+            fn()
+    torch.cuda.synchronize()
+
+
+def decrypt_kernel_name(level, count):
+    """The kernel hqc_decrypt_batch_keyed runs for this batch (default shape)."""
+    if count <= 512:
+        return "k_decrypt_latency<%d,keyed,4>" % level
+    return ("k_decrypt_team<%d,keyed>" if level == 5 else "k_decrypt_fused<%d,keyed>") % level
+
+
+def sub_steps(args):
+    """Steps of a sub-configuration: the driver's K, bounded to keep the
+    default run within a few minutes."""
+    return max(5, min(args.steps, 50)), max(3, args.warmup)
+
+
+def bench_single(ctx, wl_name, full):
+    """One level: the fused batched form (the keyed entry point) against the
+    plain per-stage form on the same inputs, every m checked."""
+    import torch
+    hqc, dist, args, device = ctx.hqc, ctx.dist, ctx.args, ctx.device
+    level, count, nkeys, desc = WORKLOADS[wl_name]
+    P, keys, u_d, v_d, k_d, m_ref, y_host, kidx = make_workload(hqc, level, count, nkeys, dist.rank, device)
+    m_out = torch.empty_like(m_ref)
+    stream = torch.cuda.Stream(device=device)
+    in_bytes = (u_d.numel() + v_d.numel()) * 8
+    flush = ctx.flush_l2 if in_bytes <= L2_BYTES else None
+    l2 = ("inputs (%d MB) larger than L2 (129 MB); no flush" % (in_bytes // 2 ** 20) if flush is None else
+          "inputs (%.1f MB) smaller than L2: a 258 MB buffer is overwritten between timed steps, outside the "
+          "events; value = count x steps / sum of the steps' own times" % (in_bytes / 2 ** 20))
+    steps, warmup = (args.steps, args.warmup) if full else sub_steps(args)
+
+    def step():
+        hqc.hqc_decrypt_batch_keyed(level, u_d, v_d, keys, k_d, m_out, stream=stream)
+
+    warm(step, warmup, stream)
+    total_ms, per, clocks = timed_steps(step, steps, stream, dist, clocks_idx=dist.local if full else None,
+                                        flush=flush)
+    max_ms = dist.max(total_ms)
+    correct = bool((m_out == m_ref).all().item())
+    wrong = int((m_out != m_ref).any(dim=1).sum().item())
+
+    # plain one-kernel-per-stage form on the same inputs
+    ws = torch.empty(hqc.hqc_staged_workspace_bytes(level, count), dtype=torch.uint8, device=device)
+    m_plain = torch.empty_like(m_ref)
+
+    def plain_step():
+        hqc.hqc_decrypt_batch_staged(level, u_d, v_d, keys=keys, key_idx=k_d, workspace=ws, m_out=m_plain,
+                                     stream=stream)
+
+    plain_steps = max(5, min(steps, 200))
+    warm(plain_step, 3, stream)
+    plain_ms, _, _ = timed_steps(plain_step, plain_steps, stream, dist, flush=flush)
+    plain_ms = dist.max(plain_ms)
+    plain_ok = bool((m_plain == m_ref).all().item())
+
+    total_count = dist.sum(float(count))
+    value = total_count * steps / (max_ms * 1e-3)
+    plain_value = total_count * plain_steps / (plain_ms * 1e-3)
+    smem_b, hbm_b, int_ops = per_decryption_work(P)
+    launch_s = (total_ms / steps) * 1e-3  # one launch of the fused kernel per step
+    kernel = decrypt_kernel_name(level, count)
+    roofline = ctx.roofline(smem_b * count, int_ops * count, hbm_b * count, launch_s, kernel,
+                            traffic=traffic_from_profile(level) if count == 65536 or count == 32768 else None)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": steps,
+        "warmup": warmup, "ms_per_step": max_ms / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": desc, "level": level, "count_per_gpu": count, "nkeys": nkeys,
+                   "inputs_bytes_per_gpu": int(in_bytes), "l2": l2,
+                   "launch": hqc.hqc_get_launch_shape(level, True),
+                   "parallelism": "replicas" if dist.world > 1 else "single GPU"},
+        "correct": correct and plain_ok, "wrong_messages": wrong,
+        "latency_ms": {"p50": pct(per, 50), "p99": pct(per, 99), "max": max(per),
+                       "what": "one batch of %d decryptions (launch to completion, device events)" % count},
+        "plain_per_stage": {"value": plain_value, "unit": UNIT, "ms_per_step": plain_ms / plain_steps,
+                            "launches_per_step": 3, "correct": plain_ok},
+        "batched_over_per_stage": value / plain_value,
+        "roofline": roofline,
+        "gpu_launches": steps,
+        "clocks": clocks,
+    }
+    if full:
+        line["e2e"] = e2e_single(ctx, level, count, P, keys, u_d, v_d, k_d, m_ref, stream)
+        line["correct"] = line["correct"] and line["e2e"].pop("correct")
+    if full and dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        rate, n, dt = oracle_rate(level, nkeys, args.cpu_seconds, cores)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": "%d ciphertexts of the same workload recipe (oracle-encrypted), %.1f s"
+                                          % (n, dt)}
+    keys.free()
+    return line
+
+
+def e2e_single(ctx, level, count, P, keys, u_d, v_d, k_d, m_ref, stream):
+    """End to end through hqc_decrypt_host_keyed: pinned host buffers in, m
+    out, copies inside the timed region."""
+    import torch
+    hqc, dist, args, device = ctx.hqc, ctx.dist, ctx.args, ctx.device
+    u_h = u_d.cpu().pin_memory()
+    v_h = v_d.cpu().pin_memory()
+    k_h = k_d.cpu().pin_memory()
+    m_h = torch.empty(m_ref.shape, dtype=torch.uint8).pin_memory()
+    u_e, v_e, k_e, m_e = torch.empty_like(u_d), torch.empty_like(v_d), torch.empty_like(k_d), torch.empty_like(m_ref)
+    ws_host = torch.empty(hqc.hqc_host_workspace_bytes(level, min(count, 16384)), dtype=torch.uint8, device=device)
+
+    def e2e_step():
+        hqc.hqc_decrypt_host_keyed(level, u_h, v_h, keys, k_h, m_h, workspace=ws_host, stream=stream)
+
+    def serial_step():
+        u_e.copy_(u_h, non_blocking=True)
+        v_e.copy_(v_h, non_blocking=True)
+        k_e.copy_(k_h, non_blocking=True)
+        hqc.hqc_decrypt_batch_keyed(level, u_e, v_e, keys, k_e, m_e, stream=stream)
+        m_h.copy_(m_e, non_blocking=True)
+
+    e2e_steps = max(5, min(args.steps, 100))
+    m_cpu = m_ref.cpu()
+    warm(serial_step, 3, stream)
+    serial_ms, _, _ = timed_steps(serial_step, e2e_steps, stream, dist)
+    serial_ms = dist.max(serial_ms)
+    serial_ok = bool((m_h == m_cpu).all().item())
+    m_h.zero_()
+    warm(e2e_step, 3, stream)
+    e2e_ms, _, _ = timed_steps(e2e_step, e2e_steps, stream, dist)
+    e2e_ms = dist.max(e2e_ms)
+    e2e_ok = bool((m_h == m_cpu).all().item()) and serial_ok
+
+    # the host link alone: the same bytes copied up without decrypting
+    def link_step():
+        u_e.copy_(u_h, non_blocking=True)
+        v_e.copy_(v_h, non_blocking=True)
+        k_e.copy_(k_h, non_blocking=True)
+
+    link_ms, _, _ = timed_steps(link_step, e2e_steps, stream, dist)
+    link_ms = dist.max(link_ms)
+    h2d = u_h.numel() * 8 + v_h.numel() * 8 + k_h.numel() * 4
+    total = dist.sum(float(count))
+    return {"value": total * e2e_steps / (e2e_ms * 1e-3), "unit": UNIT,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": m_h.numel(), "steps": e2e_steps,
+            "api": "hqc_decrypt_host_keyed: pinned host u, v, key_idx in, m out, chunked copies "
+                   "overlapped with the fused kernel",
+            "serial": {"value": total * e2e_steps / (serial_ms * 1e-3),
+                       "api": "copy in, hqc_decrypt_batch_keyed, copy out, one after another"},
+            "h2d_link_gbs": h2d * e2e_steps / (link_ms * 1e-3) / 1e9,
+            "link_bound": total * e2e_steps / (link_ms * 1e-3),
+            "link_what": "decryptions/s the host-to-device copy of the inputs alone allows",
+            "correct": e2e_ok}
+
+
+def bench_mixed(ctx, full):
     """Mixed-level batch: autotuned CUDA-graph plan vs the single mixed kernel,
     per-level fused launches and the plain per-stage form."""
     import torch
     import synth
-    import paper_2512_12904_gb300 as hqc
-
-    dist = Dist(args.gpus)
-    device = torch.device("cuda", dist.local)
-    torch.cuda.set_device(device)
-    hqc.load()
+    hqc, dist, args, device = ctx.hqc, ctx.dist, ctx.args, ctx.device
     _, count, nkeys_total, desc = WORKLOADS["mixed"]
     nk = nkeys_total // 3
+    steps, warmup = (args.steps, args.warmup) if full else sub_steps(args)
     per = {}
     for lvl, cnt in MIXED_SPLIT:
         per[lvl] = make_workload(hqc, lvl, cnt, nk, dist.rank, device)
@@ -416,25 +645,21 @@ def run_mixed(args):
     def step():
         plan.launch(stream=stream)
 
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            step()
-    torch.cuda.synchronize()
-    total_ms, per_ms, clocks = timed_steps(step, args.steps, stream, dist, clocks_idx=dist.local)
+    warm(step, warmup, stream)
+    total_ms, per_ms, clocks = timed_steps(step, steps, stream, dist, clocks_idx=dist.local if full else None)
     max_ms = dist.max(total_ms)
     correct = bool((m_out == m_expect).all().item())
 
-    def arm(fn, steps):
-        with torch.cuda.stream(stream):
-            for _ in range(3):
-                fn()
-        ms, _, _ = timed_steps(fn, steps, stream, dist)
-        return dist.max(ms) / steps
+    def arm(fn, n):
+        warm(fn, 3, stream)
+        ms, _, _ = timed_steps(fn, n, stream, dist)
+        return dist.max(ms) / n
 
+    arm_steps = max(5, min(steps, 100))
     ws_mixed = torch.zeros(hqc.hqc_mixed_workspace_bytes(), dtype=torch.uint8, device=device)
     m_single = torch.zeros_like(m_out)
     single_ms = arm(lambda: hqc.hqc_decrypt_mixed(items_d, arena, keys3, m_single, workspace=ws_mixed, stream=stream),
-                    max(5, min(args.steps, 200)))
+                    arm_steps)
     single_ok = bool((m_single == m_expect).all().item())
     outs = {lvl: torch.empty_like(per[lvl][5]) for lvl, _ in MIXED_SPLIT}
 
@@ -443,7 +668,8 @@ def run_mixed(args):
             Pl, keys, u_d, v_d, k_d, m_ref, _, _ = per[lvl]
             hqc.hqc_decrypt_batch_keyed(lvl, u_d, v_d, keys, k_d, outs[lvl], stream=stream)
 
-    levels_ms = arm(fused_levels, max(5, min(args.steps, 200)))
+    levels_ms = arm(fused_levels, arm_steps)
+    levels_ok = all(bool((outs[l] == per[l][5]).all().item()) for l, _ in MIXED_SPLIT)
     wss = {lvl: torch.empty(hqc.hqc_staged_workspace_bytes(lvl, cnt), dtype=torch.uint8, device=device)
            for lvl, cnt in MIXED_SPLIT}
     outs2 = {lvl: torch.empty_like(per[lvl][5]) for lvl, _ in MIXED_SPLIT}
@@ -454,15 +680,71 @@ def run_mixed(args):
             hqc.hqc_decrypt_batch_staged(lvl, u_d, v_d, keys=keys, key_idx=k_d, workspace=wss[lvl], m_out=outs2[lvl],
                                          stream=stream)
 
-    staged_ms = arm(staged_levels, max(5, min(args.steps, 100)))
+    staged_ms = arm(staged_levels, arm_steps)
     staged_ok = all(bool((outs2[l] == per[l][5]).all().item()) for l, _ in MIXED_SPLIT)
 
-    # end to end: the arena and item list from pinned host memory, m back
+    total = dist.sum(float(count))
+    value = total * steps / (max_ms * 1e-3)
+    plain_value = total / (staged_ms * 1e-3)
+    smem_b = sum(cnt * per_decryption_work(P[l])[0] for l, cnt in MIXED_SPLIT)
+    int_ops = sum(cnt * per_decryption_work(P[l])[2] for l, cnt in MIXED_SPLIT)
+    hbm_b = sum(cnt * per_decryption_work(P[l])[1] for l, cnt in MIXED_SPLIT)
+    step_s = (total_ms / steps) * 1e-3
+    roofline = ctx.roofline(smem_b, int_ops, hbm_b, step_s, "mixed plan (%s)" % info["form"])
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": steps,
+        "warmup": warmup, "ms_per_step": max_ms / steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": desc, "count_per_gpu": count, "split": dict((str(l), c) for l, c in MIXED_SPLIT),
+                   "nkeys": nkeys_total, "plan": info, "autotune_s": tune_s,
+                   "l2": "inputs (%d MB) larger than L2 (129 MB); no flush" % (words * 8 // 2 ** 20)},
+        "correct": correct and single_ok and staged_ok and levels_ok,
+        "wrong_messages": int((m_out != m_expect).sum().item()),
+        "latency_ms": {"p50": pct(per_ms, 50), "p99": pct(per_ms, 99), "max": max(per_ms),
+                       "what": "one mixed batch of %d decryptions (graph launch to completion)" % count},
+        "single_mixed_kernel": {"value": total / (single_ms * 1e-3), "ms_per_step": single_ms, "correct": single_ok},
+        "per_level_fused": {"value": total / (levels_ms * 1e-3), "ms_per_step": levels_ms, "launches_per_step": 3,
+                            "correct": levels_ok},
+        "plain_per_stage": {"value": plain_value, "unit": UNIT, "ms_per_step": staged_ms,
+                            "launches_per_step": 9, "correct": staged_ok},
+        "batched_over_per_stage": value / plain_value,
+        "roofline": roofline,
+        "gpu_launches": steps * (1 if info["form"] == "mixed-single-kernel" else 3),
+        "clocks": clocks,
+    }
+    if full:
+        line["e2e"] = e2e_mixed(ctx, count, arena, items_d, keys3, m_out, m_expect, stream)
+        line["correct"] = line["correct"] and line["e2e"].pop("correct")
+    if full and dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        rates = {}
+        for lvl, cnt in MIXED_SPLIT:
+            rates[lvl] = oracle_rate(lvl, 16, args.cpu_seconds / 3, cores)
+        t_total = sum(cnt / rates[l][0] for l, cnt in MIXED_SPLIT)
+        line["cpu_baseline"] = {"value": count / t_total, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": "per level %s ciphertexts timed separately, combined in the 40/35/25 mix"
+                                          % {l: rates[l][1] for l, _ in MIXED_SPLIT}}
+    plan.destroy()
+    for l in (1, 3, 5):
+        per[l][1].free()
+    return line
+
+
+def e2e_mixed(ctx, count, arena, items_d, keys3, m_out, m_expect, stream):
+    """The arena and item list from pinned host memory, m back."""
+    import torch
+    hqc, dist, args, device = ctx.hqc, ctx.dist, ctx.args, ctx.device
+    m_bytes = m_out.numel()
     arena_h = arena.cpu().pin_memory()
     items_h = items_d.cpu().pin_memory()
     m_h = torch.empty(m_bytes, dtype=torch.uint8).pin_memory()
     arena_e, items_e, m_e = torch.empty_like(arena), torch.empty_like(items_d), torch.zeros_like(m_out)
     ws_e = torch.zeros(hqc.hqc_mixed_workspace_bytes(), dtype=torch.uint8, device=device)
+
+    def arm(fn, n):
+        warm(fn, 3, stream)
+        ms, _, _ = timed_steps(fn, n, stream, dist)
+        return dist.max(ms) / n
 
     def serial_step():
         arena_e.copy_(arena_h, non_blocking=True)
@@ -473,7 +755,7 @@ def run_mixed(args):
     e2e_steps = max(5, min(args.steps, 50))
     serial_ms = arm(serial_step, e2e_steps)
     m_cpu = m_expect.cpu()
-    e2e_ok = bool((m_h == m_cpu).all().item())
+    ok = bool((m_h == m_cpu).all().item())
     # pipelined: chunks of records and arena ranges uploaded while the
     # previous chunk decrypts; a few chunk counts tried, the best kept
     tried = {}
@@ -486,79 +768,23 @@ def run_mixed(args):
     best = min(tried, key=lambda c: tried[c][0])
     m_h.zero_()
     e2e_ms = arm(tried[best][1], e2e_steps)
-    e2e_ok = e2e_ok and bool((m_h == m_cpu).all().item())
-
+    ok = ok and bool((m_h == m_cpu).all().item())
     total = dist.sum(float(count))
-    value = total * args.steps / (max_ms * 1e-3)
-    smem_b = sum(cnt * per_decryption_work(P[l])[0] for l, cnt in MIXED_SPLIT)
-    int_ops = sum(cnt * per_decryption_work(P[l])[2] for l, cnt in MIXED_SPLIT)
-    hbm_b = sum(cnt * per_decryption_work(P[l])[1] for l, cnt in MIXED_SPLIT)
-    smem_peak, int_peak = load_peaks()
-    step_s = (total_ms / args.steps) * 1e-3
-    peaks = measured_peaks_file()
-    blocks = {
-        "smem": {"bound": "smem", "achieved": smem_b / step_s / 1e9, "peak": smem_peak / 1e9, "unit": "GB/s"},
-        "alu": {"bound": "alu", "achieved": int_ops / step_s / 1e9, "peak": int_peak / 1e9, "unit": "Gop/s"},
-        "hbm": {"bound": "hbm", "achieved": hbm_b / step_s / 1e9, "peak": peaks.get("hbm_gbs"), "unit": "GB/s"},
-    }
-    for b in blocks.values():
-        b["frac"] = b["achieved"] / b["peak"] if b["peak"] else None
-    primary = max(("smem", "alu"), key=lambda k: blocks[k]["frac"] or 0)
-    roofline = dict(blocks[primary], traffic=None, kernel="mixed plan (%s)" % info["form"],
-                    others={k: v for k, v in blocks.items() if k != primary})
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": desc, "count_per_gpu": count, "split": dict((str(l), c) for l, c in MIXED_SPLIT),
-                   "nkeys": nkeys_total, "plan": info, "autotune_s": tune_s,
-                   "l2": "inputs (%d MB) larger than L2 (129 MB); no flush" % (words * 8 // 2 ** 20)},
-        "correct": correct and single_ok and staged_ok and e2e_ok,
-        "latency_ms": {"p50": pct(per_ms, 50), "p99": pct(per_ms, 99), "max": max(per_ms),
-                       "what": "one mixed batch of %d decryptions (graph launch to completion)" % count},
-        "single_mixed_kernel": {"value": total / (single_ms * 1e-3), "ms_per_step": single_ms, "correct": single_ok},
-        "per_level_fused": {"value": total / (levels_ms * 1e-3), "ms_per_step": levels_ms, "launches_per_step": 3},
-        "plain_per_stage": {"value": total / (staged_ms * 1e-3), "unit": UNIT, "ms_per_step": staged_ms,
-                            "launches_per_step": 9, "correct": staged_ok},
-        "roofline": roofline,
-        "e2e": {"value": total / (e2e_ms * 1e-3), "unit": UNIT,
-                "h2d_bytes_per_step": int(arena_h.numel() * 8 + items_h.numel()), "d2h_bytes_per_step": m_bytes,
-                "api": "hqc_decrypt_mixed_host: pinned host arena and item list in, m out, chunked uploads "
-                       "overlapped with per-level kernels",
-                "chunk": best, "chunks_tried_ms": {str(c): v[0] for c, v in tried.items()},
-                "serial": {"value": total / (serial_ms * 1e-3),
-                           "api": "copy in, hqc_decrypt_mixed (one mixed kernel), copy out"}},
-        "gpu_launches": args.steps * (1 if info["form"] == "mixed-single-kernel" else 3),
-        "clocks": clocks,
-    }
-    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
-        cores = os.cpu_count() or 1
-        rates = {}
-        for lvl, cnt in MIXED_SPLIT:
-            rates[lvl] = oracle_rate(lvl, 16, args.cpu_seconds / 3, cores)
-        t_total = sum(cnt / rates[l][0] for l, cnt in MIXED_SPLIT)
-        line["cpu_baseline"] = {"value": count / t_total, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": "per level %s ciphertexts timed separately, combined in the 40/35/25 mix"
-                                          % {l: rates[l][1] for l, _ in MIXED_SPLIT}}
-    plan.destroy()
-    for l in (1, 3, 5):
-        per[l][1].free()
-    if dist.rank == 0:
-        print(json.dumps(line), flush=True)
-    dist.close()
-    return 0
+    return {"value": total / (e2e_ms * 1e-3), "unit": UNIT,
+            "h2d_bytes_per_step": int(arena_h.numel() * 8 + items_h.numel()), "d2h_bytes_per_step": m_bytes,
+            "api": "hqc_decrypt_mixed_host: pinned host arena and item list in, m out, chunked uploads "
+                   "overlapped with per-level kernels",
+            "chunk": best, "chunks_tried_ms": {str(c): v[0] for c, v in tried.items()},
+            "serial": {"value": total / (serial_ms * 1e-3),
+                       "api": "copy in, hqc_decrypt_mixed (one mixed kernel), copy out"},
+            "correct": ok}
 
 
-def run_serving(args):
+def bench_serving(ctx, full):
     """Continuous-batching service loop at several offered loads."""
     import torch
     import synth
-    import paper_2512_12904_gb300 as hqc
-
-    dist = Dist(args.gpus)
-    device = torch.device("cuda", dist.local)
-    torch.cuda.set_device(device)
-    hqc.load()
+    hqc, dist, args, device = ctx.hqc, ctx.dist, ctx.args, ctx.device
     period = 65536
     levels = synth.level_mix(period, ((1, 0.40), (3, 0.35), (5, 0.25)), tag=201)
     per, rows_by_level = {}, {}
@@ -589,12 +815,13 @@ def run_serving(args):
     duration = max(0.2, min(2.0, args.serve_seconds))
     for load in SERVE_LOADS:
         arr = synth.burst_trace(load, duration, tag=301 + int(np.log10(load)))
-        # NVML polling every 100 ms stalls the host loop for tens of ms (p99
-        # 0.3 -> 53 ms); every 500 ms it does not show in the latencies
-        clk = Clocks(dist.local, interval_ms=500)
+        # clocks are read just before and just after each point: an NVML
+        # query while the loop runs holds the driver long enough to show in
+        # the tail latencies
+        clk_before = clocks_now(dist.local)
         st, lat, m_out, stats = hqc.hqc_serve_run(keys3, levels, key, woff, words, moff, arr, streams=4,
                                                   max_batch=16384, budget_bytes=256 << 20, max_queue=1 << 22)
-        clocks = clk.stop()
+        clk_after = clocks_now(dist.local)
         ok = st == 0
         good = True
         idx = np.nonzero(ok)[0]
@@ -611,7 +838,7 @@ def run_serving(args):
             "p99_us": float(np.percentile(l_us, 99)) if l_us.size else None,
             "p999_us": float(np.percentile(l_us, 99.9)) if l_us.size else None,
             "batches": int(stats["batches"]), "mean_batch": stats["mean_batch"], "correct": good,
-            "clocks": clocks})
+            "clocks": {"before": clk_before, "after": clk_after}})
     top = points[-1]
     line = {
         "metric": METRIC, "value": top["sustained_dec_per_s"], "unit": UNIT, "n_gpus": dist.world,
@@ -626,174 +853,24 @@ def run_serving(args):
                 "h2d_bytes_per_step": int(woff[-1] * 8), "d2h_bytes_per_step": int(moff[-1]),
                 "api": "hqc_serve_run: ciphertexts copied from a pinned host ring per batch, m copied back"},
         "gpu_launches": int(sum(p["batches"] for p in points)),
-        "clocks": top["clocks"],
+        "clocks": top["clocks"]["after"],
     }
     for l in (1, 3, 5):
         per[l][1].free()
-    if dist.rank == 0:
-        print(json.dumps(line), flush=True)
-    dist.close()
-    return 0
+    return line
 
 
-def run_ours(args):
-    import torch
-    import paper_2512_12904_gb300 as hqc
-
-    if args.workload == "mixed":
-        return run_mixed(args)
-    if args.workload == "serving":
-        return run_serving(args)
-    if args.workload in KEM_WORKLOADS:
-        return run_kem(args)
-
-    dist = Dist(args.gpus)
-    device = torch.device("cuda", dist.local)
-    torch.cuda.set_device(device)
-    hqc.load()
-    level, count, nkeys, desc = WORKLOADS[args.workload]
-    smem_peak, int_peak = load_peaks()
-    P, keys, u_d, v_d, k_d, m_ref, y_host, kidx = make_workload(hqc, level, count, nkeys, dist.rank, device)
-    m_out = torch.empty_like(m_ref)
-    stream = torch.cuda.Stream(device=device)
-    shape = hqc.hqc_get_launch_shape(level, True)
-
-    def step():
-        hqc.hqc_decrypt_batch_keyed(level, u_d, v_d, keys, k_d, m_out, stream=stream)
-
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            step()
-    torch.cuda.synchronize()
-    total_ms, per, clocks = timed_steps(step, args.steps, stream, dist, clocks_idx=dist.local)
-    max_ms = dist.max(total_ms)
-    correct = bool((m_out == m_ref).all().item())
-    wrong = int((m_out != m_ref).any(dim=1).sum().item())
-
-    # plain one-kernel-per-stage form on the same inputs
-    ws = torch.empty(hqc.hqc_staged_workspace_bytes(level, count), dtype=torch.uint8, device=device)
-    m_plain = torch.empty_like(m_ref)
-
-    def plain_step():
-        hqc.hqc_decrypt_batch_staged(level, u_d, v_d, keys=keys, key_idx=k_d, workspace=ws, m_out=m_plain,
-                                     stream=stream)
-
-    plain_steps = max(5, min(args.steps, 200))
-    with torch.cuda.stream(stream):
-        for _ in range(3):
-            plain_step()
-    plain_ms, plain_per, _ = timed_steps(plain_step, plain_steps, stream, dist)
-    plain_ms = dist.max(plain_ms)
-    plain_ok = bool((m_plain == m_ref).all().item())
-
-    # end to end through the public API with pinned host buffers
-    u_h = u_d.cpu().pin_memory()
-    v_h = v_d.cpu().pin_memory()
-    k_h = k_d.cpu().pin_memory()
-    m_h = torch.empty(m_ref.shape, dtype=torch.uint8).pin_memory()
-    u_e, v_e, k_e, m_e = torch.empty_like(u_d), torch.empty_like(v_d), torch.empty_like(k_d), torch.empty_like(m_ref)
-
-    ws_host = torch.empty(hqc.hqc_host_workspace_bytes(level, min(count, 16384)), dtype=torch.uint8, device=device)
-
-    def e2e_step():
-        hqc.hqc_decrypt_host_keyed(level, u_h, v_h, keys, k_h, m_h, workspace=ws_host, stream=stream)
-
-    def serial_step():
-        u_e.copy_(u_h, non_blocking=True)
-        v_e.copy_(v_h, non_blocking=True)
-        k_e.copy_(k_h, non_blocking=True)
-        hqc.hqc_decrypt_batch_keyed(level, u_e, v_e, keys, k_e, m_e, stream=stream)
-        m_h.copy_(m_e, non_blocking=True)
-
-    e2e_steps = max(5, min(args.steps, 100))
-    m_cpu = m_ref.cpu()
-    with torch.cuda.stream(stream):
-        for _ in range(3):
-            serial_step()
-    serial_ms, _, _ = timed_steps(serial_step, e2e_steps, stream, dist)
-    serial_ms = dist.max(serial_ms)
-    serial_ok = bool((m_h == m_cpu).all().item())
-    m_h.zero_()
-    with torch.cuda.stream(stream):
-        for _ in range(3):
-            e2e_step()
-    e2e_ms, _, _ = timed_steps(e2e_step, e2e_steps, stream, dist)
-    e2e_ms = dist.max(e2e_ms)
-    e2e_ok = bool((m_h == m_cpu).all().item()) and serial_ok
-    # the host link alone: the same bytes copied up without decrypting
-    def link_step():
-        u_e.copy_(u_h, non_blocking=True)
-        v_e.copy_(v_h, non_blocking=True)
-        k_e.copy_(k_h, non_blocking=True)
-
-    link_ms, _, _ = timed_steps(link_step, e2e_steps, stream, dist)
-    link_ms = dist.max(link_ms)
-    h2d = u_h.numel() * 8 + v_h.numel() * 8 + k_h.numel() * 4
-    d2h = m_h.numel()
-
-    total_dec = dist.sum(float(count)) * args.steps
-    value = total_dec / (max_ms * 1e-3)
-    smem_b, hbm_b, int_ops = per_decryption_work(P)
-    launch_s = (total_ms / args.steps) * 1e-3  # one launch of the fused kernel per step
-    peaks = measured_peaks_file()
-    hbm_peak = peaks.get("hbm_gbs")
-    smem_ach = smem_b * count / launch_s / 1e9
-    int_ach = int_ops * count / launch_s / 1e9
-    hbm_ach = hbm_b * count / launch_s / 1e9
-    blocks = {
-        "smem": {"bound": "smem", "achieved": smem_ach, "peak": smem_peak / 1e9, "unit": "GB/s",
-                 "frac": smem_ach / (smem_peak / 1e9) if smem_peak else None, "traffic": None,
-                 "peak_source": "measured in this run: conflict-free 32-bit shared-memory loads, all SMs"},
-        "alu": {"bound": "alu", "achieved": int_ach, "peak": int_peak / 1e9, "unit": "Gop/s",
-                "frac": int_ach / (int_peak / 1e9) if int_peak else None,
-                "peak_source": "measured in this run: 32-bit funnel-shift + XOR issue rate, all SMs"},
-        "hbm": {"bound": "hbm", "achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s",
-                "frac": hbm_ach / hbm_peak if hbm_peak else None,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if hbm_peak else "absent"},
-    }
-    primary = max(("smem", "alu"), key=lambda k: blocks[k]["frac"] or 0)
-    roofline = dict(blocks[primary])
-    roofline["kernel"] = ("k_decrypt_team<%d,keyed>" if level == 5 else "k_decrypt_fused<%d,keyed>") % level
-    roofline["traffic"] = traffic_from_profile(level)
-    roofline["others"] = {k: v for k, v in blocks.items() if k != primary}
-
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": desc, "level": level, "count_per_gpu": count, "nkeys": nkeys,
-                   "inputs_bytes_per_gpu": int(u_d.numel() * 8 + v_d.numel() * 8),
-                   "l2": "inputs (%d MB) larger than L2 (129 MB); no flush" % ((u_d.numel() + v_d.numel()) * 8 // 2 ** 20)
-                   if (u_d.numel() + v_d.numel()) * 8 > L2_BYTES else "inputs smaller than L2",
-                   "launch": shape, "parallelism": "replicas" if dist.world > 1 else "single GPU"},
-        "correct": correct and plain_ok and e2e_ok, "wrong_messages": wrong,
-        "latency_ms": {"p50": pct(per, 50), "p99": pct(per, 99), "max": max(per),
-                       "what": "one batch of %d decryptions (launch to completion, device events)" % count},
-        "plain_per_stage": {"value": dist.sum(float(count)) * plain_steps / (plain_ms * 1e-3), "unit": UNIT,
-                            "ms_per_step": plain_ms / plain_steps, "launches_per_step": 3, "correct": plain_ok},
-        "roofline": roofline,
-        "e2e": {"value": dist.sum(float(count)) * e2e_steps / (e2e_ms * 1e-3), "unit": UNIT,
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps,
-                "api": "hqc_decrypt_host_keyed: pinned host u, v, key_idx in, m out, chunked copies "
-                       "overlapped with the fused kernel",
-                "serial": {"value": dist.sum(float(count)) * e2e_steps / (serial_ms * 1e-3),
-                           "api": "copy in, hqc_decrypt_batch_keyed, copy out, one after another"},
-                "h2d_link_gbs": h2d * e2e_steps / (link_ms * 1e-3) / 1e9,
-                "link_bound": dist.sum(float(count)) * e2e_steps / (link_ms * 1e-3),
-                "link_what": "decryptions/s the host-to-device copy of the inputs alone allows"},
-        "gpu_launches": args.steps,
-        "clocks": clocks,
-    }
-    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
-        cores = os.cpu_count() or 1
-        rate, n, dt = oracle_rate(level, nkeys, args.cpu_seconds, cores)
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": "%d ciphertexts of the same workload recipe (oracle-encrypted), %.1f s" % (n, dt)}
-    keys.free()
-    if dist.rank == 0:
-        print(json.dumps(line), flush=True)
-    dist.close()
-    return 0
+def clocks_now(gpu_index):
+    """One nvidia-smi sample of the SM clock and throttle reasons."""
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + Clocks.QUERY,
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=10).stdout
+        r = out.strip().split(",")
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        return {"sm_mhz": float(r[1]), "sm_max_mhz": float(r[2]),
+                "reasons": sorted(n for n, v in zip(names, r[5:9]) if v.strip().lower() == "active")}
+    except (OSError, ValueError, IndexError, subprocess.SubprocessError):
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
 
 
 def keccak_perms(n_bytes):
@@ -818,19 +895,15 @@ def per_decaps_work(P):
     return {"decrypt": dec_ops, "derive": derive_ops, "encrypt_compare": enc_ops, "K": K_ops}
 
 
-def run_kem(args):
+def bench_kem(ctx, wl_name, full):
     """Batched KEM decapsulation (and encapsulation) on seeded key pairs."""
     import torch
     import synth
-    import paper_2512_12904_gb300 as hqc
-    dist = Dist(args.gpus)
-    device = torch.device("cuda", dist.local)
-    torch.cuda.set_device(device)
-    hqc.load()
-    level, count, nkeys, desc = WORKLOADS[args.workload]
+    hqc, dist, args, device = ctx.hqc, ctx.dist, ctx.args, ctx.device
+    level, count, nkeys, desc = WORKLOADS[wl_name]
     P = hqc.hqc_get_params(level)
-    smem_peak, int_peak = load_peaks()
     tag = 7000 + 100 * level + 10 * dist.rank
+    steps, warmup = (args.steps, args.warmup) if full else sub_steps(args)
 
     def rows(cnt, width, t):
         nw = (cnt * width + 7) // 8 + 1
@@ -865,21 +938,15 @@ def run_kem(args):
 
     with torch.cuda.stream(stream):
         encaps()
-        for _ in range(args.warmup):
-            decaps()
-    torch.cuda.synchronize()
-    total_ms, per, clocks = timed_steps(decaps, args.steps, stream, dist, clocks_idx=dist.local)
+    warm(decaps, warmup, stream)
+    total_ms, per, clocks = timed_steps(decaps, steps, stream, dist, clocks_idx=dist.local if full else None)
     max_ms = dist.max(total_ms)
     correct = bool(ok.all().item()) and bool((K_dec == K_enc).all().item())
-    sub = max(5, min(args.steps, 50))
-    with torch.cuda.stream(stream):
-        for _ in range(3):
-            encaps()
+    sub = max(5, min(steps, 50))
+    warm(encaps, 3, stream)
     enc_ms, _, _ = timed_steps(encaps, sub, stream, dist)
     enc_ms = dist.max(enc_ms)
-    with torch.cuda.stream(stream):
-        for _ in range(3):
-            decrypt_only()
+    warm(decrypt_only, 3, stream)
     dec_ms, _, _ = timed_steps(decrypt_only, sub, stream, dist)
     dec_ms = dist.max(dec_ms)
     correct = correct and bool((m_dec == m).all().item())
@@ -892,8 +959,63 @@ def run_kem(args):
     torch.cuda.synchronize()
     rejected_ok = not bool(ok_bad.any().item())
 
-    # end to end: pinned host ciphertexts and salts in, K out, chunked so the
-    # uploads overlap the kernels
+    work = per_decaps_work(P)
+    ops = sum(work.values())
+    step_s = (total_ms / steps) * 1e-3
+    alu_peak = ctx.peaks["alu_ops_per_s"] / 1e9
+    issue_peak = ctx.peaks["issue_ops_per_s"] / 1e9
+    int_ach = ops * count / step_s / 1e9
+    hbm_b = 3 * (P.W_u_pitch + P.W_v) * 8 + P.k * 2 + 16 * 2 + 32 + 8 + 4 * (2 * P.wr + P.we) * 2
+    roofline = {"bound": "alu", "achieved": int_ach, "peak": alu_peak, "unit": "Gop/s",
+                "frac": int_ach / alu_peak if alu_peak else None, "traffic": None,
+                "kernel": "whole decapsulation step (4 kernels)",
+                "ops_per_item": work,
+                "peak_source": "measured in this run: 32-bit funnel-shift + XOR issue rate, all SMs",
+                "issue": {"peak": issue_peak, "frac": int_ach / issue_peak if issue_peak else None},
+                "others": {"hbm": {"bound": "hbm", "achieved": hbm_b * count / step_s / 1e9,
+                                   "peak": ctx.hbm_peak, "unit": "GB/s"}}}
+    total = dist.sum(float(count))
+    value = total * steps / (max_ms * 1e-3)
+    line = {
+        "metric": "HQC KEM decapsulations/sec per GB300", "value": value, "unit": KEM_UNIT, "n_gpus": dist.world,
+        "steps": steps, "warmup": warmup, "ms_per_step": max_ms / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": desc, "level": level, "count_per_gpu": count, "nkeys": nkeys,
+                   "l2": "inputs (%d MB) larger than L2 (129 MB); no flush" % ((u.numel() + v.numel()) * 8 // 2 ** 20),
+                   "parallelism": "replicas" if dist.world > 1 else "single GPU"},
+        "correct": correct, "implicit_rejection_ok": rejected_ok,
+        "latency_ms": {"p50": pct(per, 50), "p99": pct(per, 99), "max": max(per)},
+        "encaps": {"value": total * sub / (enc_ms * 1e-3), "unit": "encapsulations/s", "ms_per_step": enc_ms / sub},
+        "decrypt_only": {"value": total * sub / (dec_ms * 1e-3), "unit": UNIT, "ms_per_step": dec_ms / sub},
+        "roofline": roofline,
+        "gpu_launches": 4 * steps,
+        "clocks": clocks,
+    }
+    if full:
+        line["e2e"] = e2e_kem(ctx, level, count, keys, h, s, sigma, kidx, u, v, salt, K_enc, stream)
+        line["correct"] = line["correct"] and line["e2e"].pop("correct")
+    if full and dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        import oracle
+        cores = os.cpu_count() or 1
+        n = max(4 * cores, 32)
+        hh, ss, yy = (t.cpu().numpy().view(np.uint64 if t.dtype == torch.int64 else np.uint32) for t in (h, s, y))
+        t0 = time.perf_counter()
+        Ko, oko = oracle.kem_decaps(level, hh, ss, yy, sigma.cpu().numpy(), kidx[:n].cpu().numpy(),
+                                    u[:n].cpu().numpy().view(np.uint64), v[:n].cpu().numpy().view(np.uint64),
+                                    salt[:n].cpu().numpy(), nthreads=cores)
+        dt = time.perf_counter() - t0
+        line["correct"] = line["correct"] and bool(oko.all()) and bool((Ko == K_enc[:n].cpu().numpy()).all())
+        line["cpu_baseline"] = {"value": n / dt, "unit": KEM_UNIT, "cores": cores, "kind": "oracle",
+                                "sample": "%d decapsulations of the same workload, %.1f s" % (n, dt)}
+    keys.free()
+    return line
+
+
+def e2e_kem(ctx, level, count, keys, h, s, sigma, kidx, u, v, salt, K_enc, stream):
+    """Pinned host ciphertexts and salts in, K out, chunked so the uploads
+    overlap the kernels."""
+    import torch
+    hqc, dist, args, device = ctx.hqc, ctx.dist, ctx.args, ctx.device
     u_h, v_h, s_h, k_h = (t.cpu().pin_memory() for t in (u, v, salt, kidx))
     K_h = torch.empty((count, 32), dtype=torch.uint8).pin_memory()
     ok_h = torch.empty((count,), dtype=torch.int32).pin_memory()
@@ -908,70 +1030,84 @@ def run_kem(args):
     tried = {}
     for c in (count, (count + 1) // 2, (count + 3) // 4):
         chunk_sel["chunk"] = c
-        with torch.cuda.stream(stream):
-            e2e_step()
+        warm(e2e_step, 1, stream)
         tried[c], _, _ = timed_steps(e2e_step, 3, stream, dist)
     chunk_sel["chunk"] = min(tried, key=tried.get)
-    with torch.cuda.stream(stream):
-        for _ in range(3):
-            e2e_step()
+    sub = max(5, min(args.steps, 50))
+    warm(e2e_step, 3, stream)
     e2e_ms, _, _ = timed_steps(e2e_step, sub, stream, dist)
     e2e_ms = dist.max(e2e_ms)
-    correct = correct and bool((K_h == K_enc.cpu()).all().item()) and bool(ok_h.all().item())
+    ok = bool((K_h == K_enc.cpu()).all().item()) and bool(ok_h.all().item())
     h2d = sum(t.numel() * t.element_size() for t in (u_h, v_h, s_h, k_h))
+    return {"value": dist.sum(float(count)) * sub / (e2e_ms * 1e-3), "unit": KEM_UNIT,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": K_h.numel() + 4 * ok_h.numel(), "steps": sub,
+            "api": "hqc_kem_decaps_host: pinned host u, v, salt, key_idx in, K and ok out, chunked "
+                   "copies overlapped with the kernels",
+            "chunk": chunk_sel["chunk"], "chunks_tried_ms": {str(k): v / 3 for k, v in tried.items()},
+            "correct": ok}
 
-    work = per_decaps_work(P)
-    ops = sum(work.values())
-    step_s = (total_ms / args.steps) * 1e-3
-    int_ach = ops * count / step_s / 1e9
-    hbm_b = 3 * (P.W_u_pitch + P.W_v) * 8 + P.k * 2 + 16 * 2 + 32 + 8 + 4 * (2 * P.wr + P.we) * 2
-    roofline = {"bound": "alu", "achieved": int_ach, "peak": int_peak / 1e9, "unit": "Gop/s",
-                "frac": int_ach / (int_peak / 1e9) if int_peak else None, "traffic": None,
-                "kernel": "whole decapsulation step (4 kernels)",
-                "ops_per_item": work,
-                "peak_source": "measured in this run: 32-bit funnel-shift + XOR issue rate, all SMs",
-                "others": {"hbm": {"bound": "hbm", "achieved": hbm_b * count / step_s / 1e9,
-                                   "peak": measured_peaks_file().get("hbm_gbs"), "unit": "GB/s"}}}
-    value = dist.sum(float(count)) * args.steps / (max_ms * 1e-3)
-    line = {
-        "metric": "HQC KEM decapsulations/sec per GB300", "value": value, "unit": KEM_UNIT, "n_gpus": dist.world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": desc, "level": level, "count_per_gpu": count, "nkeys": nkeys,
-                   "l2": "inputs (%d MB) larger than L2 (129 MB); no flush" % ((u.numel() + v.numel()) * 8 // 2 ** 20),
-                   "parallelism": "replicas" if dist.world > 1 else "single GPU"},
-        "correct": correct, "implicit_rejection_ok": rejected_ok,
-        "latency_ms": {"p50": pct(per, 50), "p99": pct(per, 99), "max": max(per)},
-        "encaps": {"value": dist.sum(float(count)) * sub / (enc_ms * 1e-3), "unit": "encapsulations/s",
-                   "ms_per_step": enc_ms / sub},
-        "decrypt_only": {"value": dist.sum(float(count)) * sub / (dec_ms * 1e-3), "unit": UNIT,
-                         "ms_per_step": dec_ms / sub},
-        "roofline": roofline,
-        "e2e": {"value": dist.sum(float(count)) * sub / (e2e_ms * 1e-3), "unit": KEM_UNIT,
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": K_h.numel() + 4 * ok_h.numel(), "steps": sub,
-                "api": "hqc_kem_decaps_host: pinned host u, v, salt, key_idx in, K and ok out, chunked "
-                       "copies overlapped with the kernels",
-                "chunk": chunk_sel["chunk"], "chunks_tried_ms": {str(k): v / 3 for k, v in tried.items()}},
-        "gpu_launches": 4 * args.steps,
-        "clocks": clocks,
-    }
-    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
-        import oracle
-        cores = os.cpu_count() or 1
-        n = max(4 * cores, 32)
-        hh, ss, yy = (t.cpu().numpy().view(np.uint64 if t.dtype == torch.int64 else np.uint32) for t in (h, s, y))
+
+# The sub-configurations the default run adds beside its headline: every
+# configuration of the benchmark recipe, each with its own correctness
+# check, its per-stage comparison where one exists, and its roofline.
+SUB_CONFIGS = (
+    ("C1_hqc1_plain", "single", "hqc1-plain"),
+    ("C3_hqc3", "single", "hqc3"),
+    ("C3_hqc5", "single", "hqc5"),
+    ("C4_mixed", "mixed", "mixed"),
+    ("C5_serving", "serving", "serving"),
+    ("KEM_hqc1_decaps", "kem", "kem1-decaps"),
+)
+
+
+def compact(line):
+    """A sub-configuration's result without the keys of the headline
+    contract that only the top-level line carries."""
+    drop = ("metric", "n_gpus", "higher_is_better", "scaling", "vs_baseline", "dtype", "data")
+    return {k: v for k, v in line.items() if k not in drop}
+
+
+def run_sub_configs(ctx):
+    import torch
+    out = {}
+    for name, kind, wl in SUB_CONFIGS:
         t0 = time.perf_counter()
-        Ko, oko = oracle.kem_decaps(level, hh, ss, yy, sigma.cpu().numpy(), kidx[:n].cpu().numpy(),
-                                    u[:n].cpu().numpy().view(np.uint64), v[:n].cpu().numpy().view(np.uint64),
-                                    salt[:n].cpu().numpy(), nthreads=cores)
-        dt = time.perf_counter() - t0
-        line["correct"] = line["correct"] and bool(oko.all()) and bool((Ko == K_enc[:n].cpu().numpy()).all())
-        line["cpu_baseline"] = {"value": n / dt, "unit": KEM_UNIT, "cores": cores, "kind": "oracle",
-                                "sample": "%d decapsulations of the same workload, %.1f s" % (n, dt)}
-    keys.free()
-    if dist.rank == 0:
+        try:
+            if kind == "single":
+                line = bench_single(ctx, wl, full=False)
+            elif kind == "mixed":
+                line = bench_mixed(ctx, full=False)
+            elif kind == "serving":
+                line = bench_serving(ctx, full=False)
+            else:
+                line = bench_kem(ctx, wl, full=False)
+            res = compact(line)
+        except Exception as exc:  # a failing sub-configuration is reported, not hidden
+            res = {"error": "%s: %s" % (type(exc).__name__, exc), "correct": False}
+        res["wall_s"] = time.perf_counter() - t0
+        out[name] = res
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_ours(args):
+    ctx = Ctx(args)
+    if args.workload == "mixed":
+        line = bench_mixed(ctx, full=True)
+    elif args.workload == "serving":
+        line = bench_serving(ctx, full=True)
+    elif args.workload in KEM_WORKLOADS:
+        line = bench_kem(ctx, args.workload, full=True)
+    else:
+        line = bench_single(ctx, args.workload, full=True)
+    want_configs = args.configs == "all" or (args.configs == "auto" and args.workload == "hqc1-bulk"
+                                              and ctx.dist.world == 1)
+    if want_configs:
+        line["configs"] = run_sub_configs(ctx)
+        line["configs_all_correct"] = all(c.get("correct") is True for c in line["configs"].values())
+    if ctx.dist.rank == 0:
         print(json.dumps(line), flush=True)
-    dist.close()
+    ctx.dist.close()
     return 0
 
 

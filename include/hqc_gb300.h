@@ -95,10 +95,28 @@ int hqc_keys_free(hqc_keyset_t* keys);
 int hqc_keys_info(const hqc_keyset_t* keys, int* level, int64_t* nkeys, const uint32_t** device_table);
 
 /* Decrypt with registered keys: ciphertext i uses key key_idx[i]
- * (device int32 [count]).  An index outside [0, nkeys) selects key 0.
- * Same kernel as hqc_decrypt_batch with validated supports. */
+ * (device int32 [count]).  Same kernel as hqc_decrypt_batch with
+ * validated supports.
+ * Key indices: in this and every other entry point that takes key_idx
+ * (the staged, no-alloc, plan and host forms, encryption and the KEM), an
+ * item whose index lies outside [0, nkeys) is skipped: none of its outputs
+ * (m row; u, v rows; K row; ok flag) is written.  The index says which key
+ * an item uses, which is public, so skipping it leaks nothing secret.  To
+ * learn whether a batch holds such items, call hqc_count_bad_key_idx.  The
+ * host-buffer forms (hqc_decrypt_host_keyed, hqc_kem_decaps_host) copy
+ * whole chunks back from device slots, so there a skipped item's host rows
+ * are set to zero (K zero, ok 0), as hqc_decrypt_mixed_host does for
+ * skipped items. */
 int hqc_decrypt_batch_keyed(int level, int64_t count, const uint64_t* u, const uint64_t* v, const hqc_keyset_t* keys,
                             const int32_t* key_idx, uint8_t* m_out, void* stream);
+
+/* Number of entries of key_idx (device int32 [count], count < 2^32) that
+ * lie outside [0, nkeys), written to *out (device uint32; zeroed by this
+ * call on the stream, then counted by one kernel).  The items these
+ * entries name are the ones the keyed entry points skip.  The paper has no
+ * counterpart: it is an argument check that runs on the device, since the
+ * indices live there. */
+int hqc_count_bad_key_idx(int64_t count, const int32_t* key_idx, int64_t nkeys, uint32_t* out, void* stream);
 
 /* Plain one-kernel-per-stage form (product, RM decode, RS decode as three
  * launches with intermediates in global memory): the comparison baseline
@@ -204,7 +222,9 @@ int hqc_kem_encaps(int level, int64_t count, const uint64_t* h, const uint64_t* 
  * (u, v) on the n and n1 n2 bits; K_out [count][32] = K(m', c) on a match,
  * K(sigma[key], c) otherwise (sigma [nkeys][k]), selected by mask.  ok_out
  * (optional, [count] uint32) receives 1 on a match.  Four kernels: fused
- * decrypt, derive, re-encrypt-and-compare, K. */
+ * decrypt, derive, re-encrypt-and-compare, K.  An item whose key index is
+ * outside [0, nkeys) is skipped: its K_out row and ok_out entry are not
+ * written (as in encapsulation, where its u, v and K rows are not). */
 int hqc_kem_decaps(int level, int64_t count, const hqc_keyset_t* keys, const uint64_t* h, const uint64_t* s,
                    const uint8_t* sigma, const int32_t* key_idx, const uint64_t* u, const uint64_t* v,
                    const uint8_t* salt, uint8_t* K_out, uint32_t* ok_out, void* workspace, size_t workspace_bytes,
@@ -397,7 +417,8 @@ int hqc_keygen_batch(int level, int64_t nkeys, const uint64_t* h, const uint32_t
 
 /* HQC.PKE.Encrypt (Algorithm 1): u = r1 + h*r2, v = first n1*n2 bits of
  * C.Encode(m) + s*r2 + e.  h, s [nkeys][W_u_pitch]; key_idx [count] (an
- * index outside [0, nkeys) selects key 0); m [count][k]; r1, r2
+ * item whose index is outside [0, nkeys) is skipped: its u and v rows are
+ * not written); m [count][k]; r1, r2
  * [count][wr]; e [count][we]; u_out [count][W_u_pitch] (pad bits zero);
  * v_out [count][W_v]. */
 int hqc_encrypt_batch(int level, int64_t count, const uint64_t* h, const uint64_t* s, int64_t nkeys,

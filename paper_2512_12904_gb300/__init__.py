@@ -23,7 +23,7 @@ __all__ = [
     "hqc_keys_register", "hqc_decrypt_batch_keyed", "hqc_staged_workspace_bytes",
     "hqc_decrypt_batch_staged", "hqc_decrypt_batch_staged_noalloc", "hqc_decrypt_debug", "hqc_mixed_workspace_bytes",
     "hqc_decrypt_mixed", "hqc_set_launch_config", "hqc_get_launch_shape", "hqc_keygen_batch",
-    "hqc_encrypt_batch", "LEVELS", "Plan", "hqc_plan_create_keyed", "hqc_plan_create_mixed", "hqc_serve_run",
+    "hqc_encrypt_batch", "hqc_count_bad_key_idx", "LEVELS", "Plan", "hqc_plan_create_keyed", "hqc_plan_create_mixed", "hqc_serve_run",
     "SERVE_STATUS", "hqc_decrypt_host_keyed", "hqc_host_workspace_bytes", "hqc_shake256_batch",
     "hqc_kem_keygen", "hqc_kem_workspace_bytes", "hqc_kem_encaps", "hqc_kem_decaps",
     "hqc_kem_host_workspace_bytes", "hqc_kem_decaps_host", "hqc_mixed_host_workspace_bytes",
@@ -109,6 +109,7 @@ def load(build_if_missing: bool = True):
             "hqc_decrypt_mixed_host": (i32, [i64, P, P, i64, P, P, i64, i64, P, sz, P]),
             "hqc_kem_decaps_host": (i32, [i32, i64, P, P, P, P, P, P, P, P, P, P, i64, P, sz, P]),
             "hqc_keygen_batch": (i32, [i32, i64, P, P, P, P, P]),
+            "hqc_count_bad_key_idx": (i32, [i64, P, i64, P, P]),
             "hqc_encrypt_batch": (i32, [i32, i64, P, P, i64, P, P, P, P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
@@ -244,12 +245,26 @@ def hqc_decrypt_batch_keyed(level, u, v, keys: Keyset, key_idx, m_out=None, stre
     u, v = _as_u64(u), _as_u64(v)
     cnt = u.shape[0]
     if m_out is None:
-        m_out = torch.empty((cnt, P.k), dtype=torch.uint8, device=u.device)
+        m_out = torch.zeros((cnt, P.k), dtype=torch.uint8, device=u.device)
     _check(load().hqc_decrypt_batch_keyed(level, cnt, _dev_ptr(u, torch.int64, (cnt, P.W_u_pitch), "u"),
                                           _dev_ptr(v, torch.int64, (cnt, P.W_v), "v"), keys.handle,
                                           _dev_ptr(key_idx, torch.int32, (cnt,), "key_idx"),
                                           _dev_ptr(m_out, torch.uint8, (cnt, P.k), "m_out"), _stream(stream)))
     return m_out
+
+
+def hqc_count_bad_key_idx(key_idx, nkeys: int, stream=None) -> int:
+    """How many entries of key_idx (a device int32 tensor) lie outside
+    [0, nkeys): the items every keyed entry point skips.  Counted on the
+    device by hqc_count_bad_key_idx; this wrapper waits for the result."""
+    torch = _torch()
+    cnt = key_idx.numel()
+    out = torch.empty((1,), dtype=torch.int32, device=key_idx.device)
+    _check(load().hqc_count_bad_key_idx(cnt, _dev_ptr(key_idx, torch.int32, (cnt,), "key_idx"), int(nkeys),
+                                        _dev_ptr(out, torch.int32, (1,), "out"), _stream(stream)))
+    if stream is not None:
+        stream.synchronize()
+    return int(out.item()) & 0xFFFFFFFF
 
 
 def hqc_staged_workspace_bytes(level: int, count: int) -> int:
@@ -264,7 +279,7 @@ def hqc_decrypt_batch_staged(level, u, v, y=None, keys: Keyset = None, key_idx=N
     u, v = _as_u64(u), _as_u64(v)
     cnt = u.shape[0]
     if m_out is None:
-        m_out = torch.empty((cnt, P.k), dtype=torch.uint8, device=u.device)
+        m_out = torch.zeros((cnt, P.k), dtype=torch.uint8, device=u.device)
     need = hqc_staged_workspace_bytes(level, cnt)
     if workspace is None:
         workspace = torch.empty(max(need, 16), dtype=torch.uint8, device=u.device)
@@ -296,7 +311,7 @@ def hqc_decrypt_batch_staged_noalloc(level, u, v, y=None, keys: Keyset = None, k
     u, v = _as_u64(u), _as_u64(v)
     cnt = u.shape[0]
     if m_out is None:
-        m_out = torch.empty((cnt, P.k), dtype=torch.uint8, device=u.device)
+        m_out = torch.zeros((cnt, P.k), dtype=torch.uint8, device=u.device)
     yp, kp, ip = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
     if keys is not None:
         kp = keys.handle
@@ -403,9 +418,9 @@ def hqc_encrypt_batch(level, h, s, key_idx, m, r1, r2, e, u_out=None, v_out=None
     cnt = m.shape[0]
     dev = m.device
     if u_out is None:
-        u_out = torch.empty((cnt, P.W_u_pitch), dtype=torch.int64, device=dev)
+        u_out = torch.zeros((cnt, P.W_u_pitch), dtype=torch.int64, device=dev)
     if v_out is None:
-        v_out = torch.empty((cnt, P.W_v), dtype=torch.int64, device=dev)
+        v_out = torch.zeros((cnt, P.W_v), dtype=torch.int64, device=dev)
     r1, r2, e = [t.view(torch.int32) if t.dtype == torch.uint32 else t for t in (r1, r2, e)]
     _check(load().hqc_encrypt_batch(level, cnt, _dev_ptr(h, torch.int64, (nk, P.W_u_pitch), "h"),
                                     _dev_ptr(s, torch.int64, (nk, P.W_u_pitch), "s"), nk,
@@ -571,7 +586,7 @@ def hqc_decrypt_host_keyed(level, u_host, v_host, keys: Keyset, key_idx_host, m_
     if key_idx_host.dtype != torch.int32 or tuple(key_idx_host.shape) != (cnt,):
         raise ValueError("key_idx_host must be int32 [count]")
     if m_host is None:
-        m_host = torch.empty((cnt, P.k), dtype=torch.uint8).pin_memory()
+        m_host = torch.zeros((cnt, P.k), dtype=torch.uint8).pin_memory()
     if workspace is None:
         workspace = torch.empty(hqc_host_workspace_bytes(level, chunk if chunk > 0 else max(1, min(cnt, 16384))),
                                 dtype=torch.uint8, device="cuda")
@@ -634,9 +649,9 @@ def hqc_kem_encaps(level, h, s, key_idx, m, salt, u_out=None, v_out=None, K_out=
     h, s = _as_u64(h), _as_u64(s)
     cnt = key_idx.shape[0]
     dev = key_idx.device
-    u_out = torch.empty((cnt, P.W_u_pitch), dtype=torch.int64, device=dev) if u_out is None else _as_u64(u_out)
-    v_out = torch.empty((cnt, P.W_v), dtype=torch.int64, device=dev) if v_out is None else _as_u64(v_out)
-    K_out = torch.empty((cnt, 32), dtype=torch.uint8, device=dev) if K_out is None else K_out
+    u_out = torch.zeros((cnt, P.W_u_pitch), dtype=torch.int64, device=dev) if u_out is None else _as_u64(u_out)
+    v_out = torch.zeros((cnt, P.W_v), dtype=torch.int64, device=dev) if v_out is None else _as_u64(v_out)
+    K_out = torch.zeros((cnt, 32), dtype=torch.uint8, device=dev) if K_out is None else K_out
     ws = _kem_ws(level, cnt, workspace, dev)
     _check(load().hqc_kem_encaps(level, cnt, _dev_ptr(h, torch.int64), _dev_ptr(s, torch.int64), h.shape[0],
                                  _dev_ptr(key_idx, torch.int32, (cnt,), "key_idx"),
@@ -657,8 +672,8 @@ def hqc_kem_decaps(level, keys: Keyset, h, s, sigma, key_idx, u, v, salt, K_out=
     h, s, u, v = _as_u64(h), _as_u64(s), _as_u64(u), _as_u64(v)
     cnt = key_idx.shape[0]
     dev = key_idx.device
-    K_out = torch.empty((cnt, 32), dtype=torch.uint8, device=dev) if K_out is None else K_out
-    ok_out = torch.empty((cnt,), dtype=torch.int32, device=dev) if ok_out is None else ok_out
+    K_out = torch.zeros((cnt, 32), dtype=torch.uint8, device=dev) if K_out is None else K_out
+    ok_out = torch.zeros((cnt,), dtype=torch.int32, device=dev) if ok_out is None else ok_out
     ws = _kem_ws(level, cnt, workspace, dev)
     _check(load().hqc_kem_decaps(level, cnt, keys.handle, _dev_ptr(h, torch.int64), _dev_ptr(s, torch.int64),
                                  _dev_ptr(sigma, torch.uint8, (keys.nkeys, P.k), "sigma"),

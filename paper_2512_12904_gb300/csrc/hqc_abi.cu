@@ -76,6 +76,18 @@ int check_common(int level, int64_t count, const uint64_t* u, const uint64_t* v,
 
 int launch_result(cudaError_t e, const char* what) { return e == cudaSuccess ? HQC_OK : cuda_fail(e, what); }
 
+// Adds to *out the number of key_idx entries outside [0, nkeys): one
+// warp-wide sum per warp, one atomic per warp that found any.
+constexpr int COUNT_THREADS = 256;
+__global__ void __launch_bounds__(COUNT_THREADS) k_count_bad_key_idx(int64_t count, const int32_t* __restrict__ key_idx,
+                                                                     int64_t nkeys, uint32_t* __restrict__ out) {
+  uint32_t bad = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    bad += (uint32_t)__ldg(key_idx + i) >= (uint64_t)nkeys ? 1u : 0u;
+  bad = __reduce_add_sync(0xFFFFFFFFu, bad);
+  if ((threadIdx.x & 31) == 0 && bad) atomicAdd(out, bad);
+}
+
 }  // namespace
 
 void hqc::set_last_error(const char* msg) { g_err = msg; }
@@ -179,6 +191,27 @@ int hqc_decrypt_batch_keyed(int level, int64_t count, const uint64_t* u, const u
   a.m = m_out;
   return launch_result(hqc::launch_fused(level, true, a, (cudaStream_t)stream, g_cfg[hqc::level_index(level) + 1]),
                        "fused keyed decrypt launch");
+}
+
+int hqc_count_bad_key_idx(int64_t count, const int32_t* key_idx, int64_t nkeys, uint32_t* out, void* stream) {
+  g_err.clear();
+  if (count < 0 || count > (int64_t)0xFFFFFFFFu) return fail(HQC_EINVAL, "count must be in [0, 2^32)");
+  if (nkeys < 0) return fail(HQC_EINVAL, "nkeys must be >= 0");
+  if (!out || !aligned(out, 4)) return fail(HQC_EINVAL, "out must be a non-NULL 4-byte aligned device pointer");
+  if (count > 0 && (!key_idx || !aligned(key_idx, 4)))
+    return fail(HQC_EINVAL, "key_idx must be a non-NULL 4-byte aligned device pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(uint32_t), st);
+  if (e != cudaSuccess) return cuda_fail(e, "zeroing the count");
+  if (count == 0) return HQC_OK;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t want = (count + COUNT_THREADS - 1) / COUNT_THREADS;
+  const int64_t cap = (int64_t)(sms > 0 ? sms : 1) * 8;
+  const unsigned grid = (unsigned)(want < cap ? want : cap);
+  k_count_bad_key_idx<<<grid, COUNT_THREADS, 0, st>>>(count, key_idx, nkeys, out);
+  return launch_result(cudaGetLastError(), "count launch");
 }
 
 size_t hqc_staged_workspace_bytes(int level, int64_t count) {

@@ -57,11 +57,14 @@ __global__ void __launch_bounds__(FusedBound<LEVEL>::threads, 1) k_decrypt_fused
   for (int64_t q = (int64_t)blockIdx.x * nw + warp; q < ngroups; q += (int64_t)gridDim.x * nw) {
     auto rows = [&](int g, const uint64_t*& u, const uint64_t*& v, const uint32_t*& y, uint8_t*& m) {
       const int64_t it0 = q * G + g;
-      const bool ok = it0 < a.count;
+      bool ok = it0 < a.count;
       const int64_t it = ok ? it0 : q * G;
       if (KEYED) {
+        // an index outside [0, nkeys) skips the item: m stays untouched
         const uint32_t ki = (uint32_t)__ldg(a.key_idx + it);
-        y = a.y + (ki < (uint64_t)a.nkeys ? (int64_t)ki : 0) * LV::w;  // out-of-range index -> key 0
+        const bool kok = ki < (uint64_t)a.nkeys;
+        y = a.y + (kok ? (int64_t)ki : 0) * LV::w;
+        ok = ok && kok;
       } else {
         y = a.y + it * LV::w;
       }
@@ -103,11 +106,14 @@ __global__ void __launch_bounds__(TeamBound<LEVEL>::threads, 1) k_decrypt_team(D
   for (int64_t q = (int64_t)blockIdx.x * nteams + team; q < ngroups; q += (int64_t)gridDim.x * nteams) {
     auto rows = [&](int g, const uint64_t*& u, const uint64_t*& v, const uint32_t*& y, uint8_t*& m) {
       const int64_t it0 = 2 * q + g;
-      const bool ok = it0 < a.count;
+      bool ok = it0 < a.count;
       const int64_t it = ok ? it0 : 2 * q;
       if (KEYED) {
+        // an index outside [0, nkeys) skips the item: m stays untouched
         const uint32_t ki = (uint32_t)__ldg(a.key_idx + it);
-        y = a.y + (ki < (uint64_t)a.nkeys ? (int64_t)ki : 0) * LV::w;  // out-of-range index -> key 0
+        const bool kok = ki < (uint64_t)a.nkeys;
+        y = a.y + (kok ? (int64_t)ki : 0) * LV::w;
+        ok = ok && kok;
       } else {
         y = a.y + it * LV::w;
       }
@@ -233,16 +239,20 @@ __global__ void __launch_bounds__(32 * T, 4) k_decrypt_latency(DecArgs a) {
   const TeamSync sync{1u, 32u * T};
   for (int64_t it = blockIdx.x; it < a.count; it += gridDim.x) {
     auto rows = [&](int g, const uint64_t*& u, const uint64_t*& v, const uint32_t*& y, uint8_t*& m) {
+      bool ok = g == 0;
       if (KEYED) {
+        // an index outside [0, nkeys) skips the item: m stays untouched
         const uint32_t ki = (uint32_t)__ldg(a.key_idx + it);
-        y = a.y + (ki < (uint64_t)a.nkeys ? (int64_t)ki : 0) * LV::w;  // out-of-range index -> key 0
+        const bool kok = ki < (uint64_t)a.nkeys;
+        y = a.y + (kok ? (int64_t)ki : 0) * LV::w;
+        ok = ok && kok;
       } else {
         y = a.y + it * LV::w;
       }
       u = a.u + it * LV::W_u_pitch;
       v = a.v + it * LV::W_v;
       m = a.m + it * LV::k;
-      return g == 0;
+      return ok;
     };
     decrypt_team<LV, !KEYED, T, 1>(gf, ws, wt, lane, sync, rows);
   }
@@ -371,9 +381,12 @@ __global__ void __launch_bounds__(STAGE_THREADS) k_stage_rm(int64_t count, const
 // K3: one warp per ciphertext: Reed-Solomon decode (and the debug dump).
 constexpr int RS_SCRATCH_WORDS = 24 + RS_SCRATCH;  // the n1 received bytes, then the RS scratch
 
+// With key_idx given, a ciphertext whose index is outside [0, nkeys) is
+// skipped (its m row stays untouched), as in the fused kernels.
 template <int LEVEL, bool DEBUG>
 __global__ void __launch_bounds__(STAGE_THREADS) k_stage_rs(int64_t count, const uint8_t* __restrict__ r_in,
-                                                           uint8_t* __restrict__ m_out, DebugArgs d) {
+                                                           uint8_t* __restrict__ m_out, DebugArgs d,
+                                                           const int32_t* __restrict__ key_idx, int64_t nkeys) {
   using LV = Level<LEVEL>;
   static_assert(LV::n1 <= 96, "received bytes fit in 24 words");
   extern __shared__ __align__(16) uint8_t smem[];
@@ -382,6 +395,7 @@ __global__ void __launch_bounds__(STAGE_THREADS) k_stage_rs(int64_t count, const
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t it = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
   if (it >= count) return;
+  if (key_idx && (uint32_t)__ldg(key_idx + it) >= (uint64_t)nkeys) return;
   const GF gf(smem, lane);
   uint32_t* base = reinterpret_cast<uint32_t*>(smem + GF_TABLE_BYTES) + warp * RS_SCRATCH_WORDS;
   uint8_t* rb = reinterpret_cast<uint8_t*>(base);
@@ -754,7 +768,7 @@ static cudaError_t staged_level(const DecArgs& a, uint64_t* w, uint8_t* r, const
     const int64_t blocks = (a.count + wpb - 1) / wpb;
     DebugArgs dd{};
     if (DEBUG) dd = *d;
-    kern<<<(unsigned)blocks, STAGE_THREADS, sm, st>>>(a.count, r, a.m, dd);
+    kern<<<(unsigned)blocks, STAGE_THREADS, sm, st>>>(a.count, r, a.m, dd, KEYED ? a.key_idx : nullptr, a.nkeys);
     return cudaGetLastError();
   }
 }

@@ -268,7 +268,8 @@ __global__ void __launch_bounds__(EncBound<LEVEL>::threads, 1) k_encrypt(int64_t
   uint32_t* sup = u2 + LV::U2W_FULL;
   for (int64_t it = (int64_t)blockIdx.x * nw + warp; it < count; it += (int64_t)gridDim.x * nw) {
     const uint32_t ki = (uint32_t)key_idx[it];
-    const int64_t key = ki < (uint64_t)nkeys ? (int64_t)ki : 0;
+    if (ki >= (uint64_t)nkeys) continue;  // skipped item: outputs untouched (the index is public)
+    const int64_t key = (int64_t)ki;
 
     // u = r1 + h * r2
     full_product_to_smem<LV, LV::wr, !VALID>(u2, sup, h + key * LV::W_u_pitch,
@@ -344,7 +345,10 @@ __global__ void __launch_bounds__(EncTeamBound<LEVEL>::threads, 1)
   const TeamSync sync{(uint32_t)(1 + team)};
   for (int64_t it = (int64_t)blockIdx.x * nteams + team; it < count; it += (int64_t)gridDim.x * nteams) {
     const uint32_t ki = (uint32_t)key_idx[it];
-    const int64_t key = ki < (uint64_t)nkeys ? (int64_t)ki : 0;
+    // skipped item: outputs untouched; both warps of the team see the same
+    // index, so they skip together and no barrier is left waiting
+    if (ki >= (uint64_t)nkeys) continue;
+    const int64_t key = (int64_t)ki;
     if (tid == 0) *flag = 0u;
     // u = r1 + h * r2
     load_supports<LV::n, LV::wr, 64>(sup, r2 + it * LV::wr, tid);

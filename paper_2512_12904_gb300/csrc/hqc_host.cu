@@ -224,6 +224,10 @@ extern "C" int hqc_decrypt_host_keyed(int level, int64_t count, const uint64_t* 
     return e;
   };
   auto comp = [&](int64_t, int64_t n, const Slot& s, cudaStream_t st) {
+    // the m rows come back from this slot: the ones the kernel skips (key
+    // index outside [0, nkeys)) come back as zeros, not as an older chunk's
+    cudaError_t e = cudaMemsetAsync(s.out, 0, (size_t)n * p.k, st);
+    if (e != cudaSuccess) return e;
     hqc::DecArgs a;
     a.count = n;
     a.u = s.u;
@@ -273,6 +277,11 @@ extern "C" int hqc_kem_decaps_host(int level, int64_t count, const hqc_keyset_t*
   int rc_kem = HQC_OK;
   char kem_err[400] = "";
   auto comp = [&](int64_t, int64_t n, const Slot& sl, cudaStream_t st) {
+    // K and ok come back from this slot: items skipped for a bad key index
+    // come back as zero K rows with ok = 0
+    cudaError_t e = cudaMemsetAsync(sl.out, 0, (size_t)n * 32, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sl.ok, 0, (size_t)n * 4, st);
+    if (e != cudaSuccess) return e;
     rc_kem = hqc_kem_decaps(level, n, keys, h, s, sigma, sl.k, sl.u, sl.v, sl.salt, sl.out, sl.ok, sl.kem, L.kem,
                             st);
     if (rc_kem != HQC_OK) snprintf(kem_err, sizeof kem_err, "%s", hqc_last_error());

@@ -237,14 +237,14 @@ __global__ void __launch_bounds__(KEM_K_THREADS) k_kem_K(int64_t count, const ui
   static_assert(P1 == KW + LV::W_u - 1 && R8 > 0, "U ends inside its last word");
   const int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (it >= count) return;
+  const uint32_t ki = (uint32_t)__ldg(key_idx + it);
+  if (ki >= (uint64_t)nkeys) return;  // skipped item: K untouched (the index is public)
   const uint64_t* mrow = reinterpret_cast<const uint64_t*>(m + it * LV::k);
   uint64_t keep = ~0ull;
   const uint64_t* grow = mrow;
   if (ok) {
     keep = 0ull - (uint64_t)(__ldg(ok + it) != 0u);
-    const uint32_t ki = (uint32_t)__ldg(key_idx + it);
-    const int64_t key = ki < (uint64_t)nkeys ? (int64_t)ki : 0;
-    grow = reinterpret_cast<const uint64_t*>(sigma + key * LV::k);
+    grow = reinterpret_cast<const uint64_t*>(sigma + (int64_t)ki * LV::k);
   }
   const uint64_t* urow = u + it * LV::W_u_pitch;
   const uint64_t* vrow = v + it * LV::W_v;

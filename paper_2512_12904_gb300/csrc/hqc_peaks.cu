@@ -59,6 +59,38 @@ __global__ void __launch_bounds__(PEAK_THREADS) k_int_ops(int iters, uint32_t se
   if (r == 0x12345678u) out[blockIdx.x] = r;
 }
 
+// Integer issue ceiling across two pipes: half of the operations are
+// funnel shifts and XORs (integer ALU pipe), half are 32-bit multiply-adds
+// with a runtime odd multiplier (IMAD, fused multiply-add pipe).  A kernel
+// that moves part of its integer work to multiply-adds (as the decryption
+// kernels do for butterflies and table addresses) is bounded by this rate,
+// not by the ALU pipe alone.
+__global__ void __launch_bounds__(PEAK_THREADS) k_int_mix(int iters, uint32_t seed, uint32_t* out) {
+  uint32_t a0 = seed ^ threadIdx.x, a1 = a0 * 3u, b0 = a0 + 1u, b1 = a1 + 1u;
+  uint32_t c0 = a0 * 5u, c1 = a0 * 7u, c2 = a0 * 11u, c3 = a0 * 13u;
+  const uint32_t s = seed & 31u, M = seed | 1u;
+  for (int it = 0; it < iters; it++) {
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      // 4 ALU ops (2 funnel shifts, 2 XORs) and 4 multiply-adds per step
+      a0 ^= __funnelshift_r(b0, a1, s);
+      b1 ^= __funnelshift_r(a1, b0, s);
+      c0 = c0 * M + c1;
+      c1 = c1 * M + c2;
+      c2 = c2 * M + c3;
+      c3 = c3 * M + c0;
+      a1 ^= __funnelshift_r(b1, a0, s);
+      b0 ^= __funnelshift_r(a0, b1, s);
+      c0 = c0 * M + c2;
+      c1 = c1 * M + c3;
+      c2 = c2 * M + c0;
+      c3 = c3 * M + c1;
+    }
+  }
+  const uint32_t r = a0 ^ a1 ^ b0 ^ b1 ^ c0 ^ c1 ^ c2 ^ c3;
+  if (r == 0x12345678u) out[blockIdx.x] = r;
+}
+
 template <class F>
 float time_ms(F launch, int reps) {
   cudaEvent_t e0, e1;
@@ -107,6 +139,22 @@ double hqc_peak_int_ops_per_s(void) {
   cudaFree(out);
   if (cudaGetLastError() != cudaSuccess || ms <= 0) return 0;
   const double ops = (double)grid * PEAK_THREADS * iters * 8 * 8 * 2;
+  return ops / (ms * 1e-3);
+}
+
+// 32-bit integer operations per second when half are ALU-pipe funnel
+// shifts/XORs and half multiply-adds on the FMA pipe; 0 on error.
+double hqc_peak_int_issue_ops_per_s(void) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  uint32_t* out = nullptr;
+  if (cudaMalloc(&out, 4096 * sizeof(uint32_t)) != cudaSuccess) return 0;
+  const int iters = 4000, grid = sms * 2;
+  const float ms = time_ms([&] { k_int_mix<<<grid, PEAK_THREADS>>>(iters, 0x9E3779B9u, out); }, 5);
+  cudaFree(out);
+  if (cudaGetLastError() != cudaSuccess || ms <= 0) return 0;
+  const double ops = (double)grid * PEAK_THREADS * iters * 8 * 16;
   return ops / (ms * 1e-3);
 }
 

@@ -169,3 +169,43 @@ def test_decaps_from_host_buffers_matches_device_path(hqc, level):
     with pytest.raises(hqc.HqcError):
         hqc.hqc_kem_decaps_host(level, keys, hd, sd, sig, k_h, u_h, v_h, s_h, chunk=64, workspace=short)
     keys.free()
+
+
+@pytest.mark.parametrize("level", LEVELS)
+def test_kem_skips_bad_key_index(hqc, level):
+    """An item whose key index is outside [0, nkeys) is skipped by
+    encapsulation (u, v and K rows untouched) and by decapsulation (K row
+    and ok entry untouched; zero from host buffers); every other item
+    matches the oracle."""
+    P, h, y, s, sigma, kidx, m, salt = _kem_setup(hqc, level, 4, 60, tag=900 + 10 * level)
+    bad_rows = [2, 17, 59]
+    bad = kidx.astype(np.int32).copy()
+    bad[bad_rows] = (4, -1, 10 ** 7)
+    good = np.setdiff1d(np.arange(60), bad_rows)
+    ou, ov, oK = oracle.kem_encaps(level, h, s, kidx, m, salt)
+    u0 = torch.full((60, P.W_u_pitch), 77, dtype=torch.int64, device="cuda")
+    v0 = torch.full((60, P.W_v), 77, dtype=torch.int64, device="cuda")
+    K0 = torch.full((60, 32), 0x3C, dtype=torch.uint8, device="cuda")
+    gu, gv, gK = hqc.hqc_kem_encaps(level, cu64(h), cu64(s), cu32(bad), cu8(m), cu8(salt), u_out=u0, v_out=v0,
+                                    K_out=K0)
+    gu, gv, gK = host_u64(gu), host_u64(gv), gK.cpu().numpy()
+    assert (gu[good] == ou[good]).all() and (gv[good] == ov[good]).all() and (gK[good] == oK[good]).all()
+    assert (gu[bad_rows] == 77).all() and (gv[bad_rows] == 77).all() and (gK[bad_rows] == 0x3C).all()
+    keys = hqc.Keyset(level, y)
+    K1 = torch.full((60, 32), 0x3C, dtype=torch.uint8, device="cuda")
+    ok1 = torch.full((60,), 9, dtype=torch.int32, device="cuda")
+    Kd, okd = hqc.hqc_kem_decaps(level, keys, cu64(h), cu64(s), cu8(sigma), cu32(bad), cu64(ou), cu64(ov), cu8(salt),
+                                 K_out=K1, ok_out=ok1)
+    Kd, okd = Kd.cpu().numpy(), okd.cpu().numpy()
+    assert (Kd[good] == oK[good]).all() and (okd[good] == 1).all()
+    assert (Kd[bad_rows] == 0x3C).all() and (okd[bad_rows] == 9).all()
+    # from host buffers the chunks come back whole: skipped rows are zero
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    ws = torch.empty(hqc.hqc_kem_host_workspace_bytes(level, 16), dtype=torch.uint8, device="cuda")
+    K_h, ok_h = hqc.hqc_kem_decaps_host(level, keys, cu64(h), cu64(s), cu8(sigma), pin(bad), pin(ou.view(np.int64)),
+                                        pin(ov.view(np.int64)), pin(salt), chunk=16, workspace=ws)
+    torch.cuda.synchronize()
+    K_h, ok_h = K_h.numpy(), ok_h.numpy()
+    assert (K_h[good] == oK[good]).all() and (ok_h[good] == 1).all()
+    assert (K_h[bad_rows] == 0).all() and (ok_h[bad_rows] == 0).all()
+    keys.free()

@@ -133,17 +133,107 @@ def test_ragged_counts(hqc, level, shape):
 def test_latency_form_at_its_limit_and_past_it(hqc, level):
     """Batches of 512 (the latency form's limit, one team per ciphertext)
     and 513 (the persistent fused kernel) both match the oracle's messages,
-    keyed with an out-of-range key index in each (read as key 0)."""
+    keyed with an out-of-range key index in each (that item is skipped: its
+    m row keeps what the caller put there)."""
     wl = honest(level, 4, 513, first_ct=12000, tag=13)
     keys = hqc.Keyset(level, wl.y)
     kidx = wl.key_idx.astype(np.int32).copy()
     want = wl.m.copy()
     kidx[7] = 10 ** 6
-    want[7] = oracle.decrypt(level, wl.u[7:8], wl.v[7:8], wl.y[0:1])[0]
+    want[7] = 0xA5
     for cnt in (512, 513):
-        got = host(hqc.hqc_decrypt_batch_keyed(level, u64(wl.u[:cnt]), u64(wl.v[:cnt]), keys, dev(kidx[:cnt])))
+        out = torch.full((cnt, wl.P.k), 0xA5, dtype=torch.uint8, device="cuda")
+        got = host(hqc.hqc_decrypt_batch_keyed(level, u64(wl.u[:cnt]), u64(wl.v[:cnt]), keys, dev(kidx[:cnt]),
+                                               m_out=out))
         assert (got == want[:cnt]).all(), cnt
     keys.free()
+
+
+BAD_KEY_ROWS = (3, 40, 41, 69)
+
+
+def with_bad_keys(kidx, nkeys):
+    """Key indices with entries outside [0, nkeys): nkeys itself, -1, a
+    large positive value and INT32_MIN."""
+    k = kidx.astype(np.int32).copy()
+    for r, val in zip(BAD_KEY_ROWS, (nkeys, -1, 10 ** 6, -2 ** 31)):
+        k[r] = val
+    return k
+
+
+@pytest.mark.parametrize("level", LEVELS)
+def test_bad_key_index_is_skipped_by_every_keyed_form(hqc, level):
+    """One rule for a key index outside [0, nkeys): the item is skipped and
+    its output row keeps the caller's bytes, in the keyed fused kernel (both
+    the latency form and the persistent kernel), the per-stage form, the
+    allocation-free form and a graph plan (the host-buffer pipeline returns
+    zero rows for them); every other item matches the oracle, and
+    hqc_count_bad_key_idx counts them."""
+    wl = honest(level, 4, 70, first_ct=14000, tag=24)
+    keys = hqc.Keyset(level, wl.y)
+    kidx_np = with_bad_keys(wl.key_idx, 4)
+    kidx = dev(kidx_np)
+    ud, vd = u64(wl.u), u64(wl.v)
+    want = wl.m.copy()
+    want[list(BAD_KEY_ROWS)] = 0xA5
+    assert hqc.hqc_count_bad_key_idx(kidx, 4) == len(BAD_KEY_ROWS)
+    assert hqc.hqc_count_bad_key_idx(kidx, 2 ** 31 - 1) == 2  # only the negative ones
+    assert hqc.hqc_count_bad_key_idx(kidx[:0], 4) == 0
+
+    def fresh():
+        return torch.full((70, wl.P.k), 0xA5, dtype=torch.uint8, device="cuda")
+
+    outs = {}
+    outs["latency"] = hqc.hqc_decrypt_batch_keyed(level, ud, vd, keys, kidx, m_out=fresh())
+    hqc.hqc_set_launch_config(level, 4, 0)
+    try:
+        outs["persistent"] = hqc.hqc_decrypt_batch_keyed(level, ud, vd, keys, kidx, m_out=fresh())
+    finally:
+        hqc.hqc_set_launch_config(level, 0, 0)
+    outs["staged"] = hqc.hqc_decrypt_batch_staged(level, ud, vd, keys=keys, key_idx=kidx, m_out=fresh())
+    outs["noalloc"] = hqc.hqc_decrypt_batch_staged_noalloc(level, ud, vd, keys=keys, key_idx=kidx, m_out=fresh())
+    m_plan = fresh()
+    plan = hqc.hqc_plan_create_keyed(level, ud, vd, keys, kidx, m_plan, autotune=False)
+    m_plan.fill_(0xA5)
+    plan.launch()
+    outs["plan"] = m_plan
+    u_h = torch.from_numpy(wl.u.view(np.int64).copy()).pin_memory()
+    v_h = torch.from_numpy(wl.v.view(np.int64).copy()).pin_memory()
+    k_h = torch.from_numpy(kidx_np).pin_memory()
+    m_h = torch.full((70, wl.P.k), 0xA5, dtype=torch.uint8).pin_memory()
+    ws = torch.empty(hqc.hqc_host_workspace_bytes(level, 16), dtype=torch.uint8, device="cuda")
+    hqc.hqc_decrypt_host_keyed(level, u_h, v_h, keys, k_h, m_h, chunk=16, workspace=ws)
+    torch.cuda.synchronize()
+    for name, got in outs.items():
+        assert (got.cpu().numpy() == want).all(), name
+    # the host-buffer form copies whole chunks back: skipped rows are zero
+    want_h = want.copy()
+    want_h[list(BAD_KEY_ROWS)] = 0
+    assert (m_h.numpy() == want_h).all()
+    plan.destroy()
+    keys.free()
+
+
+@pytest.mark.parametrize("level", LEVELS)
+def test_encrypt_skips_bad_key_index(hqc, level):
+    """Encryption follows the same rule: an item whose key index is outside
+    [0, nkeys) leaves its u and v rows as the caller left them."""
+    P = oracle.params(level)
+    S = synth.Shape.of(P)
+    h, x, y = synth.keys(S, 4, first=60)
+    s = oracle.keygen(level, h, x, y)
+    m, r1, r2, e = synth.ciphertext_randomness(S, 70, first=70)
+    kidx = synth.key_assignment(70, 4, tag=25)
+    want_u, want_v = oracle.encrypt(level, h, s, kidx, m, r1, r2, e)
+    bad = with_bad_keys(kidx, 4)
+    u_out = torch.full((70, P.W_u_pitch), 0x0F0F, dtype=torch.int64, device="cuda")
+    v_out = torch.full((70, P.W_v), 0x0F0F, dtype=torch.int64, device="cuda")
+    gu, gv = hqc.hqc_encrypt_batch(level, u64(h), u64(s), dev(bad), dev(m), i32(r1), i32(r2), i32(e),
+                                   u_out=u_out, v_out=v_out)
+    gu, gv = host(gu).view(np.uint64), host(gv).view(np.uint64)
+    good = np.setdiff1d(np.arange(70), BAD_KEY_ROWS)
+    assert (gu[good] == want_u[good]).all() and (gv[good] == want_v[good]).all()
+    assert (gu[list(BAD_KEY_ROWS)] == 0x0F0F).all() and (gv[list(BAD_KEY_ROWS)] == 0x0F0F).all()
 
 
 @pytest.mark.parametrize("level", LEVELS)
