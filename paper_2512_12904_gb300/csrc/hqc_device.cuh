@@ -7,6 +7,8 @@
 // Sec. III-B and III-D of the paper).
 #pragma once
 #include <cstdint>
+#include <type_traits>
+
 #include "hqc_params.cuh"
 
 namespace hqc {
@@ -421,6 +423,100 @@ struct RSDebugRow {
 // (128), log Lambda and log Omega (64 halfwords each)
 constexpr int RS_SCRATCH = 176;
 
+// Berlekamp-Massey (S8) on SEG lanes: exactly 2 delta iterations over the
+// syndromes logS (log form, with log-zero padding below index 0); writes the
+// logs of Lambda_0..Lambda_{2 delta} to logLam and returns the LFSR length L.
+template <class LV, int SEG, bool ALL_POS>
+__device__ __forceinline__ uint32_t rs_bm(const GF& gf, const uint16_t* logS, uint16_t* logLam, int lane, bool active,
+                                          const RSDebugRow* dbg) {
+  constexpr int NR = LV::NR, CAP = LV::CAP;
+  const int sl = lane % SEG;
+  // Berlekamp-Massey; lane owns coefficient c = sl + SEG x.  x^m B is only
+  // ever multiplied, so it is carried in log form (lbp, 511 = zero): it
+  // shifts with the same shuffles and, when replaced by Lambda, takes the
+  // logs of Lambda already computed for the discrepancy.
+  // At the start of iteration r, deg Lambda <= r and deg x^m B <= r + 1, so
+  // coefficient block x (c in [SEG x, SEG x + SEG)) is still all zero in
+  // both while r + 2 <= SEG x: iteration r works on the first
+  // NA(r) = min(NC, floor((r + 2) / SEG) + 1) blocks only.  r is public,
+  // so the trip counts stay independent of the data.
+  constexpr int NC = cdiv(CAP, SEG);
+  uint32_t lam[NC], lbp[NC];
+#pragma unroll
+  for (int x = 0; x < NC; x++) {
+    const int c = sl + SEG * x;
+    lam[x] = c == 0;
+    lbp[x] = c == 1 ? 0u : GF_LOG_ZERO;  // x^m B with m = 1, B = 1
+  }
+  uint32_t lb = 0, L = 0;  // log b (b = 1), LFSR length
+  auto bm_iter = [&](auto na, int rr) {
+    constexpr int NA = decltype(na)::value;
+    uint32_t llam[NA];
+    uint32_t part = 0;
+#pragma unroll
+    for (int x = 0; x < NA; x++) {
+      const int c = sl + SEG * x;  // rr - c >= -64: padding covers c > rr
+      llam[x] = gf.log(lam[x]);
+      part ^= gf.mul_l(llam[x], logS[rr - c]);
+    }
+    if constexpr (SEG == 32) {
+      part = __reduce_xor_sync(FULL_MASK, part);  // one warp-wide reduction
+    } else if constexpr (SEG == 16) {
+      // two warp-wide reductions, each over one half's partial sums
+      const uint32_t lo = __reduce_xor_sync(FULL_MASK, lane < 16 ? part : 0u);
+      const uint32_t hi = __reduce_xor_sync(FULL_MASK, lane < 16 ? 0u : part);
+      part = lane < 16 ? lo : hi;
+    } else {
+#pragma unroll
+      for (int o = SEG / 2; o > 0; o >>= 1) part ^= __shfl_xor_sync(FULL_MASK, part, o, SEG);
+    }
+    const uint32_t d = part;
+    const uint32_t ld = gf.log(d);
+    const uint32_t lcoef = sel(d == 0, GF_LOG_ZERO, sel(ld >= lb, ld - lb, ld + 255u - lb));
+    const bool cond = (d != 0) & (2 * L <= (uint32_t)rr);
+    uint32_t src[NA];
+#pragma unroll
+    for (int x = 0; x < NA; x++) {
+      lam[x] ^= gf.mul_l(lcoef, lbp[x]);
+      src[x] = sel(cond, llam[x], lbp[x]);
+    }
+#pragma unroll
+    for (int x = 0; x < NA; x++) {
+      const uint32_t up = __shfl_up_sync(FULL_MASK, src[x], 1, SEG);
+      const uint32_t carry = x > 0 ? __shfl_sync(FULL_MASK, src[x > 0 ? x - 1 : 0], SEG - 1, SEG) : GF_LOG_ZERO;
+      const uint32_t nb = sl == 0 ? carry : up;
+      lbp[x] = (sl + SEG * x) < CAP ? nb : GF_LOG_ZERO;
+    }
+    lb = sel(cond, ld, lb);
+    L = sel(cond, (uint32_t)rr + 1u - L, L);
+  };
+  // phase p runs iterations [max(0, SEG p - 2), SEG (p + 1) - 2) on p + 1
+  // blocks (the last phase runs to NR)
+  auto bm_phase = [&](auto na) {
+    constexpr int NA = decltype(na)::value;
+    constexpr int R0 = NA == 1 ? 0 : cmin(NR, SEG * (NA - 1) - 2);
+    constexpr int R1 = NA == NC ? NR : cmin(NR, SEG * NA - 2);
+#pragma unroll 1
+    for (int rr = R0; rr < R1; rr++) bm_iter(na, rr);
+  };
+  static_assert(NC >= 1 && NC <= 4, "BM phases");
+  bm_phase(std::integral_constant<int, 1>{});
+  if constexpr (NC >= 2) bm_phase(std::integral_constant<int, 2>{});
+  if constexpr (NC >= 3) bm_phase(std::integral_constant<int, 3>{});
+  if constexpr (NC >= 4) bm_phase(std::integral_constant<int, 4>{});
+#pragma unroll
+  for (int x = 0; x < NC; x++) {
+    const int c = sl + SEG * x;
+    if (c < CAP) {
+      logLam[c] = (uint16_t)gf.log(lam[x]);
+      if (ALL_POS && active) dbg->lam[c] = (uint8_t)lam[x];
+    }
+  }
+  if (ALL_POS && active && sl == 0) *dbg->L = (int32_t)L;
+  __syncwarp();
+  return L;
+}
+
 template <class LV, int SEG, bool ALL_POS>
 __device__ __forceinline__ void rs_decode_seg(const GF& gf, uint32_t* rs, const uint8_t* r, int lane, bool active,
                                               uint8_t* __restrict__ m_out, const RSDebugRow* dbg) {
@@ -466,78 +562,18 @@ __device__ __forceinline__ void rs_decode_seg(const GF& gf, uint32_t* rs, const 
   }
   __syncwarp();
 
-  // Berlekamp-Massey; lane owns coefficient c = sl + SEG x.  x^m B is only
-  // ever multiplied, so it is carried in log form (lbp, 511 = zero): it
-  // shifts with the same shuffles and, when replaced by Lambda, takes the
-  // logs of Lambda already computed for the discrepancy.
-  constexpr int NC = cdiv(CAP, SEG);
-  uint32_t lam[NC], lbp[NC];
-#pragma unroll
-  for (int x = 0; x < NC; x++) {
-    const int c = sl + SEG * x;
-    lam[x] = c == 0;
-    lbp[x] = c == 1 ? 0u : GF_LOG_ZERO;  // x^m B with m = 1, B = 1
-  }
-  uint32_t lb = 0, L = 0;  // log b (b = 1), LFSR length
-#pragma unroll 1
-  for (int rr = 0; rr < NR; rr++) {
-    uint32_t llam[NC];
-    uint32_t part = 0;
-#pragma unroll
-    for (int x = 0; x < NC; x++) {
-      const int c = sl + SEG * x;  // rr - c >= -64: padding covers c > rr
-      llam[x] = gf.log(lam[x]);
-      part ^= gf.mul_l(llam[x], logS[rr - c]);
-    }
-    if constexpr (SEG == 32) {
-      part = __reduce_xor_sync(FULL_MASK, part);  // one warp-wide reduction
-    } else if constexpr (SEG == 16) {
-      // two warp-wide reductions, each over one half's partial sums
-      const uint32_t lo = __reduce_xor_sync(FULL_MASK, lane < 16 ? part : 0u);
-      const uint32_t hi = __reduce_xor_sync(FULL_MASK, lane < 16 ? 0u : part);
-      part = lane < 16 ? lo : hi;
-    } else {
-#pragma unroll
-      for (int o = SEG / 2; o > 0; o >>= 1) part ^= __shfl_xor_sync(FULL_MASK, part, o, SEG);
-    }
-    const uint32_t d = part;
-    const uint32_t ld = gf.log(d);
-    const uint32_t lcoef = sel(d == 0, GF_LOG_ZERO, sel(ld >= lb, ld - lb, ld + 255u - lb));
-    const bool cond = (d != 0) & (2 * L <= (uint32_t)rr);
-    uint32_t src[NC];
-#pragma unroll
-    for (int x = 0; x < NC; x++) {
-      lam[x] ^= gf.mul_l(lcoef, lbp[x]);
-      src[x] = sel(cond, llam[x], lbp[x]);
-    }
-#pragma unroll
-    for (int x = 0; x < NC; x++) {
-      const uint32_t up = __shfl_up_sync(FULL_MASK, src[x], 1, SEG);
-      const uint32_t carry = x > 0 ? __shfl_sync(FULL_MASK, src[x > 0 ? x - 1 : 0], SEG - 1, SEG) : GF_LOG_ZERO;
-      const uint32_t nb = sl == 0 ? carry : up;
-      lbp[x] = (sl + SEG * x) < CAP ? nb : GF_LOG_ZERO;
-    }
-    lb = sel(cond, ld, lb);
-    L = sel(cond, (uint32_t)rr + 1u - L, L);
-  }
-#pragma unroll
-  for (int x = 0; x < NC; x++) {
-    const int c = sl + SEG * x;
-    if (c < CAP) {
-      logLam[c] = (uint16_t)gf.log(lam[x]);
-      if (ALL_POS && active) dbg->lam[c] = (uint8_t)lam[x];
-    }
-  }
-  if (ALL_POS && active && sl == 0) *dbg->L = (int32_t)L;
-  __syncwarp();
+  const uint32_t L = rs_bm<LV, SEG, ALL_POS>(gf, logS, logLam, lane, active, dbg);
 
-  // Omega_k = sum_{c <= k} Lambda_c S_{k+1-c}, k < 2 delta
+  // Omega_k = sum_{c <= k} Lambda_c S_{k+1-c}, k < 2 delta.  The lanes of
+  // block x hold k < SEG (x + 1), so terms c >= SEG (x + 1) vanish for all
+  // of them: block x sums over c < min(2 delta, SEG (x + 1)).
 #pragma unroll
   for (int x = 0; x < NS; x++) {
     const int kk = sl + SEG * x;
     uint32_t om = 0;
+    const int cend = cmin(NR, SEG * (x + 1));
 #pragma unroll 4
-    for (int c = 0; c < NR; c++) {
+    for (int c = 0; c < cend; c++) {
       const int idx = kk < NR ? kk - c : -1;  // c > kk reads the log-zero padding
       om ^= gf.mul_l(logLam[c], logS[idx]);
     }
@@ -545,7 +581,10 @@ __device__ __forceinline__ void rs_decode_seg(const GF& gf, uint32_t* rs, const 
   }
   __syncwarp();
 
-  // Chien + Forney at position j: powers of alpha^{-j}
+  // Chien + Forney at position j: powers of X = alpha^{-j}.  In
+  // characteristic 2 the odd part of Lambda is X Lambda'(X), so one sum of
+  // the terms Lambda_c X^c gives both Lambda(X) (all terms) and Lambda'(X)
+  // (odd terms divided by X), and e_j = Omega(X) X / Lambda_odd(X).
   constexpr int NPOS = ALL_POS ? cdiv(n1, SEG) : cdiv(k, SEG);
   uint32_t roots = 0;
 #pragma unroll
@@ -554,20 +593,23 @@ __device__ __forceinline__ void rs_decode_seg(const GF& gf, uint32_t* rs, const 
     const int j = ALL_POS ? pos : (n1 - k) + pos;
     const bool valid = ALL_POS ? pos < n1 : pos < k;
     const uint32_t jj = valid ? (uint32_t)j : 0u;
-    const uint32_t step = jj == 0 ? 0u : 255u - jj;
-    uint32_t ec = 0, ecp = 0, lamv = 0, omv = 0, dlv = 0;
+    const uint32_t step = jj == 0 ? 0u : 255u - jj;  // log X
+    uint32_t ec = 0, lev = 0, lod = 0, omv = 0;
 #pragma unroll
     for (int c = 0; c < CAP; c++) {
-      const uint32_t llc = logLam[c];
-      lamv ^= gf.exp(min(llc + ec, GF_LOG_ZERO));
-      if (c & 1) dlv ^= gf.exp(min(llc + ecp, GF_LOG_ZERO));
+      const uint32_t t = gf.exp(min((uint32_t)logLam[c] + ec, GF_LOG_ZERO));
+      if (c & 1) lod ^= t; else lev ^= t;
       if (c < NR) omv ^= gf.exp(min((uint32_t)logOm[c] + ec, GF_LOG_ZERO));
-      ecp = ec;
       ec += step;
       ec = ec >= 255u ? ec - 255u : ec;
     }
-    const bool root = lamv == 0;
-    const uint32_t ev = sel(root, gf.div_l(gf.log(omv), gf.log(dlv)), 0u);
+    const bool root = (lev ^ lod) == 0;
+    // log(Omega X) = log Omega + log X mod 255 (Omega = 0 keeps log zero)
+    const uint32_t lom = gf.log(omv);
+    uint32_t lomx = lom + step;
+    lomx = lomx >= 255u ? lomx - 255u : lomx;
+    lomx = sel(lom >= GF_LOG_ZERO, GF_LOG_ZERO, lomx);
+    const uint32_t ev = sel(root, gf.div_l(lomx, gf.log(lod)), 0u);
     const uint32_t cwj = (uint32_t)r[jj] ^ ev;
     if (ALL_POS) {
       const uint32_t segmask = SEG == 32 ? FULL_MASK : (((1u << SEG) - 1u) << (lane - sl));
@@ -684,6 +726,135 @@ struct TeamSync {
   }
 };
 
+// S8-S9 of ONE received word by a team of T warps (tid = 32 wt + lane):
+// the syndromes split by position over the warps, Berlekamp-Massey on warp
+// 0 (the serial part), Omega by coefficient over the lanes, and Chien +
+// Forney at the k message positions with each position's sums over the
+// 2 delta + 1 coefficients split over the warps.  Partial sums meet in
+// shared memory between team barriers.  Same arithmetic, term for term, as
+// rs_decode_seg; only the order of the XORs differs.  rs: RS_TEAM_SCRATCH
+// words of shared scratch.  An inactive word is decoded but not stored.
+template <int T>
+__host__ __device__ constexpr int rs_team_scratch() { return 176 + 40 * T; }
+
+template <class LV, int T>
+__device__ __forceinline__ void rs_decode_team(const GF& gf, uint32_t* rs, const uint8_t* r, int wt, int lane,
+                                               const TeamSync& sync, bool active, uint8_t* __restrict__ m_out) {
+  constexpr int n1 = LV::n1, k = LV::k, NR = LV::NR, CAP = LV::CAP;
+  static_assert(n1 <= 96 && CAP <= 64 && k <= 32, "RS scratch sizes");
+  const int tid = wt * 32 + lane;
+  uint16_t* logr = reinterpret_cast<uint16_t*>(rs);
+  uint16_t* logS = reinterpret_cast<uint16_t*>(rs + 48) + 64;
+  uint16_t* logLam = reinterpret_cast<uint16_t*>(rs + 112);
+  uint16_t* logOm = reinterpret_cast<uint16_t*>(rs + 144);
+  uint8_t* partS = reinterpret_cast<uint8_t*>(rs + 176);           // [T][64] partial syndromes
+  uint8_t* partC = reinterpret_cast<uint8_t*>(rs + 176 + 16 * T);  // [T][3][32] partial Chien sums
+
+  for (int j = tid; j < n1; j += 32 * T) logr[j] = (uint16_t)gf.log(r[j]);
+  for (int j = tid; j < 64; j += 32 * T) logS[j - 64] = (uint16_t)GF_LOG_ZERO;
+  sync();
+
+  // partial syndromes over positions [J0, J1): lane owns i = lane + 1 + 32 s
+  constexpr int NS = cdiv(NR, 32);
+  constexpr int JW = cdiv(n1, T);
+  {
+    const int J0 = wt * JW, J1 = cmin(n1, J0 + JW);
+    uint32_t acc[NS], e[NS];
+#pragma unroll
+    for (int s = 0; s < NS; s++) {
+      acc[s] = 0;
+      e[s] = ((uint32_t)(lane + 1 + 32 * s) * (uint32_t)J0) % 255u;  // log of alpha^{i J0}
+    }
+#pragma unroll 2
+    for (int j = J0; j < J1; j++) {
+      const uint32_t lr = logr[j];
+#pragma unroll
+      for (int s = 0; s < NS; s++) {
+        acc[s] ^= gf.exp(min(lr + e[s], GF_LOG_ZERO));
+        e[s] += (uint32_t)(lane + 1 + 32 * s);
+        e[s] = e[s] >= 255u ? e[s] - 255u : e[s];
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < NS; s++) {
+      const int i = lane + 1 + 32 * s;
+      if (i <= NR) partS[wt * 64 + i - 1] = (uint8_t)acc[s];
+    }
+  }
+  sync();
+  if (wt == 0) {
+#pragma unroll
+    for (int s = 0; s < NS; s++) {
+      const int i = lane + 1 + 32 * s;
+      if (i <= NR) {
+        uint32_t S = 0;
+#pragma unroll
+        for (int w = 0; w < T; w++) S ^= partS[w * 64 + i - 1];
+        logS[i - 1] = (uint16_t)gf.log(S);
+      }
+    }
+    __syncwarp();
+    rs_bm<LV, 32, false>(gf, logS, logLam, lane, active, nullptr);
+  }
+  sync();
+
+  // Omega_kk for kk = tid < 2 delta: warp wt holds kk < 32 (wt + 1), so it
+  // sums over c < min(2 delta, 32 (wt + 1)); warps past 2 delta idle
+  if (32 * wt < NR) {
+    const int kk = tid;
+    const int cend = cmin(NR, 32 * (wt + 1));
+    uint32_t om = 0;
+#pragma unroll 4
+    for (int c = 0; c < cend; c++) {
+      const int idx = kk < NR ? kk - c : -1;  // c > kk reads the log-zero padding
+      om ^= gf.mul_l(logLam[c], logS[idx]);
+    }
+    if (kk < NR) logOm[kk] = (uint16_t)gf.log(om);
+  }
+  sync();
+
+  // Chien + Forney: lane = message position; warp wt sums the terms
+  // c in [C0, C1) of Lambda_even, Lambda_odd and Omega at X = alpha^{-j}
+  constexpr int CW = cdiv(CAP, T);
+  const int pos = lane;
+  const uint32_t jj = (uint32_t)((n1 - k) + (pos < k ? pos : 0));
+  const uint32_t step = jj == 0 ? 0u : 255u - jj;  // log X
+  {
+    const int C0 = wt * CW, C1 = cmin(CAP, C0 + CW);
+    uint32_t ec = (step * (uint32_t)C0) % 255u;
+    uint32_t lev = 0, lod = 0, omv = 0;
+#pragma unroll 4
+    for (int c = C0; c < C1; c++) {
+      const uint32_t t = gf.exp(min((uint32_t)logLam[c] + ec, GF_LOG_ZERO));
+      lod ^= (c & 1) ? t : 0u;
+      lev ^= (c & 1) ? 0u : t;
+      if (c < NR) omv ^= gf.exp(min((uint32_t)logOm[c] + ec, GF_LOG_ZERO));
+      ec += step;
+      ec = ec >= 255u ? ec - 255u : ec;
+    }
+    partC[(wt * 3 + 0) * 32 + lane] = (uint8_t)lev;
+    partC[(wt * 3 + 1) * 32 + lane] = (uint8_t)lod;
+    partC[(wt * 3 + 2) * 32 + lane] = (uint8_t)omv;
+  }
+  sync();
+  if (wt == 0) {
+    uint32_t lev = 0, lod = 0, omv = 0;
+#pragma unroll
+    for (int w = 0; w < T; w++) {
+      lev ^= partC[(w * 3 + 0) * 32 + lane];
+      lod ^= partC[(w * 3 + 1) * 32 + lane];
+      omv ^= partC[(w * 3 + 2) * 32 + lane];
+    }
+    const bool root = (lev ^ lod) == 0;
+    const uint32_t lom = gf.log(omv);
+    uint32_t lomx = lom + step;
+    lomx = lomx >= 255u ? lomx - 255u : lomx;
+    lomx = sel(lom >= GF_LOG_ZERO, GF_LOG_ZERO, lomx);
+    const uint32_t ev = sel(root, gf.div_l(lomx, gf.log(lod)), 0u);
+    if (pos < k && active) m_out[pos] = (uint8_t)((uint32_t)r[jj] ^ ev);
+  }
+}
+
 template <class LV, int T = 2, int NI = 2>
 struct Team {
   static constexpr int WPT2 = odd_at_least(cdiv(LV::W_v32, 32 * T));
@@ -691,7 +862,7 @@ struct Team {
   static constexpr int RB = cdiv(LV::n1, 4) * 4;  // bytes per stored RM word
   static constexpr int WORDS = round_up(U2W + LV::WP + NI * (RB / 4), 4);  // shared words per team
   static_assert(NI >= 1 && NI <= T, "one RS word per warp at most");
-  static_assert(NI * RS_SCRATCH <= U2W, "the RS scratches fit in u2");
+  static_assert(NI * RS_SCRATCH <= U2W && rs_team_scratch<T>() <= U2W, "the RS scratches fit in u2");
   static_assert(U2W % 4 == 0 && LV::WP % 4 == 0 && WORDS % 4 == 0, "16-byte alignment");
 };
 
@@ -740,7 +911,11 @@ __device__ __forceinline__ void decrypt_team(const GF& gf, uint32_t* ws, int wt,
 #pragma unroll 1
   for (int g = 0; g < NI; g++)
     if (rows(g, u, v, y, m)) product_rm_team<LV, MASKED, T>(ws, tid, sync, u, v, y, rbuf + g * TT::RB);
-  if (wt < NI) {
+  if constexpr (NI == 1 && T > 1) {
+    // one ciphertext per turn: the whole team shares its RS stage
+    const bool act = rows(0, u, v, y, m);
+    rs_decode_team<LV, T>(gf, ws, rbuf, wt, lane, sync, act, m);
+  } else if (wt < NI) {
     const bool act = rows(wt, u, v, y, m);
     rs_decode_seg<LV, 32, false>(gf, ws + wt * RS_SCRATCH, rbuf + wt * TT::RB, lane, act, m, nullptr);
   }

@@ -25,6 +25,7 @@ template <> struct LevelConst<5> {
 __host__ __device__ constexpr int cdiv(int a, int b) { return (a + b - 1) / b; }
 __host__ __device__ constexpr int odd_at_least(int x) { return x | 1; }
 __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
+__host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
 __host__ __device__ constexpr int round_up(int a, int b) { return cdiv(a, b) * b; }
 
 // Layout in HBM (bit i of a vector = bit i%64 of 64-bit word i/64):
