@@ -838,6 +838,7 @@ def bench_serving(ctx, full):
             "p99_us": float(np.percentile(l_us, 99)) if l_us.size else None,
             "p999_us": float(np.percentile(l_us, 99.9)) if l_us.size else None,
             "batches": int(stats["batches"]), "mean_batch": stats["mean_batch"], "correct": good,
+            "transfer": "in place (kernels read the pinned host ring)" if stats["in_place"] else "copy engines",
             "clocks": {"before": clk_before, "after": clk_after}})
     top = points[-1]
     line = {

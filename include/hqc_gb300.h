@@ -363,10 +363,26 @@ int hqc_plan_destroy(hqc_plan_t* plan);
  * its k result bytes at m_out + ring->m_off[j] (host; NULL to drop results;
  * a later request on the same entry overwrites them).
  * One host thread admits arrived requests into batches for `streams` CUDA
- * streams while a batch fits that stream's budget_bytes / streams of
- * device memory and max_batch requests; each batch is one copy in, one
- * persistent kernel per level present, one copy out.  Batches run
+ * streams while a batch fits that stream's budget_bytes / streams (of
+ * request bytes in flight) and max_batch requests.  Batches run
  * concurrently, and new arrivals are admitted whenever a stream frees up.
+ * A batch of at most 512 requests is one launch of the latency form, a
+ * larger one one persistent kernel per level present.  How the request
+ * bytes reach the GPU (cfg->transfer):
+ *   1  copy mode: one H2D copy of the batch's ring range into device
+ *      memory, the kernels, one D2H copy of the m bytes;
+ *   2  in place: the kernels read the batch's u and v rows straight from
+ *      the host ring and write m into mapped pinned memory, so no copy
+ *      engine is on the request path.  Needs a ring the device can address
+ *      (mapped pinned memory, or any host memory on a device that uses the
+ *      host's page tables, such as GB300 with its C2C link), 16-byte
+ *      aligned, with even word offsets; HQC_EINVAL otherwise;
+ *   0  in place when possible, else copy mode (stats->in_place says which).
+ * On GB300 the copy engines' H2D rate was measured to collapse from ~192 to
+ * ~8 GB/s for tens of milliseconds about twice a second, while SM loads
+ * from the same memory hold ~182 GB/s, which is why 0 prefers in place.
+ * word_off and m_off must start at 0 and never decrease (HQC_EINVAL
+ * otherwise).
  * A request that arrives while max_queue requests wait is rejected.
  * Outputs per request: status[i] (HQC_STATUS_*) and latency_ns[i] =
  * completion time - arrival time (-1 unless DONE).  The call allocates the
@@ -391,6 +407,7 @@ typedef struct hqc_serve_cfg_s {
   int64_t max_queue;      /* waiting requests at most */
   int32_t warps_per_cta;  /* launch shape of the per-level kernels (0 = default) */
   int32_t stall_ms;       /* per-batch completion limit in ms (0 = 10,000; < 0 is an error) */
+  int32_t transfer;       /* 0 in place when possible, 1 copy engines, 2 in place (see above) */
 } hqc_serve_cfg_t;
 typedef struct hqc_serve_ring_s {
   int64_t period;
@@ -405,6 +422,7 @@ typedef struct hqc_serve_stats_s {
   double mean_batch;
   int64_t wall_ns;          /* start to last completion */
   int64_t items_per_slot;   /* batch capacity the budget allows */
+  int64_t in_place;         /* 1 if the kernels read the ring in place, 0 if copied */
 } hqc_serve_stats_t;
 int hqc_serve_run(const hqc_serve_cfg_t* cfg, const hqc_keyset_t* const keys[3], const hqc_serve_ring_t* ring,
                   int64_t count, const int64_t* arrival_ns, int32_t* status, int64_t* latency_ns, uint8_t* m_out,

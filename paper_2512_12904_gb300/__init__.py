@@ -499,7 +499,8 @@ def hqc_plan_create_mixed(items, arena, keys, m_arena, autotune=True, stream=Non
 
 class _ServeCfg(ctypes.Structure):
     _fields_ = [("streams", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("budget_bytes", ctypes.c_int64),
-                ("max_queue", ctypes.c_int64), ("warps_per_cta", ctypes.c_int32), ("stall_ms", ctypes.c_int32)]
+                ("max_queue", ctypes.c_int64), ("warps_per_cta", ctypes.c_int32), ("stall_ms", ctypes.c_int32),
+                ("transfer", ctypes.c_int32)]
 
 
 class _ServeRing(ctypes.Structure):
@@ -511,7 +512,7 @@ class _ServeStats(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_int64), ("rejected_queue", ctypes.c_int64),
                 ("rejected_invalid", ctypes.c_int64), ("rejected_size", ctypes.c_int64),
                 ("batches", ctypes.c_int64), ("mean_batch", ctypes.c_double), ("wall_ns", ctypes.c_int64),
-                ("items_per_slot", ctypes.c_int64)]
+                ("items_per_slot", ctypes.c_int64), ("in_place", ctypes.c_int64)]
 
 
 SERVE_STATUS = {0: "done", 1: "queued", 2: "running", 3: "rejected", 4: "invalid", 5: "too_large"}
@@ -519,13 +520,14 @@ SERVE_STATUS = {0: "done", 1: "queued", 2: "running", 3: "rejected", 4: "invalid
 
 def hqc_serve_run(keys, ring_level, ring_key, ring_word_off, ring_words, ring_m_off, arrival_ns, streams=4,
                   max_batch=8192, budget_bytes=256 << 20, max_queue=1 << 20, warps_per_cta=0, want_m=True,
-                  stall_ms=0):
+                  stall_ms=0, transfer=0):
     """Run the continuous-batching loop over a request trace (hqc_serve_run).
 
     ring_words must be a PINNED uint64/int64 CPU tensor; the other ring
     arrays are numpy.  Returns (status, latency_ns, m_out or None, stats).
     A batch incomplete stall_ms after its launch (0: 10 s) raises HqcError
-    with code HQC_ETIMEOUT."""
+    with code HQC_ETIMEOUT.  transfer: 0 in place when possible, 1 copy
+    engines, 2 in place (the kernels read the ring from host memory)."""
     torch = _torch()
     if not isinstance(ring_words, torch.Tensor) or ring_words.is_cuda or not ring_words.is_pinned():
         raise ValueError("ring_words must be a pinned CPU tensor")
@@ -543,7 +545,7 @@ def hqc_serve_run(keys, ring_level, ring_key, ring_word_off, ring_words, ring_m_
     status = np.zeros(cnt, np.int32)
     lat = np.zeros(cnt, np.int64)
     m_out = np.zeros(int(moff[-1]), np.uint8) if want_m else None
-    cfg = _ServeCfg(streams, max_batch, budget_bytes, max_queue, warps_per_cta, stall_ms)
+    cfg = _ServeCfg(streams, max_batch, budget_bytes, max_queue, warps_per_cta, stall_ms, transfer)
     ring = _ServeRing(period, lvl.ctypes.data_as(ctypes.c_void_p), key.ctypes.data_as(ctypes.c_void_p),
                       woff.ctypes.data_as(ctypes.c_void_p), ctypes.c_void_p(ring_words.data_ptr()),
                       moff.ctypes.data_as(ctypes.c_void_p))

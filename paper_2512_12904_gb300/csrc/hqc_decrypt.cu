@@ -348,15 +348,17 @@ __global__ void __launch_bounds__(STAGE_THREADS) k_stage_product(DecArgs a, uint
   }
   load_supports<LV::n, LV::w>(ws + LV::U2W, yrow, lane);
   build_doubled<LV::n, LV::W_u_pitch, LV::U2W>(ws, a.u + it * LV::W_u_pitch, lane);
-  uint32_t acc[LV::WPT];
-  rot_xor_product<LV::WPT, LV::w, !KEYED>(ws, ws + LV::U2W, lane, acc);
+  using PS = ProductStrips<LEVEL>;
+  const int w0 = PS::start(lane), wn = PS::len(lane);
+  uint32_t acc[PS::MAXLEN];
+  rot_xor_product<PS::MAXLEN, LV::w, !KEYED>(ws, ws + LV::U2W, w0, acc);
   const uint32_t* v32 = reinterpret_cast<const uint32_t*>(a.v + it * LV::W_v);
   uint32_t* w32 = reinterpret_cast<uint32_t*>(w_out + it * LV::W_v);
   uint32_t* t32 = WITH_T ? reinterpret_cast<uint32_t*>(t_out + it * LV::W_v) : nullptr;
 #pragma unroll
-  for (int k = 0; k < LV::WPT; k++) {
-    const int i = lane * LV::WPT + k;
-    if (i < LV::W_v32) {
+  for (int k = 0; k < PS::MAXLEN; k++) {
+    const int i = w0 + k;
+    if (k < wn && i < LV::W_v32) {
       if (WITH_T) t32[i] = acc[k];
       w32[i] = acc[k] ^ v32[i];
     }

@@ -184,11 +184,11 @@ __device__ __forceinline__ void load_supports(uint32_t* sup, const uint32_t* __r
 // positions, so the strips cover the product with odd WPT and no tail.)
 // ---------------------------------------------------------------------------
 template <int WPT, int W, bool MASKED>
-__device__ __forceinline__ void rot_xor_product(const uint32_t* u2, const uint32_t* sup, int lane,
+__device__ __forceinline__ void rot_xor_product(const uint32_t* u2, const uint32_t* sup, int w0,
                                                 uint32_t (&acc)[WPT]) {
 #pragma unroll
   for (int k = 0; k < WPT; k++) acc[k] = 0;
-  const char* base = reinterpret_cast<const char*>(u2 + lane * WPT);
+  const char* base = reinterpret_cast<const char*>(u2 + w0);
   if (MASKED) {
 #pragma unroll 1
     for (int t = 0; t < W; t++) {
@@ -635,25 +635,27 @@ template <class LV, bool MASKED>
 __device__ __forceinline__ void product_rm_one(uint32_t* ws, int lane, const uint64_t* __restrict__ urow,
                                                const uint64_t* __restrict__ vrow, const uint32_t* __restrict__ yrow,
                                                uint8_t* r_out) {
-  constexpr int WPT = LV::WPT, W_v32 = LV::W_v32;
+  using PS = ProductStrips<LV::level>;
+  constexpr int WPT = PS::MAXLEN, W_v32 = LV::W_v32;
   uint32_t* u2 = ws;
   uint32_t* sup = ws + LV::U2W;
   load_supports<LV::n, LV::w>(sup, yrow, lane);
   build_doubled<LV::n, LV::W_u_pitch, LV::U2W>(u2, urow, lane);
+  const int w0 = PS::start(lane), wn = PS::len(lane);
   uint32_t acc[WPT];
-  rot_xor_product<WPT, LV::w, MASKED>(u2, sup, lane, acc);
+  rot_xor_product<WPT, LV::w, MASKED>(u2, sup, w0, acc);
   // S4: w = v + t, truncated (only the first n1*n2 bits were computed)
   const uint32_t* v32 = reinterpret_cast<const uint32_t*>(vrow);
 #pragma unroll
   for (int k = 0; k < WPT; k++) {
-    const int i = lane * WPT + k;
-    if (i < W_v32) acc[k] ^= __ldcs(v32 + i);
+    const int i = w0 + k;
+    if (k < wn && i < W_v32) acc[k] ^= __ldcs(v32 + i);
   }
   __syncwarp();
 #pragma unroll
   for (int k = 0; k < WPT; k++) {
-    const int i = lane * WPT + k;
-    if (i < W_v32) u2[i] = acc[k];
+    const int i = w0 + k;
+    if (k < wn && i < W_v32) u2[i] = acc[k];
   }
   __syncwarp();
   rm_decode_warp<LV>(u2, r_out, lane);
@@ -878,7 +880,7 @@ __device__ __forceinline__ void product_rm_team(uint32_t* ws, int tid, const Tea
   load_supports<LV::n, LV::w, 32 * T>(sup, yrow, tid);
   build_doubled<LV::n, LV::W_u_pitch, TT::U2W, 32 * T>(u2, urow, tid, sync);
   uint32_t acc[WPT];
-  rot_xor_product<WPT, LV::w, MASKED>(u2, sup, tid, acc);
+  rot_xor_product<WPT, LV::w, MASKED>(u2, sup, tid * WPT, acc);
   const uint32_t* v32 = reinterpret_cast<const uint32_t*>(vrow);
 #pragma unroll
   for (int k = 0; k < WPT; k++) {

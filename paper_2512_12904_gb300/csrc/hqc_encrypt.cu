@@ -103,7 +103,7 @@ __device__ __forceinline__ void full_product_to_smem(uint32_t* u2, uint32_t* sup
   load_supports<LV::n, W>(sup, supp, lane);
   build_doubled<LV::n, LV::W_u_pitch, LV::U2W_FULL>(u2, dense, lane);
   uint32_t acc[WPT];
-  rot_xor_product<WPT, W, MASKED>(u2, sup, lane, acc);
+  rot_xor_product<WPT, W, MASKED>(u2, sup, lane * WPT, acc);
   __syncwarp();
 #pragma unroll
   for (int k = 0; k < WPT; k++) {
@@ -117,14 +117,16 @@ __device__ __forceinline__ void full_product_to_smem(uint32_t* u2, uint32_t* sup
 // u2[0, W_v32).
 template <class LV, int W, bool MASKED>
 __device__ __forceinline__ void truncated_product_to_smem(uint32_t* u2, const uint32_t* sup, int lane) {
-  constexpr int WPT = LV::WPT;
+  using PS = ProductStrips<LV::level>;
+  constexpr int WPT = PS::MAXLEN;
+  const int w0 = PS::start(lane), wn = PS::len(lane);
   uint32_t acc[WPT];
-  rot_xor_product<WPT, W, MASKED>(u2, sup, lane, acc);
+  rot_xor_product<WPT, W, MASKED>(u2, sup, w0, acc);
   __syncwarp();
 #pragma unroll
   for (int k = 0; k < WPT; k++) {
-    const int i = lane * WPT + k;
-    if (i < LV::W_v32) u2[i] = acc[k];
+    const int i = w0 + k;
+    if (k < wn && i < LV::W_v32) u2[i] = acc[k];
   }
   __syncwarp();
 }
@@ -354,7 +356,7 @@ __global__ void __launch_bounds__(EncTeamBound<LEVEL>::threads, 1)
     load_supports<LV::n, LV::wr, 64>(sup, r2 + it * LV::wr, tid);
     build_doubled<LV::n, LV::W_u_pitch, T::U2W, 64, TeamSync>(u2, h + key * LV::W_u_pitch, tid, sync);
     uint32_t acc[WPT];
-    rot_xor_product<WPT, LV::wr, !VALID>(u2, sup, tid, acc);
+    rot_xor_product<WPT, LV::wr, !VALID>(u2, sup, tid * WPT, acc);
     sync();
 #pragma unroll
     for (int kk = 0; kk < WPT; kk++) {
@@ -379,7 +381,7 @@ __global__ void __launch_bounds__(EncTeamBound<LEVEL>::threads, 1)
     sync();
     // s * r2, truncated to n1*n2 bits, plus e
     build_doubled<LV::n, LV::W_u_pitch, T::U2W, 64, TeamSync>(u2, s + key * LV::W_u_pitch, tid, sync);
-    rot_xor_product<WPT, LV::wr, !VALID>(u2, sup, tid, acc);
+    rot_xor_product<WPT, LV::wr, !VALID>(u2, sup, tid * WPT, acc);
     sync();
 #pragma unroll
     for (int kk = 0; kk < WPT; kk++) {

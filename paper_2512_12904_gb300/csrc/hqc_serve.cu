@@ -6,14 +6,25 @@
 //   * admits arrived requests into a batch for any free stream, while the
 //     batch fits that stream's share of the device-memory budget and
 //     max_batch; arrivals beyond max_queue waiting requests are rejected;
-//   * per batch: one H2D copy of the contiguous ring range, the item list
-//     grouped by level, one persistent kernel per level present, one D2H
+//   * per batch: the item list grouped by level, then either (in-place
+//     mode) the kernels read the batch's ring range straight from host
+//     memory and write m into mapped pinned memory -- one launch (small
+//     batch) or one persistent kernel per level, then an event; or (copy
+//     mode) one H2D copy of the contiguous ring range, the kernels, one D2H
 //     copy of the m bytes, an event;
 //   * polls the events; a completed batch frees its memory and stamps every
 //     request's completion time.
 // So requests that arrive while batches run on the GPU are admitted as soon
 // as a stream and its memory free up, and up to `streams` batches overlap
 // on the device.  Keys stay resident (registered keysets).
+//
+// Why in-place reads: measured on GB300, DMA copies from pinned host memory
+// run at ~192 GB/s but collapse to ~8 GB/s for tens of milliseconds about
+// twice a second, while loads that the SMs issue to the same host memory
+// over the C2C link hold ~182 GB/s throughout.  A batch whose upload falls
+// into such a window waits milliseconds, and at high load the backlog it
+// leaves sets the tail latency.  Reading the ring from the kernels keeps
+// the copy engines off the request path altogether.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -43,11 +54,13 @@ int sfail(int code, const char* fmt, ...) {
 struct Slot {
   cudaStream_t st = nullptr;
   cudaEvent_t ev = nullptr;
-  uint64_t* d_words = nullptr;       // ring bytes of the batch
-  uint8_t* d_m = nullptr;            // m bytes of the batch
-  hqc::MixedItem* d_items = nullptr; // grouped by level
-  hqc::MixedItem* h_items = nullptr; // pinned
-  uint8_t* h_m = nullptr;            // pinned
+  uint64_t* d_words = nullptr;       // ring bytes of the batch (copy mode)
+  uint8_t* d_m = nullptr;            // m bytes of the batch (copy mode)
+  hqc::MixedItem* d_items = nullptr; // grouped by level (copy mode)
+  hqc::MixedItem* h_items = nullptr; // pinned, mapped
+  uint8_t* h_m = nullptr;            // pinned, mapped
+  const hqc::MixedItem* k_items = nullptr;  // what the kernels read: d_items, or h_items' device address
+  uint8_t* k_m = nullptr;                   // what the kernels write: d_m, or h_m's device address
   int64_t words_cap = 0, m_cap = 0;
   bool busy = false;
   int64_t t_launch = 0;              // host time the batch was issued
@@ -78,11 +91,44 @@ extern "C" int hqc_serve_run(const hqc_serve_cfg_t* cfg, const hqc_keyset_t* con
   if (ring->period < 1 || !ring->level || !ring->key || !ring->word_off || !ring->words || !ring->m_off)
     return sfail(HQC_EINVAL, "ring is incomplete");
   if (count < 0) return sfail(HQC_EINVAL, "count must be >= 0");
+  if (cfg->transfer < 0 || cfg->transfer > 2) return sfail(HQC_EINVAL, "transfer must be 0, 1 or 2");
   const int lv[3] = {1, 3, 5};
   hqc_params_t prm[3];
   for (int i = 0; i < 3; i++) hqc_get_params(lv[i], &prm[i]);
   for (int i = 0; i < 3; i++)
     if (keys[i] && keys[i]->level != lv[i]) return sfail(HQC_EINVAL, "keys[%d] is not a level-%d keyset", i, lv[i]);
+  // every ring entry's rows lie inside [0, word_off[period]) and its m bytes
+  // inside [0, m_off[period]): in in-place mode the kernels read the ring
+  // at these offsets, so they are checked once here
+  if (ring->word_off[0] != 0 || ring->m_off[0] != 0) return sfail(HQC_EINVAL, "ring offsets must start at 0");
+  bool even = ((uintptr_t)ring->words % 16) == 0;  // every row 16-byte aligned in host memory
+  for (int64_t j = 0; j < ring->period; j++) {
+    if (ring->word_off[j + 1] < ring->word_off[j] || ring->m_off[j + 1] < ring->m_off[j])
+      return sfail(HQC_EINVAL, "ring offsets must be non-decreasing (entry %lld)", (long long)j);
+    even = even && (ring->word_off[j] & 1) == 0;
+  }
+  // In-place reads need a device address for the caller's ring -- the mapped
+  // address of pinned memory, or the host address itself on a device that
+  // reads pageable host memory through the host's page tables -- and rows
+  // on 16-byte boundaries (the kernels load u with 16-byte vectors).
+  const uint64_t* ring_dev = nullptr;
+  if (cfg->transfer == 2 && !even)
+    return sfail(HQC_EINVAL, "transfer 2 needs a 16-byte aligned ring with even word offsets");
+  if (cfg->transfer != 1 && even) {
+    void* p = nullptr;
+    if (cudaHostGetDevicePointer(&p, const_cast<uint64_t*>(ring->words), 0) == cudaSuccess) {
+      ring_dev = static_cast<const uint64_t*>(p);
+    } else {
+      cudaGetLastError();
+      int dev = 0, pageable = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccessUsesHostPageTables, dev);
+      if (pageable) ring_dev = ring->words;
+    }
+    if (!ring_dev && cfg->transfer == 2)
+      return sfail(HQC_EINVAL, "transfer 2: the device cannot read the ring in place (not mapped, no host page tables)");
+  }
+  const bool in_place = ring_dev != nullptr;
 
   // per-slot device memory: an even split of the budget between words,
   // m bytes and item records in proportion to the largest request
@@ -115,11 +161,28 @@ extern "C" int hqc_serve_run(const hqc_serve_cfg_t* cfg, const hqc_keyset_t* con
     }
     if ((e = cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming)) != cudaSuccess ||
-        (e = cudaMalloc(&s.d_words, s.words_cap * 8)) != cudaSuccess || (e = cudaMalloc(&s.d_m, s.m_cap)) != cudaSuccess ||
-        (e = cudaMalloc(&s.d_items, item_bytes)) != cudaSuccess ||
-        (e = cudaMallocHost(&s.h_items, item_bytes)) != cudaSuccess || (e = cudaMallocHost(&s.h_m, s.m_cap)) != cudaSuccess) {
+        (e = cudaHostAlloc(&s.h_items, item_bytes, cudaHostAllocMapped)) != cudaSuccess ||
+        (e = cudaHostAlloc(&s.h_m, s.m_cap, cudaHostAllocMapped)) != cudaSuccess) {
       cleanup();
       return sfail(HQC_ENOMEM, "serving buffers: %s", cudaGetErrorString(e));
+    }
+    if (in_place) {
+      void *pi = nullptr, *pm = nullptr;
+      if ((e = cudaHostGetDevicePointer(&pi, s.h_items, 0)) != cudaSuccess ||
+          (e = cudaHostGetDevicePointer(&pm, s.h_m, 0)) != cudaSuccess) {
+        cleanup();
+        return sfail(HQC_ECUDA, "mapping the serving buffers: %s", cudaGetErrorString(e));
+      }
+      s.k_items = static_cast<const hqc::MixedItem*>(pi);
+      s.k_m = static_cast<uint8_t*>(pm);
+    } else {
+      if ((e = cudaMalloc(&s.d_words, s.words_cap * 8)) != cudaSuccess ||
+          (e = cudaMalloc(&s.d_m, s.m_cap)) != cudaSuccess || (e = cudaMalloc(&s.d_items, item_bytes)) != cudaSuccess) {
+        cleanup();
+        return sfail(HQC_ENOMEM, "serving buffers: %s", cudaGetErrorString(e));
+      }
+      s.k_items = s.d_items;
+      s.k_m = s.d_m;
     }
   }
   hqc::LaunchCfg lcfg;
@@ -156,6 +219,7 @@ extern "C" int hqc_serve_run(const hqc_serve_cfg_t* cfg, const hqc_keyset_t* con
     stats->mean_batch = batches ? (double)batch_items / (double)batches : 0.0;
     stats->wall_ns = t_last - t0;
     stats->items_per_slot = max_items;
+    stats->in_place = in_place ? 1 : 0;
   };
   // a batch past its limit: wait a bounded time for everything in flight,
   // free the buffers if it all finished, and report the stall
@@ -297,24 +361,30 @@ extern "C" int hqc_serve_run(const hqc_serve_cfg_t* cfg, const hqc_keyset_t* con
         nitems += (int64_t)lists[li].size();
       }
       const int64_t wbytes = words * 8;  // up to the last admitted request (<= words_cap)
-      e = cudaMemcpyAsync(s.d_words, ring->words + ring->word_off[base], (size_t)wbytes, cudaMemcpyHostToDevice, s.st);
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(s.d_items, s.h_items, (size_t)nitems * sizeof(hqc::MixedItem), cudaMemcpyHostToDevice,
+      const uint64_t* arena = s.d_words;
+      if (in_place) {
+        arena = ring_dev + ring->word_off[base];
+      } else {
+        e = cudaMemcpyAsync(s.d_words, ring->words + ring->word_off[base], (size_t)wbytes, cudaMemcpyHostToDevice,
                             s.st);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(s.d_items, s.h_items, (size_t)nitems * sizeof(hqc::MixedItem), cudaMemcpyHostToDevice,
+                              s.st);
+      }
       if (nitems <= kSmallBatch && e == cudaSuccess) {
         // a small batch: one launch of the latency form of the mixed kernel
         // (a team of warps per item), so its items spread over every SM and
         // the slowest one's chain is split over its team
         hqc::MixedArgs a;
         a.count = nitems;
-        a.items = s.d_items;
-        a.arena = s.d_words;
+        a.items = s.k_items;
+        a.arena = arena;
         a.arena_words = wbytes / 8;
         for (int k = 0; k < 3; k++) {
           a.keys[k] = keys[k] ? keys[k]->d_table : nullptr;
           a.nkeys[k] = keys[k] ? keys[k]->nkeys : 0;
         }
-        a.m = s.d_m;
+        a.m = s.k_m;
         a.m_bytes = mbytes;
         e = hqc::launch_mixed_latency(a, s.st);
         for (auto& l : lists) l.clear();
@@ -323,18 +393,19 @@ extern "C" int hqc_serve_run(const hqc_serve_cfg_t* cfg, const hqc_keyset_t* con
         if (lists[li].empty()) continue;
         hqc::MixedArgs a;
         a.count = (int64_t)lists[li].size();
-        a.items = s.d_items + start[li];
-        a.arena = s.d_words;
+        a.items = s.k_items + start[li];
+        a.arena = arena;
         a.arena_words = wbytes / 8;
         for (int k = 0; k < 3; k++) {
           a.keys[k] = keys[k] ? keys[k]->d_table : nullptr;
           a.nkeys[k] = keys[k] ? keys[k]->nkeys : 0;
         }
-        a.m = s.d_m;
+        a.m = s.k_m;
         a.m_bytes = mbytes;
         e = hqc::launch_items(lv[li], a, 0, s.st, lcfg);
       }
-      if (e == cudaSuccess) e = cudaMemcpyAsync(s.h_m, s.d_m, (size_t)mbytes, cudaMemcpyDeviceToHost, s.st);
+      if (e == cudaSuccess && !in_place)
+        e = cudaMemcpyAsync(s.h_m, s.d_m, (size_t)mbytes, cudaMemcpyDeviceToHost, s.st);
       if (e == cudaSuccess) e = cudaEventRecord(s.ev, s.st);
       if (e != cudaSuccess) {
         cleanup();

@@ -179,7 +179,7 @@ def test_serving_argument_checks_without_a_gpu():
                                  one64.ctypes.data_as(ctypes.c_void_p), st.ctypes.data_as(ctypes.c_void_p),
                                  lat.ctypes.data_as(ctypes.c_void_p), None, None)
 
-    assert ctypes.sizeof(hqc._ServeCfg) == 32
+    assert ctypes.sizeof(hqc._ServeCfg) == 40  # 7 fields, padded to 8 bytes
     assert call(hqc._ServeCfg(1, 1, 1 << 20, 1, 0, -1)) == hqc.HQC_EINVAL
     assert b"stall_ms" in lib.hqc_last_error()
     assert call(hqc._ServeCfg(0, 1, 1 << 20, 1, 0, 0)) == hqc.HQC_EINVAL
@@ -200,3 +200,34 @@ def test_noalloc_limit_is_the_largest_count_whose_workspace_fits(level, limit):
     assert rc == -1
     msg = lib.hqc_last_error()
     assert b"exceeds the static scratch" in msg and str(limit).encode() in msg
+
+
+def test_serving_rejects_rings_whose_offsets_decrease_without_a_gpu():
+    """The serving loop checks the ring's offsets on the host before it
+    touches the device: offsets must start at 0 and never decrease, and
+    in-place reads (transfer 2) need even word offsets."""
+    lib = hqc.load()
+    level = np.array([1, 1], np.int32)
+    key = np.zeros(2, np.int32)
+    words = np.zeros(2000, np.uint64)
+    arr = np.zeros(2, np.int64)
+    st = np.zeros(2, np.int32)
+    lat = np.zeros(2, np.int64)
+    P = ctypes.c_void_p
+
+    def call(woff, moff, transfer=0):
+        cfg = hqc._ServeCfg(1, 8, 1 << 20, 16, 0, 0, transfer)
+        ring = hqc._ServeRing(2, level.ctypes.data_as(P), key.ctypes.data_as(P), woff.ctypes.data_as(P),
+                              words.ctypes.data_as(P), moff.ctypes.data_as(P))
+        keys = (P * 3)(None, None, None)
+        stats = hqc._ServeStats()
+        return lib.hqc_serve_run(ctypes.byref(cfg), keys, ctypes.byref(ring), 2, arr.ctypes.data_as(P),
+                                 st.ctypes.data_as(P), lat.ctypes.data_as(P), None, ctypes.byref(stats))
+
+    assert call(np.array([0, 554, 500], np.int64), np.array([0, 16, 32], np.int64)) == -1
+    assert b"non-decreasing" in lib.hqc_last_error()
+    assert call(np.array([0, 554, 1108], np.int64), np.array([0, 16, 8], np.int64)) == -1
+    assert call(np.array([1, 554, 1108], np.int64), np.array([0, 16, 32], np.int64)) == -1
+    assert call(np.array([0, 555, 1109], np.int64), np.array([0, 16, 32], np.int64), transfer=2) == -1
+    assert b"even word offsets" in lib.hqc_last_error()
+    assert call(np.array([0, 554, 1108], np.int64), np.array([0, 16, 32], np.int64), transfer=3) == -1

@@ -21,16 +21,24 @@ def hqc():
     return lib
 
 
-def _median_ms(fn, reps=9):
-    ts = []
-    for _ in range(reps):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        fn()
-        b.record()
-        torch.cuda.synchronize()
-        ts.append(a.elapsed_time(b))
-    return float(np.median(ts))
+def _interleaved_medians(fns, rounds=9):
+    """Median time of each call in fns (name -> callable), measured round
+    robin: every round times each call once, in a fixed cyclic order, so a
+    drift of the GPU clock or the cache state during the measurement falls
+    on all of them alike instead of on whichever ran first."""
+    for fn in fns.values():
+        for _ in range(3):
+            fn()
+    ts = {name: [] for name in fns}
+    for _ in range(rounds):
+        for name, fn in fns.items():
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts[name].append(a.elapsed_time(b))
+    return {name: float(np.median(t)) for name, t in ts.items()}
 
 
 @pytest.mark.parametrize("level", [1, 5])
@@ -45,16 +53,15 @@ def test_fused_time_does_not_depend_on_the_data(hqc, level):
         "garbage": (synth.words(wl.u.size, tag=42).reshape(wl.u.shape),
                     synth.words(wl.v.size, tag=43).reshape(wl.v.shape)),
     }
-    times = {}
+    fns, outs = {}, {}
     for name, (u, v) in batches.items():
         ud = torch.from_numpy(np.ascontiguousarray(u).view(np.int64)).cuda()
         vd = torch.from_numpy(np.ascontiguousarray(v).view(np.int64)).cuda()
         m = torch.empty((cnt, wl.P.k), dtype=torch.uint8, device="cuda")
-        for _ in range(3):
-            hqc.hqc_decrypt_batch_keyed(level, ud, vd, keys, kidx, m)
-        times[name] = _median_ms(lambda: hqc.hqc_decrypt_batch_keyed(level, ud, vd, keys, kidx, m))
-        if name == "honest":
-            assert (m.cpu().numpy() == wl.m).all()
+        outs[name] = m
+        fns[name] = (lambda ud=ud, vd=vd, m=m: hqc.hqc_decrypt_batch_keyed(level, ud, vd, keys, kidx, m))
+    times = _interleaved_medians(fns)
+    assert (outs["honest"].cpu().numpy() == wl.m).all()
     keys.free()
     spread = max(times.values()) / min(times.values())
     assert spread < 1.05, times
@@ -85,14 +92,13 @@ def test_decapsulation_time_does_not_depend_on_acceptance(hqc, level):
     g_v = torch.from_numpy(synth.words(v.numel(), tag=58).view(np.int64).reshape(tuple(v.shape))).cuda()
     ws = torch.empty(hqc.hqc_kem_workspace_bytes(level, cnt), dtype=torch.uint8, device="cuda")
     Kd = torch.empty_like(K)
-    ok = torch.empty((cnt,), dtype=torch.int32, device="cuda")
-    times, accepted = {}, {}
+    fns, oks, accepted = {}, {}, {}
     for name, (uu, vv) in {"accept": (u, v), "reject": (u, v_bad), "garbage": (g_u, g_v)}.items():
-        run = lambda: hqc.hqc_kem_decaps(level, keys, h, s, sigma, kidx, uu, vv, salt, Kd, ok, workspace=ws)
-        for _ in range(3):
-            run()
-        times[name] = _median_ms(run)
-        accepted[name] = int(ok.sum().item())
+        oks[name] = torch.empty((cnt,), dtype=torch.int32, device="cuda")
+        fns[name] = (lambda uu=uu, vv=vv, o=oks[name]:
+                     hqc.hqc_kem_decaps(level, keys, h, s, sigma, kidx, uu, vv, salt, Kd, o, workspace=ws))
+    times = _interleaved_medians(fns)
+    accepted = {name: int(o.sum().item()) for name, o in oks.items()}
     keys.free()
     assert accepted == {"accept": cnt, "reject": 0, "garbage": 0}, accepted
     spread = max(times.values()) / min(times.values())

@@ -50,14 +50,21 @@ def run(hqc, R, arrivals, level=None, key=None, **kw):
                              R["word_off"], R["words"], R["m_off"], arrivals, **kw)
 
 
-def test_results_alone_and_in_the_mix(hqc):
+@pytest.mark.parametrize("transfer", [1, 2])
+def test_results_alone_and_in_the_mix(hqc, transfer):
+    """Copy mode (1) and in-place reads of the ring (2): every request's
+    result is its message, in a burst mix, spread out, and alone."""
     R = make_ring(hqc, 300, tag=1)
     # everything at once (a burst mix), then spread out one by one
-    st, lat, m_mix, stats = run(hqc, R, np.zeros(300, np.int64), streams=3, max_batch=64)
+    st, lat, m_mix, stats = run(hqc, R, np.zeros(300, np.int64), streams=3, max_batch=64, transfer=transfer)
     assert (st == 0).all() and (lat >= 0).all() and stats["completed"] == 300
     assert (m_mix == R["want"]).all() and stats["batches"] >= 5
-    st2, lat2, m_spread, _ = run(hqc, R, np.arange(300, dtype=np.int64) * 20000, streams=2)
+    assert stats["in_place"] == (transfer == 2)
+    st2, lat2, m_spread, _ = run(hqc, R, np.arange(300, dtype=np.int64) * 20000, streams=2, transfer=transfer)
     assert (st2 == 0).all() and (m_spread == R["want"]).all()
+    # large batches take the per-level persistent kernels
+    st3, _, m_big, stats3 = run(hqc, R, np.zeros(300, np.int64), streams=1, max_batch=4096, transfer=transfer)
+    assert (st3 == 0).all() and (m_big == R["want"]).all() and stats3["batches"] == 1
     # a few entries alone: a one-entry ring holding the same ciphertext
     for j in (0, 7, 123, 299):
         w0, w1 = R["word_off"][j], R["word_off"][j + 1]
@@ -65,7 +72,8 @@ def test_results_alone_and_in_the_mix(hqc):
         one = torch.from_numpy(R["words"][w0:w1].numpy().copy()).pin_memory()
         st1, _, m1_out, _ = hqc.hqc_serve_run(R["keys"], R["level"][j:j + 1], R["key"][j:j + 1],
                                               np.array([0, w1 - w0], np.int64), one,
-                                              np.array([0, m1 - m0], np.int64), np.zeros(1, np.int64))
+                                              np.array([0, m1 - m0], np.int64), np.zeros(1, np.int64),
+                                              transfer=transfer)
         assert st1[0] == 0 and (m1_out == m_mix[m0:m1]).all()
 
 
@@ -95,10 +103,11 @@ def test_memory_budget_admission(hqc):
         assert (m[R["m_off"][j]:R["m_off"][j + 1]] == R["want"][R["m_off"][j]:R["m_off"][j + 1]]).all()
 
 
-def test_queue_limit_rejects_and_the_admitted_decrypt(hqc):
+@pytest.mark.parametrize("transfer", [0, 1])
+def test_queue_limit_rejects_and_the_admitted_decrypt(hqc, transfer):
     R = make_ring(hqc, 200, tag=4)
     arr = np.zeros(1000, np.int64)     # 1000 requests at once, ring entries reused
-    st, lat, m, stats = run(hqc, R, arr, streams=1, max_batch=32, max_queue=100)
+    st, lat, m, stats = run(hqc, R, arr, streams=1, max_batch=32, max_queue=100, transfer=transfer)
     assert stats["rejected_queue"] > 0 and stats["completed"] + stats["rejected_queue"] == 1000
     assert set(np.unique(st)) <= {0, 3}
     assert (lat[st == 0] >= 0).all()
