@@ -327,30 +327,65 @@ int hqc_get_launch_shape(int level, int keyed, int32_t* warps, int32_t* ctas_per
 /* Plans: one fixed batch (these exact pointers and count) captured in a
  * CUDA graph and replayed with hqc_plan_launch (one graph launch per
  * batch).  Creating a plan allocates small plan-owned device buffers and,
- * with autotune != 0, first times candidate launch shapes on `stream` with
- * the caller's data (which writes m_out); launching allocates nothing.  The
- * data behind the pointers may change between launches, the pointers and
- * count may not.
- *   keyed: the fused kernel of hqc_decrypt_batch_keyed; the tuner picks
- *          warps per block and blocks per SM.
+ * with autotune != 0, first times candidates on `stream` with the caller's
+ * data (which writes m_out); launching allocates nothing.  The data behind
+ * the pointers may change between launches, the pointers and count may
+ * not.  Every candidate computes the same messages; only speed differs.
+ *   keyed: the persistent kernel of hqc_decrypt_batch_keyed.  The tuner
+ *          times every kernel variant -- the library's default choice,
+ *          solo warps taking G = 1, 2 or 4 ciphertexts per turn (their RS
+ *          stages side by side on 32 / G lanes; no G = 4 at HQC-5), two-warp
+ *          teams sharing one doubled operand -- at every launch shape
+ *          (warps per block x blocks per SM) and keeps the fastest.
  *   mixed: the items of hqc_decrypt_mixed.  The tuner compares the single
- *          mixed persistent kernel (form 1) with two level-split forms: the
- *          list is split by level once at creation, then one persistent
- *          kernel per level runs either side by side as parallel graph
- *          branches on a tuned share of the SMs each (form 2) or one after
- *          another on the whole GPU (form 3). */
+ *          mixed persistent kernel (form 1) with three level-split forms:
+ *          the list is split by level once at creation, then one
+ *          persistent kernel per level runs either side by side as
+ *          parallel graph branches on a tuned share of the SMs each (form
+ *          2), or one after another on the whole GPU (form 3); or one
+ *          launch runs all three, its blocks taking a level by block range
+ *          with that level's warp count and shared-memory layout (form 4).
+ *          Forms 2-4 use per level the kernel variant that ran it fastest
+ *          alone. */
 typedef struct hqc_plan_s hqc_plan_t;
 int hqc_plan_create_keyed(int level, int64_t count, const uint64_t* u, const uint64_t* v, const hqc_keyset_t* keys,
                           const int32_t* key_idx, uint8_t* m_out, int autotune, void* stream, hqc_plan_t** out);
 int hqc_plan_create_mixed(int64_t count, const hqc_item_t* items, const uint64_t* arena, int64_t arena_words,
                           const hqc_keyset_t* const keys[3], uint8_t* m_arena, int64_t m_bytes, int autotune,
                           void* stream, hqc_plan_t** out);
+/* Plans with a configuration the caller names instead of tuning (for
+ * instance one that hqc_plan_describe reported for the same batch shape
+ * earlier), so that start-up can skip the tuner:
+ *   keyed: variant 0 the library's default, 1/2/3 solo warps with G =
+ *          1/2/4 ciphertexts per turn (3 not at level 5), 4 two-warp teams;
+ *          cfg the launch shape (NULL or zeros: the variant's default).
+ *   mixed: form 1-4 as above; cfg the shape of form 1; variants3 the kernel
+ *          variant of levels 1, 3, 5 for forms 2 and 3 (NULL: 0); grids3
+ *          the blocks per level for forms 2 and 4 (each >= 1 for a level
+ *          present).  Form 4's kernel fixes its variants (G = 2, G = 1,
+ *          teams).
+ * HQC_EINVAL for a variant, form or shape that does not exist; a shape
+ * that does not fit the device fails at creation with HQC_ECUDA. */
+int hqc_plan_create_keyed_fixed(int level, int64_t count, const uint64_t* u, const uint64_t* v,
+                                const hqc_keyset_t* keys, const int32_t* key_idx, uint8_t* m_out, int variant,
+                                const hqc_launch_cfg_t* cfg, void* stream, hqc_plan_t** out);
+int hqc_plan_create_mixed_fixed(int64_t count, const hqc_item_t* items, const uint64_t* arena, int64_t arena_words,
+                                const hqc_keyset_t* const keys[3], uint8_t* m_arena, int64_t m_bytes, int form,
+                                const hqc_launch_cfg_t* cfg, const int32_t* variants3, const int32_t* grids3,
+                                void* stream, hqc_plan_t** out);
 int hqc_plan_launch(hqc_plan_t* plan, void* stream);
 /* form: 0 keyed, 1 mixed single kernel, 2 mixed level-partitioned, 3 mixed
- * per-level sequential; cfg: the
- * chosen shape (forms 0, 1); grids3: blocks per level 1/3/5 (form 2);
+ * per-level sequential, 4 mixed one launch by block ranges; cfg: the
+ * chosen shape (forms 0, 1); grids3: blocks per level 1/3/5 (forms 2, 4);
  * tuned_ms: the best time the tuner measured (0 without autotune). */
 int hqc_plan_info(const hqc_plan_t* plan, int32_t* form, hqc_launch_cfg_t* cfg, int32_t* grids3, float* tuned_ms);
+/* The plan's choice and every candidate the tuner timed, as one JSON
+ * object written to buf (host memory, cap bytes, NUL-terminated):
+ * {"form", "variant" (keyed) or "level_variants" (mixed), "warps_per_cta",
+ *  "ctas_per_sm", "grids", "tuned_ms", "candidates": [{"form", "variants",
+ *  "warps", "ctas", "grids", "ms"}, ...] fastest first}.  HQC_ENOMEM (and
+ * nothing written) if cap is too small. */
+int hqc_plan_describe(const hqc_plan_t* plan, char* buf, size_t cap);
 int hqc_plan_destroy(hqc_plan_t* plan);
 
 /* Continuous-batching service loop over an open-loop request trace.

@@ -23,7 +23,7 @@ __all__ = [
     "hqc_keys_register", "hqc_decrypt_batch_keyed", "hqc_staged_workspace_bytes",
     "hqc_decrypt_batch_staged", "hqc_decrypt_batch_staged_noalloc", "hqc_decrypt_debug", "hqc_mixed_workspace_bytes",
     "hqc_decrypt_mixed", "hqc_set_launch_config", "hqc_get_launch_shape", "hqc_keygen_batch",
-    "hqc_encrypt_batch", "hqc_count_bad_key_idx", "LEVELS", "Plan", "hqc_plan_create_keyed", "hqc_plan_create_mixed", "hqc_serve_run",
+    "hqc_encrypt_batch", "hqc_count_bad_key_idx", "LEVELS", "Plan", "PLAN_VARIANTS", "PLAN_FORMS", "hqc_plan_create_keyed", "hqc_plan_create_mixed", "hqc_serve_run",
     "SERVE_STATUS", "hqc_decrypt_host_keyed", "hqc_host_workspace_bytes", "hqc_shake256_batch",
     "hqc_kem_keygen", "hqc_kem_workspace_bytes", "hqc_kem_encaps", "hqc_kem_decaps",
     "hqc_kem_host_workspace_bytes", "hqc_kem_decaps_host", "hqc_mixed_host_workspace_bytes",
@@ -110,6 +110,9 @@ def load(build_if_missing: bool = True):
             "hqc_kem_decaps_host": (i32, [i32, i64, P, P, P, P, P, P, P, P, P, P, i64, P, sz, P]),
             "hqc_keygen_batch": (i32, [i32, i64, P, P, P, P, P]),
             "hqc_count_bad_key_idx": (i32, [i64, P, i64, P, P]),
+            "hqc_plan_describe": (i32, [P, P, sz]),
+            "hqc_plan_create_keyed_fixed": (i32, [i32, i64, P, P, P, P, P, i32, P, P, P]),
+            "hqc_plan_create_mixed_fixed": (i32, [i64, P, P, i64, P, P, i64, i32, P, P, P, P, P]),
             "hqc_encrypt_batch": (i32, [i32, i64, P, P, i64, P, P, P, P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
@@ -452,9 +455,17 @@ class Plan:
         ms = ctypes.c_float()
         _check(load().hqc_plan_info(self._h, ctypes.byref(form), ctypes.byref(cfg), grids, ctypes.byref(ms)))
         return dict(form={0: "keyed", 1: "mixed-single-kernel", 2: "mixed-level-partitioned",
-                          3: "mixed-per-level-sequential"}[form.value],
+                          3: "mixed-per-level-sequential", 4: "mixed-one-launch-block-ranges"}[form.value],
                     warps_per_cta=cfg.warps_per_cta, ctas_per_sm=cfg.ctas_per_sm, grids=list(grids),
                     tuned_ms=ms.value)
+
+    def describe(self):
+        """The chosen form, kernel variant(s) and shape, and every candidate
+        the tuner timed (fastest first), from hqc_plan_describe."""
+        import json
+        buf = ctypes.create_string_buffer(1 << 20)
+        _check(load().hqc_plan_describe(self._h, buf, len(buf)))
+        return json.loads(buf.value.decode())
 
     def destroy(self):
         if self._h:
@@ -468,21 +479,40 @@ class Plan:
             pass
 
 
-def hqc_plan_create_keyed(level, u, v, keys: Keyset, key_idx, m_out, autotune=True, stream=None) -> Plan:
+# kernel variants of the keyed and per-level plans (hqc_plan_create_*_fixed)
+PLAN_VARIANTS = {"default": 0, "solo-G1": 1, "solo-G2": 2, "solo-G4": 3, "team2": 4}
+PLAN_FORMS = {"mixed-single-kernel": 1, "mixed-level-partitioned": 2, "mixed-per-level-sequential": 3,
+              "mixed-one-launch-block-ranges": 4}
+
+
+def hqc_plan_create_keyed(level, u, v, keys: Keyset, key_idx, m_out, autotune=True, stream=None, variant=None,
+                          warps_per_cta=0, ctas_per_sm=0) -> Plan:
+    """Keyed plan: tuned (autotune), the library default, or -- with
+    variant (a PLAN_VARIANTS name or number) -- that variant at the given
+    shape (hqc_plan_create_keyed_fixed)."""
     torch = _torch()
     P = hqc_get_params(level)
     u, v = _as_u64(u), _as_u64(v)
     cnt = u.shape[0]
     h = ctypes.c_void_p()
-    _check(load().hqc_plan_create_keyed(level, cnt, _dev_ptr(u, torch.int64, (cnt, P.W_u_pitch), "u"),
-                                        _dev_ptr(v, torch.int64, (cnt, P.W_v), "v"), keys.handle,
-                                        _dev_ptr(key_idx, torch.int32, (cnt,), "key_idx"),
-                                        _dev_ptr(m_out, torch.uint8, (cnt, P.k), "m_out"), int(bool(autotune)),
-                                        _stream(stream), ctypes.byref(h)))
+    args = (level, cnt, _dev_ptr(u, torch.int64, (cnt, P.W_u_pitch), "u"), _dev_ptr(v, torch.int64, (cnt, P.W_v), "v"),
+            keys.handle, _dev_ptr(key_idx, torch.int32, (cnt,), "key_idx"),
+            _dev_ptr(m_out, torch.uint8, (cnt, P.k), "m_out"))
+    if variant is None:
+        _check(load().hqc_plan_create_keyed(*args, int(bool(autotune)), _stream(stream), ctypes.byref(h)))
+    else:
+        var = PLAN_VARIANTS[variant] if isinstance(variant, str) else int(variant)
+        cfg = _LaunchCfg(warps_per_cta, ctas_per_sm)
+        _check(load().hqc_plan_create_keyed_fixed(*args, var, ctypes.byref(cfg), _stream(stream), ctypes.byref(h)))
     return Plan(h, (u, v, keys, key_idx, m_out))
 
 
-def hqc_plan_create_mixed(items, arena, keys, m_arena, autotune=True, stream=None) -> Plan:
+def hqc_plan_create_mixed(items, arena, keys, m_arena, autotune=True, stream=None, form=None, variants=None,
+                          grids=None, warps_per_cta=0, ctas_per_sm=0) -> Plan:
+    """Mixed plan: tuned (autotune) or the single mixed kernel, or -- with
+    form (a PLAN_FORMS name or 1-4) -- that form with the given per-level
+    variants (names or numbers) and blocks per level
+    (hqc_plan_create_mixed_fixed)."""
     torch = _torch()
     if items.dtype != torch.uint8 or items.numel() % ITEM_DTYPE.itemsize:
         raise TypeError("items must be a uint8 tensor of packed ITEM_DTYPE records")
@@ -490,10 +520,18 @@ def hqc_plan_create_mixed(items, arena, keys, m_arena, autotune=True, stream=Non
     arena = _as_u64(arena)
     karr = (ctypes.c_void_p * 3)(*[(k.handle if k is not None else None) for k in keys])
     h = ctypes.c_void_p()
-    _check(load().hqc_plan_create_mixed(cnt, _dev_ptr(items, torch.uint8, None, "items"),
-                                        _dev_ptr(arena, torch.int64, None, "arena"), arena.numel(), karr,
-                                        _dev_ptr(m_arena, torch.uint8, None, "m_arena"), m_arena.numel(),
-                                        int(bool(autotune)), _stream(stream), ctypes.byref(h)))
+    args = (cnt, _dev_ptr(items, torch.uint8, None, "items"), _dev_ptr(arena, torch.int64, None, "arena"),
+            arena.numel(), karr, _dev_ptr(m_arena, torch.uint8, None, "m_arena"), m_arena.numel())
+    if form is None:
+        _check(load().hqc_plan_create_mixed(*args, int(bool(autotune)), _stream(stream), ctypes.byref(h)))
+    else:
+        f = PLAN_FORMS[form] if isinstance(form, str) else int(form)
+        vs = (ctypes.c_int32 * 3)(*[(PLAN_VARIANTS[x] if isinstance(x, str) else int(x))
+                                    for x in (variants or (0, 0, 0))])
+        gs = (ctypes.c_int32 * 3)(*(grids or (0, 0, 0)))
+        cfg = _LaunchCfg(warps_per_cta, ctas_per_sm)
+        _check(load().hqc_plan_create_mixed_fixed(*args, f, ctypes.byref(cfg), vs, gs, _stream(stream),
+                                                  ctypes.byref(h)))
     return Plan(h, (items, arena, keys, m_arena))
 
 

@@ -17,9 +17,9 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libhqc_gb300.so")
 PEAKS_LIB = os.path.join(BUILD, "libhqc_peaks.so")
-SOURCES = ["hqc_decrypt.cu", "hqc_encrypt.cu", "hqc_abi.cu", "hqc_noalloc.cu", "hqc_plan.cu", "hqc_serve.cu", "hqc_host.cu", "hqc_kem.cu"]
+SOURCES = ["hqc_decrypt.cu", "hqc_stage.cu", "hqc_tune.cu", "hqc_encrypt.cu", "hqc_abi.cu", "hqc_noalloc.cu", "hqc_plan.cu", "hqc_serve.cu", "hqc_host.cu", "hqc_kem.cu"]
 PEAKS_SOURCES = ["hqc_peaks.cu"]
-HEADERS = ["hqc_params.cuh", "hqc_device.cuh", "hqc_internal.h", "hqc_keccak.cuh"]
+HEADERS = ["hqc_params.cuh", "hqc_device.cuh", "hqc_kernels.cuh", "hqc_internal.h", "hqc_keccak.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]
 
@@ -41,14 +41,14 @@ def _digest() -> str:
 
 
 def kernel_digest() -> str:
-    """Digest of the device code of the decryption kernels (hqc_decrypt.cu up
-    to its launch helpers, and the headers it includes): profile counters of
-    those kernels stay valid while it holds."""
+    """Digest of the device code of the decryption kernels (the kernel
+    templates up to their launch helpers, and the headers they include):
+    profile counters of those kernels stay valid while it holds."""
     h = hashlib.sha256()
-    for f in ("hqc_decrypt.cu", "hqc_device.cuh", "hqc_params.cuh", "hqc_internal.h"):
+    for f in ("hqc_kernels.cuh", "hqc_device.cuh", "hqc_params.cuh", "hqc_internal.h"):
         with open(os.path.join(CSRC, f), "rb") as fh:
             data = fh.read()
-        if f == "hqc_decrypt.cu":
+        if f == "hqc_kernels.cuh":
             cut = data.find(b"// Launch helpers")
             data = data[:cut] if cut >= 0 else data
         h.update(data)

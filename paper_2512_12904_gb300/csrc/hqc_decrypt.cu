@@ -1,152 +1,17 @@
-// Decryption kernels for sm_103a:
-//   * k_decrypt_fused  -- persistent kernel, one warp per ciphertext at a
-//     time, S1-S9 fused with every intermediate in shared memory/registers;
-//   * k_decrypt_mixed  -- the same for a shuffled HQC-1/3/5 item list with a
-//     dynamic work counter;
-//   * k_stage_*        -- the plain one-kernel-per-stage form (product, RM,
-//     RS) with intermediates in global memory, also used by the debug path
-//     that dumps every intermediate.
+// The default decryption kernels and their launchers: the fused
+// persistent kernels, the latency forms, the mixed-level kernels.
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <map>
-#include <mutex>
-#include <tuple>
 #include <type_traits>
-#include <utility>
 
-#include "hqc_device.cuh"
-#include "hqc_internal.h"
+#include "hqc_kernels.cuh"
 
 namespace hqc {
 
 int level_index(int level) { return level == 1 ? 0 : level == 3 ? 1 : level == 5 ? 2 : -1; }
 
-// Largest block of the persistent kernels per level.  Shared memory caps
-// the warps per SM at about 40 / 20 / 13 for HQC-1 / 3 / 5; the bound lets
-// the compiler spend the rest of the register file on each warp.
-template <int LEVEL> struct FusedBound;
-template <> struct FusedBound<1> { static constexpr int threads = 1024; };
-template <> struct FusedBound<3> { static constexpr int threads = 640; };
-template <> struct FusedBound<5> { static constexpr int threads = 416; };
-constexpr int MIXED_MAX_THREADS = 416;
-
-// Ciphertexts a warp takes per turn: their Reed-Solomon stages run side by
-// side on 32 / G lanes each.  Measured on GB300 (G = 1, 2, 4): two per turn
-// pays for HQC-1 (+6 %), one is best for HQC-3 and HQC-5.
-template <int LEVEL> struct FusedGroup { static constexpr int G = 1; };
-template <> struct FusedGroup<1> { static constexpr int G = 2; };
-
-template <int LEVEL>
-__host__ __device__ constexpr int fused_words() { return fused_warp_words<Level<LEVEL>, FusedGroup<LEVEL>::G>(); }
-
-// ---------------------------------------------------------------------------
-// Fused persistent kernel, one level.  Warp w takes groups of G consecutive
-// ciphertexts w, w + (all warps), ...
-// ---------------------------------------------------------------------------
-template <int LEVEL, bool KEYED, int G = FusedGroup<LEVEL>::G>
-__global__ void __launch_bounds__(FusedBound<LEVEL>::threads, 1) k_decrypt_fused(DecArgs a) {
-  using LV = Level<LEVEL>;
-  extern __shared__ __align__(16) uint8_t smem[];
-  gf_tables_init(smem, threadIdx.x, blockDim.x);
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const GF gf(smem, lane);
-  uint32_t* ws = reinterpret_cast<uint32_t*>(smem + GF_TABLE_BYTES) + warp * fused_warp_words<LV, G>();
-  const int64_t ngroups = (a.count + G - 1) / G;
-  for (int64_t q = (int64_t)blockIdx.x * nw + warp; q < ngroups; q += (int64_t)gridDim.x * nw) {
-    auto rows = [&](int g, const uint64_t*& u, const uint64_t*& v, const uint32_t*& y, uint8_t*& m) {
-      const int64_t it0 = q * G + g;
-      bool ok = it0 < a.count;
-      const int64_t it = ok ? it0 : q * G;
-      if (KEYED) {
-        // an index outside [0, nkeys) skips the item: m stays untouched
-        const uint32_t ki = (uint32_t)__ldg(a.key_idx + it);
-        const bool kok = ki < (uint64_t)a.nkeys;
-        y = a.y + (kok ? (int64_t)ki : 0) * LV::w;
-        ok = ok && kok;
-      } else {
-        y = a.y + it * LV::w;
-      }
-      u = a.u + it * LV::W_u_pitch;
-      v = a.v + it * LV::W_v;
-      m = a.m + it * LV::k;
-      return ok;
-    };
-    decrypt_group<LV, G, !KEYED>(gf, ws, lane, rows);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Fused persistent kernel with two-warp teams (HQC-3 and HQC-5): team t of
-// the grid takes pairs of consecutive ciphertexts t, t + (all teams), ...
-// At most 15 teams per block (named barriers 1..15).
-// ---------------------------------------------------------------------------
-template <int LEVEL> struct TeamBound;
-template <> struct TeamBound<1> { static constexpr int threads = 960; };
-template <> struct TeamBound<3> { static constexpr int threads = 960; };
-template <> struct TeamBound<5> { static constexpr int threads = 768; };
-// Levels that use the team kernels.  Measured on GB300: HQC-5 gains 26 %
-// (24 warps per SM instead of 13); HQC-3 loses 17 % (its half strips waste
-// 8.6 % of the product and 20 solo warps already hide enough latency).
-template <int LEVEL> struct UseTeam { static constexpr bool value = LEVEL == 5; };
-
-template <int LEVEL, bool KEYED>
-__global__ void __launch_bounds__(TeamBound<LEVEL>::threads, 1) k_decrypt_team(DecArgs a) {
-  using LV = Level<LEVEL>;
-  extern __shared__ __align__(16) uint8_t smem[];
-  gf_tables_init(smem, threadIdx.x, blockDim.x);
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int team = warp >> 1, wt = warp & 1, nteams = blockDim.x >> 6;
-  const GF gf(smem, lane);
-  uint32_t* ws = reinterpret_cast<uint32_t*>(smem + GF_TABLE_BYTES) + team * Team<LV>::WORDS;
-  const TeamSync sync{(uint32_t)(1 + team)};
-  const int64_t ngroups = (a.count + 1) / 2;
-  for (int64_t q = (int64_t)blockIdx.x * nteams + team; q < ngroups; q += (int64_t)gridDim.x * nteams) {
-    auto rows = [&](int g, const uint64_t*& u, const uint64_t*& v, const uint32_t*& y, uint8_t*& m) {
-      const int64_t it0 = 2 * q + g;
-      bool ok = it0 < a.count;
-      const int64_t it = ok ? it0 : 2 * q;
-      if (KEYED) {
-        // an index outside [0, nkeys) skips the item: m stays untouched
-        const uint32_t ki = (uint32_t)__ldg(a.key_idx + it);
-        const bool kok = ki < (uint64_t)a.nkeys;
-        y = a.y + (kok ? (int64_t)ki : 0) * LV::w;
-        ok = ok && kok;
-      } else {
-        y = a.y + it * LV::w;
-      }
-      u = a.u + it * LV::W_u_pitch;
-      v = a.v + it * LV::W_v;
-      m = a.m + it * LV::k;
-      return ok;
-    };
-    decrypt_team<LV, !KEYED>(gf, ws, wt, lane, sync, rows);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Fused persistent kernel over a mixed-level item list.  Each warp claims
-// the next item from a.counter (or walks a static stride when no counter is
-// given); shared memory per warp is sized for HQC-5.  Items whose level,
-// key or offsets fall outside the given arrays are skipped.
-// ---------------------------------------------------------------------------
-constexpr int MIXED_WARP_WORDS =
-    cmax(fused_warp_words<Level<1>, 1>(), cmax(fused_warp_words<Level<3>, 1>(), fused_warp_words<Level<5>, 1>()));
-
-template <class LV>
-__device__ __forceinline__ void mixed_item(const GF& gf, uint32_t* ws, int lane, const MixedArgs& a,
-                                           const MixedItem& it) {
-  const int li = LV::level == 1 ? 0 : LV::level == 3 ? 1 : 2;
-  const bool ok = (uint32_t)it.key < (uint64_t)a.nkeys[li] && it.u_off >= 0 && (it.u_off & 1) == 0 &&
-                  it.u_off + LV::W_u_pitch <= a.arena_words && it.v_off >= 0 &&
-                  it.v_off + LV::W_v <= a.arena_words && it.m_off >= 0 && it.m_off + LV::k <= a.m_bytes;
-  if (!ok) return;
-  decrypt_one<LV, false>(gf, ws, lane, a.arena + it.u_off, a.arena + it.v_off, a.keys[li] + (int64_t)it.key * LV::w,
-                         a.m + it.m_off);
-}
-
+// Fused persistent kernel over a mixed-level item list (see mixed_item).
 __global__ void __launch_bounds__(MIXED_MAX_THREADS, 1) k_decrypt_mixed(MixedArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   gf_tables_init(smem, threadIdx.x, blockDim.x);
@@ -174,312 +39,6 @@ __global__ void __launch_bounds__(MIXED_MAX_THREADS, 1) k_decrypt_mixed(MixedArg
       it += stride;
     }
   }
-}
-
-// ---------------------------------------------------------------------------
-// Latency form of the mixed kernel: a team of LAT_TEAM warps decodes one
-// item of any level at a time, splitting the product strips and the RM
-// blocks over the team; the first warp runs the Reed-Solomon stage.  One
-// team per block, so a small batch spreads over every SM.  In a batch that
-// fits one wave the slowest item sets the time, and its chain is shorter.
-// ---------------------------------------------------------------------------
-constexpr int LAT_TEAM = 4;
-constexpr int64_t MAX_LATENCY_GRID = 65535;
-template <int T>
-__host__ __device__ constexpr int lat_team_words() {
-  return cmax(Team<Level<1>, T, 1>::WORDS, cmax(Team<Level<3>, T, 1>::WORDS, Team<Level<5>, T, 1>::WORDS));
-}
-
-template <class LV, int T>
-__device__ __forceinline__ void mixed_item_team(const GF& gf, uint32_t* ws, int wt, int lane, const TeamSync& sync,
-                                                const MixedArgs& a, const MixedItem& it) {
-  const int li = LV::level == 1 ? 0 : LV::level == 3 ? 1 : 2;
-  const bool ok = (uint32_t)it.key < (uint64_t)a.nkeys[li] && it.u_off >= 0 && (it.u_off & 1) == 0 &&
-                  it.u_off + LV::W_u_pitch <= a.arena_words && it.v_off >= 0 &&
-                  it.v_off + LV::W_v <= a.arena_words && it.m_off >= 0 && it.m_off + LV::k <= a.m_bytes;
-  if (!ok) return;  // the same item for the whole team: all its warps leave together
-  auto rows = [&](int g, const uint64_t*& u, const uint64_t*& v, const uint32_t*& y, uint8_t*& m) {
-    u = a.arena + it.u_off;
-    v = a.arena + it.v_off;
-    y = a.keys[li] + (int64_t)it.key * LV::w;
-    m = a.m + it.m_off;
-    return g == 0;
-  };
-  decrypt_team<LV, false, T, 1>(gf, ws, wt, lane, sync, rows);
-}
-
-template <int T>
-__global__ void __launch_bounds__(32 * T, 4) k_decrypt_mixed_team(MixedArgs a) {
-  extern __shared__ __align__(16) uint8_t smem[];
-  gf_tables_init(smem, threadIdx.x, blockDim.x);
-  __syncthreads();
-  const int lane = threadIdx.x & 31, wt = threadIdx.x >> 5;
-  const GF gf(smem, lane);
-  uint32_t* ws = reinterpret_cast<uint32_t*>(smem + GF_TABLE_BYTES);
-  const TeamSync sync{1u, 32u * T};
-  for (int64_t it = blockIdx.x; it < a.count; it += gridDim.x) {
-    const MixedItem item = a.items[it];
-    if (item.level == 1) mixed_item_team<Level<1>, T>(gf, ws, wt, lane, sync, a, item);
-    else if (item.level == 3) mixed_item_team<Level<3>, T>(gf, ws, wt, lane, sync, a, item);
-    else if (item.level == 5) mixed_item_team<Level<5>, T>(gf, ws, wt, lane, sync, a, item);
-  }
-}
-
-// The same latency form for a batch of one level (literal or keyed
-// supports): block b decodes ciphertexts b, b + grid, ... with its team.
-template <int LEVEL, bool KEYED, int T>
-__global__ void __launch_bounds__(32 * T, 4) k_decrypt_latency(DecArgs a) {
-  using LV = Level<LEVEL>;
-  extern __shared__ __align__(16) uint8_t smem[];
-  gf_tables_init(smem, threadIdx.x, blockDim.x);
-  __syncthreads();
-  const int lane = threadIdx.x & 31, wt = threadIdx.x >> 5;
-  const GF gf(smem, lane);
-  uint32_t* ws = reinterpret_cast<uint32_t*>(smem + GF_TABLE_BYTES);
-  const TeamSync sync{1u, 32u * T};
-  for (int64_t it = blockIdx.x; it < a.count; it += gridDim.x) {
-    auto rows = [&](int g, const uint64_t*& u, const uint64_t*& v, const uint32_t*& y, uint8_t*& m) {
-      bool ok = g == 0;
-      if (KEYED) {
-        // an index outside [0, nkeys) skips the item: m stays untouched
-        const uint32_t ki = (uint32_t)__ldg(a.key_idx + it);
-        const bool kok = ki < (uint64_t)a.nkeys;
-        y = a.y + (kok ? (int64_t)ki : 0) * LV::w;
-        ok = ok && kok;
-      } else {
-        y = a.y + it * LV::w;
-      }
-      u = a.u + it * LV::W_u_pitch;
-      v = a.v + it * LV::W_v;
-      m = a.m + it * LV::k;
-      return ok;
-    };
-    decrypt_team<LV, !KEYED, T, 1>(gf, ws, wt, lane, sync, rows);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Persistent kernel over the items of ONE level taken from a mixed list
-// (the item list was partitioned by level beforehand).  Static stride:
-// every item of a level costs the same.  Used by the level-partitioned
-// plan, which runs one of these per level side by side in a CUDA graph.
-// ---------------------------------------------------------------------------
-template <int LEVEL>
-__global__ void __launch_bounds__(FusedBound<LEVEL>::threads, 1) k_decrypt_items(MixedArgs a) {
-  using LV = Level<LEVEL>;
-  constexpr int G = FusedGroup<LEVEL>::G;
-  constexpr int li = LEVEL == 1 ? 0 : LEVEL == 3 ? 1 : 2;
-  extern __shared__ __align__(16) uint8_t smem[];
-  gf_tables_init(smem, threadIdx.x, blockDim.x);
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const GF gf(smem, lane);
-  uint32_t* ws = reinterpret_cast<uint32_t*>(smem + GF_TABLE_BYTES) + warp * fused_words<LEVEL>();
-  const int64_t ngroups = (a.count + G - 1) / G;
-  for (int64_t q = (int64_t)blockIdx.x * nw + warp; q < ngroups; q += (int64_t)gridDim.x * nw) {
-    auto rows = [&](int g, const uint64_t*& u, const uint64_t*& v, const uint32_t*& y, uint8_t*& m) {
-      const int64_t it = q * G + g;
-      if (it >= a.count) return false;
-      const MixedItem item = a.items[it];
-      const bool ok = item.level == LEVEL && (uint32_t)item.key < (uint64_t)a.nkeys[li] && item.u_off >= 0 &&
-                      (item.u_off & 1) == 0 && item.u_off + LV::W_u_pitch <= a.arena_words && item.v_off >= 0 &&
-                      item.v_off + LV::W_v <= a.arena_words && item.m_off >= 0 && item.m_off + LV::k <= a.m_bytes;
-      u = a.arena + (ok ? item.u_off : 0);
-      v = a.arena + (ok ? item.v_off : 0);
-      y = a.keys[li] + (ok ? (int64_t)item.key * LV::w : 0);
-      m = a.m + (ok ? item.m_off : 0);
-      return ok;
-    };
-    decrypt_group<LV, G, false>(gf, ws, lane, rows);
-  }
-}
-
-template <int LEVEL>
-__global__ void __launch_bounds__(TeamBound<LEVEL>::threads, 1) k_decrypt_items_team(MixedArgs a) {
-  using LV = Level<LEVEL>;
-  constexpr int li = LEVEL == 1 ? 0 : LEVEL == 3 ? 1 : 2;
-  extern __shared__ __align__(16) uint8_t smem[];
-  gf_tables_init(smem, threadIdx.x, blockDim.x);
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int team = warp >> 1, wt = warp & 1, nteams = blockDim.x >> 6;
-  const GF gf(smem, lane);
-  uint32_t* ws = reinterpret_cast<uint32_t*>(smem + GF_TABLE_BYTES) + team * Team<LV>::WORDS;
-  const TeamSync sync{(uint32_t)(1 + team)};
-  const int64_t ngroups = (a.count + 1) / 2;
-  for (int64_t q = (int64_t)blockIdx.x * nteams + team; q < ngroups; q += (int64_t)gridDim.x * nteams) {
-    auto rows = [&](int g, const uint64_t*& u, const uint64_t*& v, const uint32_t*& y, uint8_t*& m) {
-      const int64_t it = 2 * q + g;
-      if (it >= a.count) return false;
-      const MixedItem item = a.items[it];
-      const bool ok = item.level == LEVEL && (uint32_t)item.key < (uint64_t)a.nkeys[li] && item.u_off >= 0 &&
-                      (item.u_off & 1) == 0 && item.u_off + LV::W_u_pitch <= a.arena_words && item.v_off >= 0 &&
-                      item.v_off + LV::W_v <= a.arena_words && item.m_off >= 0 && item.m_off + LV::k <= a.m_bytes;
-      u = a.arena + (ok ? item.u_off : 0);
-      v = a.arena + (ok ? item.v_off : 0);
-      y = a.keys[li] + (ok ? (int64_t)item.key * LV::w : 0);
-      m = a.m + (ok ? item.m_off : 0);
-      return ok;
-    };
-    decrypt_team<LV, false>(gf, ws, wt, lane, sync, rows);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Plain per-stage form.
-// K1: product + XOR with v (warp per ciphertext), w (and t) to global.
-// ---------------------------------------------------------------------------
-constexpr int STAGE_THREADS = 256;
-
-template <int LEVEL, bool KEYED, bool WITH_T>
-__global__ void __launch_bounds__(STAGE_THREADS) k_stage_product(DecArgs a, uint64_t* w_out, uint64_t* t_out) {
-  using LV = Level<LEVEL>;
-  extern __shared__ __align__(16) uint8_t smem[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t it = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-  if (it >= a.count) return;
-  uint32_t* ws = reinterpret_cast<uint32_t*>(smem) + warp * LV::WARP_WORDS;
-  const uint32_t* yrow;
-  if (KEYED) {
-    const uint32_t ki = (uint32_t)__ldg(a.key_idx + it);
-    yrow = a.y + (ki < (uint64_t)a.nkeys ? (int64_t)ki : 0) * LV::w;
-  } else {
-    yrow = a.y + it * LV::w;
-  }
-  load_supports<LV::n, LV::w>(ws + LV::U2W, yrow, lane);
-  build_doubled<LV::n, LV::W_u_pitch, LV::U2W>(ws, a.u + it * LV::W_u_pitch, lane);
-  using PS = ProductStrips<LEVEL>;
-  const int w0 = PS::start(lane), wn = PS::len(lane);
-  uint32_t acc[PS::MAXLEN];
-  rot_xor_product<PS::MAXLEN, LV::w, !KEYED>(ws, ws + LV::U2W, w0, acc);
-  const uint32_t* v32 = reinterpret_cast<const uint32_t*>(a.v + it * LV::W_v);
-  uint32_t* w32 = reinterpret_cast<uint32_t*>(w_out + it * LV::W_v);
-  uint32_t* t32 = WITH_T ? reinterpret_cast<uint32_t*>(t_out + it * LV::W_v) : nullptr;
-#pragma unroll
-  for (int k = 0; k < PS::MAXLEN; k++) {
-    const int i = w0 + k;
-    if (k < wn && i < LV::W_v32) {
-      if (WITH_T) t32[i] = acc[k];
-      w32[i] = acc[k] ^ v32[i];
-    }
-  }
-}
-
-// K2: one lane pair per (ciphertext, RS symbol): duplicated RM decode.
-template <int LEVEL>
-__global__ void __launch_bounds__(STAGE_THREADS) k_stage_rm(int64_t count, const uint64_t* __restrict__ w,
-                                                           uint8_t* __restrict__ r_out) {
-  using LV = Level<LEVEL>;
-  const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 1;  // pair index
-  const int64_t total = count * LV::n1;
-  const int64_t gg = g < total ? g : total - 1;  // both lanes of every pair stay active
-  const int64_t it = gg / LV::n1;
-  const int j = (int)(gg - it * LV::n1);
-  const uint32_t* blk = reinterpret_cast<const uint32_t*>(w + it * LV::W_v) + j * (LV::n2 / 32);
-  const uint32_t byte = rm_decode_pair<LV::mult>(blk, threadIdx.x & 1);
-  if (g < total && (threadIdx.x & 1) == 0) r_out[it * LV::n1 + j] = (uint8_t)byte;
-}
-
-// K3: one warp per ciphertext: Reed-Solomon decode (and the debug dump).
-constexpr int RS_SCRATCH_WORDS = 24 + RS_SCRATCH;  // the n1 received bytes, then the RS scratch
-
-// With key_idx given, a ciphertext whose index is outside [0, nkeys) is
-// skipped (its m row stays untouched), as in the fused kernels.
-template <int LEVEL, bool DEBUG>
-__global__ void __launch_bounds__(STAGE_THREADS) k_stage_rs(int64_t count, const uint8_t* __restrict__ r_in,
-                                                           uint8_t* __restrict__ m_out, DebugArgs d,
-                                                           const int32_t* __restrict__ key_idx, int64_t nkeys) {
-  using LV = Level<LEVEL>;
-  static_assert(LV::n1 <= 96, "received bytes fit in 24 words");
-  extern __shared__ __align__(16) uint8_t smem[];
-  gf_tables_init(smem, threadIdx.x, blockDim.x);
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t it = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-  if (it >= count) return;
-  if (key_idx && (uint32_t)__ldg(key_idx + it) >= (uint64_t)nkeys) return;
-  const GF gf(smem, lane);
-  uint32_t* base = reinterpret_cast<uint32_t*>(smem + GF_TABLE_BYTES) + warp * RS_SCRATCH_WORDS;
-  uint8_t* rb = reinterpret_cast<uint8_t*>(base);
-  for (int j = lane; j < LV::n1; j += 32) rb[j] = r_in[it * LV::n1 + j];
-  __syncwarp();
-  if (DEBUG) {
-    RSDebugRow row{d.S + it * LV::NR, d.lam + it * LV::CAP, d.L + it,  d.errmask + it * LV::n1,
-                   d.errval + it * LV::n1, d.cw + it * LV::n1, d.flag + it};
-    rs_decode_seg<LV, 32, true>(gf, base + 24, rb, lane, true, m_out + it * LV::k, &row);
-  } else {
-    rs_decode_seg<LV, 32, false>(gf, base + 24, rb, lane, true, m_out + it * LV::k, nullptr);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Launch helpers
-// ---------------------------------------------------------------------------
-template <int LEVEL>
-[[maybe_unused]] static size_t fused_smem(int warps) {
-  return (size_t)GF_TABLE_BYTES + (size_t)warps * fused_words<LEVEL>() * 4;
-}
-
-static std::mutex g_shape_mu;
-static std::map<std::pair<const void*, int>, size_t> g_shape_attr;
-static std::map<std::tuple<const void*, int, int, size_t>, int> g_shape_occ;
-
-static int device_props(int* sms, int* smem_optin) {
-  int dev = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaDeviceGetAttribute(smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  return dev;
-}
-
-// per_warp: shared bytes per warp (for teams: per team / 2); teams: the
-// warp count must be even and at most 30 (15 named barriers).
-template <class KernelT>
-static cudaError_t shape_for(KernelT kern, int max_threads, size_t per_warp, const LaunchCfg& cfg, int* warps,
-                             int* ctas, int* grid, size_t* smem_bytes, bool teams = false) {
-  int sms = 0, optin = 0;
-  const int dev = device_props(&sms, &optin);
-  int nw = cfg.warps_per_cta;
-  if (nw <= 0) {
-    nw = (int)((optin - GF_TABLE_BYTES) / per_warp);
-    if (nw > max_threads / 32) nw = max_threads / 32;
-    if (teams) nw = std::min(nw & ~1, 30);
-  }
-  if (nw < 1 || (teams && (nw & 1))) return cudaErrorInvalidValue;
-  if (nw > max_threads / 32 || (teams && nw > 30)) return cudaErrorInvalidValue;
-  const size_t sm = GF_TABLE_BYTES + (size_t)nw * per_warp;
-  if (sm > (size_t)optin) return cudaErrorInvalidValue;
-  // the shared-memory attribute only grows, and occupancies are looked up
-  // once per (kernel, device, warps, bytes): repeated launches of small
-  // batches pay no runtime queries
-  const void* kp = reinterpret_cast<const void*>(kern);
-  int occ = 0;
-  {
-    std::lock_guard<std::mutex> lock(g_shape_mu);
-    size_t& attr = g_shape_attr[{kp, dev}];
-    if (sm > attr) {
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      if (e != cudaSuccess) return e;
-      attr = sm;
-    }
-    const auto key = std::make_tuple(kp, dev, nw, sm);
-    const auto hit = g_shape_occ.find(key);
-    if (hit != g_shape_occ.end()) {
-      occ = hit->second;
-    } else {
-      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, nw * 32, sm);
-      if (e != cudaSuccess) return e;
-      g_shape_occ[key] = occ;
-    }
-  }
-  if (occ < 1) return cudaErrorInvalidConfiguration;
-  int c = cfg.ctas_per_sm > 0 ? cfg.ctas_per_sm : occ;
-  if (c > occ) c = occ;
-  *warps = nw;
-  *ctas = c;
-  *grid = sms * c;
-  *smem_bytes = sm;
-  return cudaSuccess;
 }
 
 // Largest batch that runs the latency form (one four-warp team per
@@ -736,61 +295,6 @@ cudaError_t mixed_occupancy(const LaunchCfg& cfg, int* warps, int* ctas, int* gr
   if (ctas) *ctas = c;
   if (grid) *grid = g;
   return e;
-}
-
-template <int LEVEL, bool KEYED, bool DEBUG>
-static cudaError_t staged_level(const DecArgs& a, uint64_t* w, uint8_t* r, const DebugArgs* d, cudaStream_t st) {
-  using LV = Level<LEVEL>;
-  if (a.count == 0) return cudaSuccess;
-  const int wpb = STAGE_THREADS / 32;
-  // K1
-  {
-    auto kern = k_stage_product<LEVEL, KEYED, DEBUG>;
-    const size_t sm = (size_t)wpb * LV::WARP_WORDS * 4;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    const int64_t blocks = (a.count + wpb - 1) / wpb;
-    kern<<<(unsigned)blocks, STAGE_THREADS, sm, st>>>(a, w, DEBUG ? d->t : nullptr);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  // K2
-  {
-    const int64_t threads = 2 * a.count * LV::n1;
-    const int64_t blocks = (threads + STAGE_THREADS - 1) / STAGE_THREADS;
-    k_stage_rm<LEVEL><<<(unsigned)blocks, STAGE_THREADS, 0, st>>>(a.count, w, r);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  // K3
-  {
-    auto kern = k_stage_rs<LEVEL, DEBUG>;
-    const size_t sm = GF_TABLE_BYTES + (size_t)wpb * RS_SCRATCH_WORDS * 4;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    const int64_t blocks = (a.count + wpb - 1) / wpb;
-    DebugArgs dd{};
-    if (DEBUG) dd = *d;
-    kern<<<(unsigned)blocks, STAGE_THREADS, sm, st>>>(a.count, r, a.m, dd, KEYED ? a.key_idx : nullptr, a.nkeys);
-    return cudaGetLastError();
-  }
-}
-
-cudaError_t launch_staged(int level, bool keyed, const DecArgs& a, uint64_t* w, uint8_t* r, cudaStream_t st) {
-  switch (level) {
-    case 1: return keyed ? staged_level<1, true, false>(a, w, r, nullptr, st) : staged_level<1, false, false>(a, w, r, nullptr, st);
-    case 3: return keyed ? staged_level<3, true, false>(a, w, r, nullptr, st) : staged_level<3, false, false>(a, w, r, nullptr, st);
-    case 5: return keyed ? staged_level<5, true, false>(a, w, r, nullptr, st) : staged_level<5, false, false>(a, w, r, nullptr, st);
-  }
-  return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_debug(int level, const DecArgs& a, const DebugArgs& d, cudaStream_t st) {
-  switch (level) {
-    case 1: return staged_level<1, false, true>(a, d.w, d.r, &d, st);
-    case 3: return staged_level<3, false, true>(a, d.w, d.r, &d, st);
-    case 5: return staged_level<5, false, true>(a, d.w, d.r, &d, st);
-  }
-  return cudaErrorInvalidValue;
 }
 
 }  // namespace hqc

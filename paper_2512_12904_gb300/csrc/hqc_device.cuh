@@ -499,11 +499,15 @@ __device__ __forceinline__ uint32_t rs_bm(const GF& gf, const uint16_t* logS, ui
 #pragma unroll 1
     for (int rr = R0; rr < R1; rr++) bm_iter(na, rr);
   };
-  static_assert(NC >= 1 && NC <= 4, "BM phases");
+  static_assert(NC >= 1 && NC <= 8, "BM phases");
   bm_phase(std::integral_constant<int, 1>{});
   if constexpr (NC >= 2) bm_phase(std::integral_constant<int, 2>{});
   if constexpr (NC >= 3) bm_phase(std::integral_constant<int, 3>{});
   if constexpr (NC >= 4) bm_phase(std::integral_constant<int, 4>{});
+  if constexpr (NC >= 5) bm_phase(std::integral_constant<int, 5>{});
+  if constexpr (NC >= 6) bm_phase(std::integral_constant<int, 6>{});
+  if constexpr (NC >= 7) bm_phase(std::integral_constant<int, 7>{});
+  if constexpr (NC >= 8) bm_phase(std::integral_constant<int, 8>{});
 #pragma unroll
   for (int x = 0; x < NC; x++) {
     const int c = sl + SEG * x;

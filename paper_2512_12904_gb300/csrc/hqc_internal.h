@@ -88,6 +88,23 @@ cudaError_t launch_items(int level, const MixedArgs& a, int grid, cudaStream_t s
 cudaError_t items_occupancy(int level, const LaunchCfg& cfg, int* warps, int* ctas_per_sm, int* grid);
 cudaError_t mixed_occupancy(const LaunchCfg& cfg, int* warps, int* ctas_per_sm, int* grid);
 
+// Kernel variants of the keyed and per-level persistent decryption that
+// the plans' tuner times (hqc_tune.cu).  VAR_DEFAULT is the library's own
+// choice (launch_fused / launch_items); the others fix the mapping of
+// ciphertexts to warps: solo warps with G = 1, 2, 4 per turn, or two-warp
+// teams.  HQC-5 has no G = 4 instance.
+enum DecVariant : int { VAR_DEFAULT = 0, VAR_SOLO1 = 1, VAR_SOLO2 = 2, VAR_SOLO4 = 3, VAR_TEAM = 4, VAR_COUNT = 5 };
+bool variant_exists(int level, int variant);
+const char* variant_name(int variant);
+cudaError_t launch_fused_variant(int level, int variant, const DecArgs& a, cudaStream_t st, const LaunchCfg& cfg);
+cudaError_t launch_items_variant(int level, int variant, const MixedArgs& a, int grid, cudaStream_t st,
+                                 const LaunchCfg& cfg);
+cudaError_t items_variant_occupancy(int level, int variant, const LaunchCfg& cfg, int* warps, int* ctas_per_sm,
+                                    int* grid);
+// One launch over the three per-level lists of a partitioned mixed batch,
+// grid[li] blocks for level li (0 for an empty list).
+cudaError_t launch_mixed_ranges(const MixedArgs part[3], const int grid[3], cudaStream_t st);
+
 cudaError_t launch_keygen(int level, int64_t nkeys, const uint64_t* h, const uint32_t* x, const uint32_t* y,
                           uint64_t* s, cudaStream_t st);
 cudaError_t launch_encrypt(int level, int64_t count, const uint64_t* h, const uint64_t* s, int64_t nkeys,

@@ -362,6 +362,7 @@ extern "C" int hqc_serve_run(const hqc_serve_cfg_t* cfg, const hqc_keyset_t* con
       }
       const int64_t wbytes = words * 8;  // up to the last admitted request (<= words_cap)
       const uint64_t* arena = s.d_words;
+      e = cudaSuccess;  // (e may still hold another slot's not-ready poll)
       if (in_place) {
         arena = ring_dev + ring->word_off[base];
       } else {

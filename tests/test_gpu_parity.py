@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 import synth
-from workloads import adversarial, honest, with_garbage_padding
+from workloads import adversarial, honest, noisy_keyed, with_garbage_padding
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -349,7 +349,7 @@ def test_mixed_plan_graph_autotuned(hqc):
     m = torch.zeros(nbytes, dtype=torch.uint8, device="cuda")
     plan = hqc.hqc_plan_create_mixed(items, arena, keys, m, autotune=True)
     info = plan.info()
-    assert info["form"] in ("mixed-single-kernel", "mixed-level-partitioned", "mixed-per-level-sequential")
+    assert info["form"] in hqc.PLAN_FORMS
     for _ in range(2):
         m.zero_()
         plan.launch()
@@ -520,3 +520,102 @@ def test_large_batch_2_20_hqc1(hqc):
     want = oracle.decrypt(level, host(u_d[idx]).view(np.uint64), host(v_d[idx]).view(np.uint64), y[kidx[idx]])
     assert (host(got[idx]) == want).all()
     keys.free()
+
+
+VARIANTS = ("default", "solo-G1", "solo-G2", "solo-G4", "team2")
+
+
+@pytest.mark.parametrize("level", LEVELS)
+def test_every_keyed_plan_variant_matches_oracle(hqc, level):
+    """Every kernel variant the keyed plan's tuner chooses among -- solo
+    warps with G = 1, 2, 4 ciphertexts per turn, two-warp teams and the
+    library's default -- at a full-GPU shape and at a one-warp-per-SM shape
+    (several turns per warp), decrypts exactly as the oracle does on a batch
+    with hard ciphertexts mixed in; G = 4 does not exist at HQC-5.  The
+    tuned plan reports its choice and the candidates it timed."""
+    wl, u, v = noisy_keyed(level, 8, 700, first_ct=40000, tag=60 + level)
+    want = oracle.decrypt(level, u, v, wl.y_rows)
+    keys = hqc.Keyset(level, wl.y)
+    ud, vd, kidx = u64(u), u64(v), dev(wl.key_idx.astype(np.int32))
+    for var in VARIANTS:
+        for w, c in ((0, 0), (2, 1)):
+            m = torch.full((700, wl.P.k), 0xA5, dtype=torch.uint8, device="cuda")
+            if var == "solo-G4" and level == 5:
+                with pytest.raises(hqc.HqcError):
+                    hqc.hqc_plan_create_keyed(level, ud, vd, keys, kidx, m, variant=var)
+                continue
+            plan = hqc.hqc_plan_create_keyed(level, ud, vd, keys, kidx, m, variant=var, warps_per_cta=w,
+                                             ctas_per_sm=c)
+            plan.launch()
+            torch.cuda.synchronize()
+            assert (host(m) == want).all(), (var, w, c)
+            plan.destroy()
+    m = torch.zeros((700, wl.P.k), dtype=torch.uint8, device="cuda")
+    plan = hqc.hqc_plan_create_keyed(level, ud, vd, keys, kidx, m, autotune=True)
+    d = plan.describe()
+    assert d["form"] == "keyed" and d["variant"] in VARIANTS
+    assert len(d["candidates"]) >= 40
+    assert [x["ms"] for x in d["candidates"]] == sorted(x["ms"] for x in d["candidates"])
+    assert abs(d["candidates"][0]["ms"] - d["tuned_ms"]) < 1e-6
+    m.zero_()
+    plan.launch()
+    torch.cuda.synchronize()
+    assert (host(m) == want).all()
+    plan.destroy()
+    keys.free()
+
+
+def _mixed_batch(hqc, counts, tag):
+    """A shuffled HQC-1/3/5 item list (noisy ciphertexts), its arena and the
+    oracle's messages in arena order."""
+    parts = {lvl: noisy_keyed(lvl, 8, cnt, first_ct=45000, tag=tag + lvl) for lvl, cnt in counts}
+    seq = [(lvl, i) for lvl, cnt in counts for i in range(cnt)]
+    order = synth.shuffle(np.arange(len(seq), dtype=np.int32), tag=tag)
+    seq = [seq[j] for j in order]
+    items = np.zeros(len(seq), dtype=hqc.ITEM_DTYPE)
+    arena, want, words, m_off = [], [], 0, 0
+    exp = {lvl: oracle.decrypt(lvl, u, v, wl.y_rows) for lvl, (wl, u, v) in parts.items()}
+    for idx, (lvl, i) in enumerate(seq):
+        wl, u, v = parts[lvl]
+        items[idx] = (lvl, wl.key_idx[i], words, words + wl.P.W_u_pitch, m_off)
+        arena += [u[i], v[i]]
+        want.append(exp[lvl][i])
+        words += wl.P.W_u_pitch + wl.P.W_v
+        m_off += wl.P.k
+    keys = [hqc.Keyset(l, parts[l][0].y) for l in (1, 3, 5)]
+    return dev(items.view(np.uint8)), u64(np.concatenate(arena)), keys, np.concatenate(want), m_off
+
+
+def test_every_mixed_plan_form_matches_oracle(hqc):
+    """Every form of the mixed plan -- the single mixed kernel, the levels
+    side by side as graph branches, one after another, and one launch by
+    block ranges -- with every per-level kernel variant, matches the
+    oracle; the tuned plan reports per-level variants and candidates."""
+    items, arena, keys, want, m_bytes = _mixed_batch(hqc, ((1, 400), (3, 350), (5, 250)), tag=300)
+
+    def check(**kw):
+        m = torch.full((m_bytes,), 0xA5, dtype=torch.uint8, device="cuda")
+        plan = hqc.hqc_plan_create_mixed(items, arena, keys, m, **kw)
+        plan.launch()
+        torch.cuda.synchronize()
+        assert (host(m) == want).all(), kw
+        return plan
+
+    check(form=1).destroy()
+    check(form=1, warps_per_cta=4, ctas_per_sm=1).destroy()
+    for var in VARIANTS:
+        vs = [var if (var != "solo-G4" or lvl != 5) else "default" for lvl in (1, 3, 5)]
+        check(form=2, variants=vs, grids=(20, 40, 92)).destroy()
+        check(form=3, variants=vs).destroy()
+    check(form=4, grids=(30, 50, 72)).destroy()
+    check(form=4, grids=(3, 2, 5)).destroy()
+    with pytest.raises(hqc.HqcError):
+        check(form=2, grids=(0, 40, 92))
+    plan = check(autotune=True)
+    d = plan.describe()
+    assert d["form"] in hqc.PLAN_FORMS and len(d["level_variants"]) == 3
+    forms = {c["form"] for c in d["candidates"]}
+    assert forms == set(hqc.PLAN_FORMS), forms
+    plan.destroy()
+    for k in keys:
+        k.free()

@@ -87,3 +87,27 @@ def adversarial(level: int, tag: int = 0):
             vv[i, lo: lo + P.n2 // 64] ^= synth.words(P.n2 // 64, tag=95 + tag, index=i * 1000 + int(j))
     u = np.concatenate([u, extra.u]); v = np.concatenate([v, vv]); y = np.concatenate([y, extra.y_rows])
     return P, u, v, y
+
+
+def noisy_keyed(level: int, nkeys: int, count: int, first_ct: int, tag: int):
+    """Honest ciphertexts under nkeys valid keys, a fifth of them made hard:
+    random v (far beyond delta errors), heavy noise on delta-1 .. n1/2 RM
+    blocks, all-zero u, or garbage in u's padding.  Returns (workload, u, v);
+    the supports stay valid, so the rows suit the keyed entry points."""
+    wl = honest(level, nkeys, count, first_ct=first_ct, tag=tag)
+    P = wl.P
+    u, v = wl.u.copy(), wl.v.copy()
+    for i in range(0, count, 5):
+        kind = (i // 5) % 4
+        if kind == 0:
+            v[i] = synth.words(P.W_v, tag=tag + 1, index=i)
+        elif kind == 1:
+            nb = [P.delta - 1, P.delta, P.delta + 1, P.n1 // 2][(i // 20) % 4]
+            for j in synth.support(P.n1, nb, tag=tag + 2, index=i):
+                lo = int(j) * P.n2 // 64
+                v[i, lo:lo + P.n2 // 64] ^= synth.words(P.n2 // 64, tag=tag + 3, index=i * 1000 + int(j))
+        elif kind == 2:
+            u[i] = 0
+        else:
+            u[i] = with_garbage_padding(P, u[i:i + 1], tag=tag + 4 + i)[0]
+    return wl, u, v
