@@ -520,6 +520,9 @@ def bench_single(ctx, wl_name, full):
     if full:
         line["e2e"] = e2e_single(ctx, level, count, P, keys, u_d, v_d, k_d, m_ref, stream)
         line["correct"] = line["correct"] and line["e2e"].pop("correct")
+    if count <= 512:
+        line["one_ciphertext_us"] = one_ciphertext_latency(ctx, stream)
+        line["correct"] = line["correct"] and all(x["correct"] for x in line["one_ciphertext_us"].values())
     if full and dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         rate, n, dt = oracle_rate(level, nkeys, args.cpu_seconds, cores)
@@ -528,6 +531,27 @@ def bench_single(ctx, wl_name, full):
                                           % (n, dt)}
     keys.free()
     return line
+
+
+def one_ciphertext_latency(ctx, stream, reps=200):
+    """Device time of decrypting ONE ciphertext per level through the keyed
+    entry point (the latency form: a four-warp team), median and p99 of
+    `reps` launches, each timed alone with events on the launching stream;
+    the L2 is flushed before each."""
+    import torch
+    hqc, dist, device = ctx.hqc, ctx.dist, ctx.device
+    out = {}
+    for level in (1, 3, 5):
+        P, keys, u_d, v_d, k_d, m_ref, _, _ = make_workload(hqc, level, 1, 1, dist.rank, device)
+        m = torch.zeros_like(m_ref)
+        fn = lambda: hqc.hqc_decrypt_batch_keyed(level, u_d, v_d, keys, k_d, m, stream=stream)
+        warm(fn, 5, stream)
+        _, per, _ = timed_steps(fn, reps, stream, dist, flush=ctx.flush_l2)
+        out[str(level)] = {"p50": 1e3 * pct(per, 50), "p99": 1e3 * pct(per, 99),
+                           "correct": bool((m == m_ref).all().item()),
+                           "kernel": decrypt_kernel_name(level, 1)}
+        keys.free()
+    return out
 
 
 def e2e_single(ctx, level, count, P, keys, u_d, v_d, k_d, m_ref, stream):
@@ -641,6 +665,12 @@ def bench_mixed(ctx, full):
     torch.cuda.synchronize()
     tune_s = time.perf_counter() - t0
     info = plan.info()
+    desc = plan.describe()
+    info["level_variants"] = desc["level_variants"]
+    info["best_ms_per_form"] = {}
+    for c in desc["candidates"]:  # fastest first
+        info["best_ms_per_form"].setdefault(c["form"], c["ms"])
+    info["candidates_timed"] = len(desc["candidates"])
 
     def step():
         plan.launch(stream=stream)

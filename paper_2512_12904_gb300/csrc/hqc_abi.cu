@@ -109,7 +109,7 @@ const char* hqc_last_error(void) { return g_err.c_str(); }
 
 int hqc_decrypt_batch(int level, int64_t count, const uint64_t* u, const uint64_t* v, const uint32_t* y,
                       uint8_t* m_out, void* stream) {
-  hqc_params_t p;
+  hqc_params_t p{};
   int rc = check_common(level, count, u, v, m_out, &p);
   if (rc != HQC_OK || count == 0) return rc;
   if (!y || !aligned(y, 4)) return fail(HQC_EINVAL, "y must be a non-NULL 4-byte aligned device pointer");
@@ -125,7 +125,7 @@ int hqc_decrypt_batch(int level, int64_t count, const uint64_t* u, const uint64_
 
 int hqc_keys_register(int level, int64_t nkeys, const uint32_t* y_host, hqc_keyset_t** out) {
   g_err.clear();
-  hqc_params_t p;
+  hqc_params_t p{};
   if (!out) return fail(HQC_EINVAL, "out is NULL");
   *out = nullptr;
   if (!params_of(level, &p)) return fail(HQC_EINVAL, "level must be 1, 3 or 5 (got %d)", level);
@@ -176,7 +176,7 @@ int hqc_keys_info(const hqc_keyset_t* keys, int* level, int64_t* nkeys, const ui
 
 int hqc_decrypt_batch_keyed(int level, int64_t count, const uint64_t* u, const uint64_t* v, const hqc_keyset_t* keys,
                             const int32_t* key_idx, uint8_t* m_out, void* stream) {
-  hqc_params_t p;
+  hqc_params_t p{};
   int rc = check_common(level, count, u, v, m_out, &p);
   if (rc != HQC_OK || count == 0) return rc;
   if (!keys || keys->level != level) return fail(HQC_EINVAL, "keys missing or registered for another level");
@@ -215,7 +215,7 @@ int hqc_count_bad_key_idx(int64_t count, const int32_t* key_idx, int64_t nkeys, 
 }
 
 size_t hqc_staged_workspace_bytes(int level, int64_t count) {
-  hqc_params_t p;
+  hqc_params_t p{};
   if (!params_of(level, &p) || count <= 0) return 0;
   const size_t w = (size_t)count * p.W_v * 8;
   const size_t r = ((size_t)count * p.n1 + 15) / 16 * 16;
@@ -225,7 +225,7 @@ size_t hqc_staged_workspace_bytes(int level, int64_t count) {
 int hqc_decrypt_batch_staged(int level, int64_t count, const uint64_t* u, const uint64_t* v, const uint32_t* y,
                              const hqc_keyset_t* keys, const int32_t* key_idx, void* workspace,
                              size_t workspace_bytes, uint8_t* m_out, void* stream) {
-  hqc_params_t p;
+  hqc_params_t p{};
   int rc = check_common(level, count, u, v, m_out, &p);
   if (rc != HQC_OK || count == 0) return rc;
   const bool keyed = keys != nullptr;
@@ -253,7 +253,7 @@ int hqc_decrypt_batch_staged(int level, int64_t count, const uint64_t* u, const 
 
 int hqc_decrypt_debug(int level, int64_t count, const uint64_t* u, const uint64_t* v, const uint32_t* y,
                       const hqc_debug_dump_t* dump, uint8_t* m_out, void* stream) {
-  hqc_params_t p;
+  hqc_params_t p{};
   int rc = check_common(level, count, u, v, m_out, &p);
   if (rc != HQC_OK || count == 0) return rc;
   if (!y || !dump) return fail(HQC_EINVAL, "y and dump must be non-NULL");
@@ -340,7 +340,7 @@ int hqc_get_launch_shape(int level, int keyed, int32_t* warps, int32_t* ctas_per
 int hqc_keygen_batch(int level, int64_t nkeys, const uint64_t* h, const uint32_t* x, const uint32_t* y,
                      uint64_t* s_out, void* stream) {
   g_err.clear();
-  hqc_params_t p;
+  hqc_params_t p{};
   if (!params_of(level, &p)) return fail(HQC_EINVAL, "level must be 1, 3 or 5");
   if (nkeys < 0) return fail(HQC_EINVAL, "nkeys must be >= 0");
   if (nkeys == 0) return HQC_OK;
@@ -353,7 +353,7 @@ int hqc_encrypt_batch(int level, int64_t count, const uint64_t* h, const uint64_
                       const int32_t* key_idx, const uint8_t* m, const uint32_t* r1, const uint32_t* r2,
                       const uint32_t* e, uint64_t* u_out, uint64_t* v_out, void* stream) {
   g_err.clear();
-  hqc_params_t p;
+  hqc_params_t p{};
   if (!params_of(level, &p)) return fail(HQC_EINVAL, "level must be 1, 3 or 5");
   if (count < 0 || nkeys < 0) return fail(HQC_EINVAL, "count and nkeys must be >= 0");
   if (count == 0) return HQC_OK;

@@ -565,7 +565,7 @@ def test_every_keyed_plan_variant_matches_oracle(hqc, level):
     keys.free()
 
 
-def _mixed_batch(hqc, counts, tag):
+def _noisy_mixed_batch(hqc, counts, tag):
     """A shuffled HQC-1/3/5 item list (noisy ciphertexts), its arena and the
     oracle's messages in arena order."""
     parts = {lvl: noisy_keyed(lvl, 8, cnt, first_ct=45000, tag=tag + lvl) for lvl, cnt in counts}
@@ -591,7 +591,7 @@ def test_every_mixed_plan_form_matches_oracle(hqc):
     side by side as graph branches, one after another, and one launch by
     block ranges -- with every per-level kernel variant, matches the
     oracle; the tuned plan reports per-level variants and candidates."""
-    items, arena, keys, want, m_bytes = _mixed_batch(hqc, ((1, 400), (3, 350), (5, 250)), tag=300)
+    items, arena, keys, want, m_bytes = _noisy_mixed_batch(hqc, ((1, 400), (3, 350), (5, 250)), tag=300)
 
     def check(**kw):
         m = torch.full((m_bytes,), 0xA5, dtype=torch.uint8, device="cuda")
