@@ -668,8 +668,9 @@ def bench_mixed(ctx, full):
     desc = plan.describe()
     info["level_variants"] = desc["level_variants"]
     info["best_ms_per_form"] = {}
-    for c in desc["candidates"]:  # fastest first
-        info["best_ms_per_form"].setdefault(c["form"], c["ms"])
+    for c in desc["candidates"]:  # fastest first; whole-batch runs only
+        if c["whole_batch"]:
+            info["best_ms_per_form"].setdefault(c["form"], c["ms"])
     info["candidates_timed"] = len(desc["candidates"])
 
     def step():

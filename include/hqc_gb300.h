@@ -382,9 +382,11 @@ int hqc_plan_info(const hqc_plan_t* plan, int32_t* form, hqc_launch_cfg_t* cfg, 
 /* The plan's choice and every candidate the tuner timed, as one JSON
  * object written to buf (host memory, cap bytes, NUL-terminated):
  * {"form", "variant" (keyed) or "level_variants" (mixed), "warps_per_cta",
- *  "ctas_per_sm", "grids", "tuned_ms", "candidates": [{"form", "variants",
- *  "warps", "ctas", "grids", "ms"}, ...] fastest first}.  HQC_ENOMEM (and
- * nothing written) if cap is too small. */
+ *  "ctas_per_sm", "grids", "tuned_ms", "candidates": [{"form",
+ *  "whole_batch", "levels", "variants", "warps", "ctas", "grids", "ms"},
+ *  ...] fastest first}.  Mixed plans also list the per-level solo runs that
+ * chose each level's variant (whole_batch false, levels: the one level
+ * timed).  HQC_ENOMEM (and nothing written) if cap is too small. */
 int hqc_plan_describe(const hqc_plan_t* plan, char* buf, size_t cap);
 int hqc_plan_destroy(hqc_plan_t* plan);
 

@@ -39,6 +39,7 @@
 // shape or per-level block counts, and the mean time of one batch.
 struct PlanCand {
   int kind;
+  int levels;      // bit i set: level i's items took part (all present ones, except in per-level solo runs)
   int variant[3];  // keyed: variant[0]; mixed forms 2-4: per level 1, 3, 5
   int warps, ctas;
   int grid[3];
@@ -145,6 +146,12 @@ float measure(hqc_plan_s* p, cudaStream_t st, int reps) {
   }
   PlanCand c;
   c.kind = p->kind;
+  c.levels = 0;
+  if (p->kind == 0 || p->kind == 1) {
+    c.levels = 7;
+  } else {
+    for (int i = 0; i < 3; i++) c.levels |= p->part[i].count > 0 ? 1 << i : 0;
+  }
   if (p->kind == 0) {
     c.variant[0] = p->variant;
     c.variant[1] = c.variant[2] = -1;
@@ -558,15 +565,28 @@ int hqc_plan_describe(const hqc_plan_t* plan, char* buf, size_t cap) {
            plan->cfg.warps_per_cta, plan->cfg.ctas_per_sm, plan->grid[0], plan->grid[1], plan->grid[2],
            plan->tuned_ms);
   o += t;
+  // the levels the whole batch holds (candidates with fewer were per-level
+  // solo runs that chose each level's variant)
+  int whole = 7;
+  if (plan->kind != 0) {
+    whole = 0;
+    for (int i = 0; i < 3; i++) whole |= plan->part[i].count > 0 ? 1 << i : 0;
+    if (plan->kind == 1 && whole == 0) whole = 7;
+  }
   std::vector<PlanCand> c = plan->cands;
+  for (auto& x : c)
+    if (x.kind == 0 || x.kind == 1) x.levels = whole;
   std::sort(c.begin(), c.end(), [](const PlanCand& x, const PlanCand& y) { return x.ms < y.ms; });
   o += "\"candidates\": [";
   for (size_t i = 0; i < c.size(); i++) {
     snprintf(t, sizeof t,
-             "%s{\"form\": \"%s\", \"variants\": [\"%s\", \"%s\", \"%s\"], \"warps\": %d, \"ctas\": %d, "
-             "\"grids\": [%d, %d, %d], \"ms\": %.5f}",
-             i ? ", " : "", form_name(c[i].kind), vname(c[i].variant[0]), vname(c[i].variant[1]),
-             vname(c[i].variant[2]), c[i].warps, c[i].ctas, c[i].grid[0], c[i].grid[1], c[i].grid[2], c[i].ms);
+             "%s{\"form\": \"%s\", \"whole_batch\": %s, \"levels\": [%s%s%s], \"variants\": [\"%s\", \"%s\", "
+             "\"%s\"], \"warps\": %d, \"ctas\": %d, \"grids\": [%d, %d, %d], \"ms\": %.5f}",
+             i ? ", " : "", form_name(c[i].kind), c[i].levels == whole ? "true" : "false",
+             c[i].levels & 1 ? "1" : "", c[i].levels & 2 ? ((c[i].levels & 1) ? ", 3" : "3") : "",
+             c[i].levels & 4 ? ((c[i].levels & 3) ? ", 5" : "5") : "", vname(c[i].variant[0]),
+             vname(c[i].variant[1]), vname(c[i].variant[2]), c[i].warps, c[i].ctas, c[i].grid[0], c[i].grid[1],
+             c[i].grid[2], c[i].ms);
     o += t;
   }
   o += "]}";

@@ -614,8 +614,11 @@ def test_every_mixed_plan_form_matches_oracle(hqc):
     plan = check(autotune=True)
     d = plan.describe()
     assert d["form"] in hqc.PLAN_FORMS and len(d["level_variants"]) == 3
-    forms = {c["form"] for c in d["candidates"]}
+    whole = [c for c in d["candidates"] if c["whole_batch"]]
+    forms = {c["form"] for c in whole}
     assert forms == set(hqc.PLAN_FORMS), forms
+    assert abs(min(c["ms"] for c in whole) - d["tuned_ms"]) < 1e-6
+    assert any(not c["whole_batch"] and len(c["levels"]) == 1 for c in d["candidates"])
     plan.destroy()
     for k in keys:
         k.free()
