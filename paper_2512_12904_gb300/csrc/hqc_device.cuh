@@ -732,13 +732,92 @@ struct TeamSync {
   }
 };
 
+// Berlekamp-Massey on one warp (32 lanes, lane owns coefficient c = lane +
+// 32 x) with the discrepancy carried ahead instead of summed at the top of
+// each iteration.  With coef_r = d_r / b and x^m B written B_r:
+//   Lambda_{r+1} = Lambda_r + coef_r B_r, so
+//   d_{r+1} = sum_c Lambda_{r+1,c} S_{r+2-c} = P_r + coef_r Q_r, where
+//   P_r = sum_c Lambda_{r,c} S_{r+2-c} and Q_r = sum_c B_{r,c} S_{r+2-c};
+//   B_{r+1} = x (cond ? Lambda_r : B_r) gives Q_{r+1} = cond ? P_r : Q_r.
+// So each iteration sums P_r from Lambda_r (off the serial path) while the
+// serial path from d_r to d_{r+1} is one log, one product and one XOR;
+// Lambda, B, b and L take exactly the textbook values.  d_0 = Q_0 = S_1.
+// Same block skipping as rs_bm.  Returns L; writes log Lambda to logLam.
+template <class LV>
+__device__ __forceinline__ uint32_t rs_bm_lookahead(const GF& gf, const uint16_t* logS, uint16_t* logLam, int lane) {
+  constexpr int NR = LV::NR, CAP = LV::CAP, SEG = 32;
+  constexpr int NC = cdiv(CAP, SEG);
+  uint32_t lam[NC], lbp[NC];
+#pragma unroll
+  for (int x = 0; x < NC; x++) {
+    const int c = lane + SEG * x;
+    lam[x] = c == 0;
+    lbp[x] = c == 1 ? 0u : GF_LOG_ZERO;  // B = x (m = 1, B = 1)
+  }
+  uint32_t lb = 0, L = 0;                 // log b (b = 1), LFSR length
+  uint32_t d = gf.exp(logS[0]);           // d_0 = S_1
+  uint32_t lq = logS[0];                  // log Q_0 = log S_1
+  auto iter = [&](auto na, int rr) {
+    constexpr int NA = decltype(na)::value;
+    uint32_t llam[NA];
+    uint32_t part = 0;
+#pragma unroll
+    for (int x = 0; x < NA; x++) {
+      const int c = lane + SEG * x;  // rr + 1 - c >= -64: padding covers c > rr + 1
+      llam[x] = gf.log(lam[x]);
+      part ^= gf.mul_l(llam[x], logS[rr + 1 - c]);
+    }
+    const uint32_t P = __reduce_xor_sync(FULL_MASK, part);
+    const uint32_t ld = gf.log(d);
+    const uint32_t lcoef = sel(d == 0, GF_LOG_ZERO, sel(ld >= lb, ld - lb, ld + 255u - lb));
+    const bool cond = (d != 0) & (2 * L <= (uint32_t)rr);
+    uint32_t src[NA];
+#pragma unroll
+    for (int x = 0; x < NA; x++) {
+      lam[x] ^= gf.mul_l(lcoef, lbp[x]);
+      src[x] = sel(cond, llam[x], lbp[x]);
+    }
+#pragma unroll
+    for (int x = 0; x < NA; x++) {
+      const uint32_t up = __shfl_up_sync(FULL_MASK, src[x], 1);
+      const uint32_t carry = x > 0 ? __shfl_sync(FULL_MASK, src[x > 0 ? x - 1 : 0], SEG - 1) : GF_LOG_ZERO;
+      const uint32_t nb = lane == 0 ? carry : up;
+      lbp[x] = (lane + SEG * x) < CAP ? nb : GF_LOG_ZERO;
+    }
+    d = P ^ gf.mul_l(lcoef, lq);          // d_{r+1}
+    lq = sel(cond, gf.log(P), lq);        // log Q_{r+1}
+    lb = sel(cond, ld, lb);
+    L = sel(cond, (uint32_t)rr + 1u - L, L);
+  };
+  // block x of Lambda_r, B_r is zero while r + 2 <= SEG x; P_r reads
+  // Lambda_r only (degree <= r), so the phases of rs_bm hold here too
+  auto phase = [&](auto na) {
+    constexpr int NA = decltype(na)::value;
+    constexpr int R0 = NA == 1 ? 0 : cmin(NR, SEG * (NA - 1) - 2);
+    constexpr int R1 = NA == NC ? NR : cmin(NR, SEG * NA - 2);
+#pragma unroll 2
+    for (int rr = R0; rr < R1; rr++) iter(na, rr);
+  };
+  static_assert(NC >= 1 && NC <= 2, "look-ahead BM phases");
+  phase(std::integral_constant<int, 1>{});
+  if constexpr (NC >= 2) phase(std::integral_constant<int, 2>{});
+#pragma unroll
+  for (int x = 0; x < NC; x++) {
+    const int c = lane + SEG * x;
+    if (c < CAP) logLam[c] = (uint16_t)gf.log(lam[x]);
+  }
+  __syncwarp();
+  return L;
+}
+
 // S8-S9 of ONE received word by a team of T warps (tid = 32 wt + lane):
 // the syndromes split by position over the warps, Berlekamp-Massey on warp
 // 0 (the serial part), Omega by coefficient over the lanes, and Chien +
 // Forney at the k message positions with each position's sums over the
 // 2 delta + 1 coefficients split over the warps.  Partial sums meet in
-// shared memory between team barriers.  Same arithmetic, term for term, as
-// rs_decode_seg; only the order of the XORs differs.  rs: RS_TEAM_SCRATCH
+// shared memory between team barriers.  Same field arithmetic as
+// rs_decode_seg, with Berlekamp-Massey's discrepancy carried ahead
+// (rs_bm_lookahead); only the order of the XORs differs.  rs: RS_TEAM_SCRATCH
 // words of shared scratch.  An inactive word is decoded but not stored.
 template <int T>
 __host__ __device__ constexpr int rs_team_scratch() { return 176 + 40 * T; }
@@ -800,7 +879,7 @@ __device__ __forceinline__ void rs_decode_team(const GF& gf, uint32_t* rs, const
       }
     }
     __syncwarp();
-    rs_bm<LV, 32, false>(gf, logS, logLam, lane, active, nullptr);
+    rs_bm_lookahead<LV>(gf, logS, logLam, lane);
   }
   sync();
 

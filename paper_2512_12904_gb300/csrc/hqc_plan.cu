@@ -198,9 +198,9 @@ void release(hqc_plan_s* p) {
 // Candidate launch shapes for a single persistent kernel.
 std::vector<hqc::LaunchCfg> shape_candidates(int max_warps) {
   std::vector<hqc::LaunchCfg> c;
-  for (int w : {4, 8, 12, 16, 20, 24, 32})
+  for (int w : {4, 8, 12, 16, 18, 20, 22, 24, 26, 27, 28, 30, 32})
     if (w <= max_warps)
-      for (int k : {1, 2, 4}) c.push_back(hqc::LaunchCfg{w, k});
+      for (int k : {1, 2}) c.push_back(hqc::LaunchCfg{w, k});
   c.push_back(hqc::LaunchCfg{});  // library default
   return c;
 }
