@@ -491,6 +491,23 @@ def bench_single(ctx, wl_name, full):
     plain_ms = dist.max(plain_ms)
     plain_ok = bool((m_plain == m_ref).all().item())
 
+    # the same batch through an autotuned keyed plan (one graph launch of the
+    # tuner's kernel variant and shape per step)
+    tuned = None
+    if count >= 4096:
+        m_plan = torch.zeros_like(m_ref)
+        plan = hqc.hqc_plan_create_keyed(level, u_d, v_d, keys, k_d, m_plan, autotune=True, stream=stream)
+        d = plan.describe()
+        fn = lambda: plan.launch(stream=stream)
+        warm(fn, 3, stream)
+        plan_ms, _, _ = timed_steps(fn, steps, stream, dist)
+        plan_ms = dist.max(plan_ms)
+        tuned = {"value": dist.sum(float(count)) * steps / (plan_ms * 1e-3), "unit": UNIT,
+                 "ms_per_step": plan_ms / steps, "variant": d["variant"], "warps_per_cta": d["warps_per_cta"],
+                 "ctas_per_sm": d["ctas_per_sm"], "candidates_timed": len(d["candidates"]),
+                 "correct": bool((m_plan == m_ref).all().item()),
+                 "api": "hqc_plan_create_keyed(autotune) + hqc_plan_launch"}
+        plan.destroy()
     total_count = dist.sum(float(count))
     value = total_count * steps / (max_ms * 1e-3)
     plain_value = total_count * plain_steps / (plain_ms * 1e-3)
@@ -517,6 +534,9 @@ def bench_single(ctx, wl_name, full):
         "gpu_launches": steps,
         "clocks": clocks,
     }
+    if tuned is not None:
+        line["tuned_plan"] = tuned
+        line["correct"] = line["correct"] and tuned["correct"]
     if full:
         line["e2e"] = e2e_single(ctx, level, count, P, keys, u_d, v_d, k_d, m_ref, stream)
         line["correct"] = line["correct"] and line["e2e"].pop("correct")

@@ -68,17 +68,10 @@ static cudaError_t team_level(const DecArgs& a, cudaStream_t st, const LaunchCfg
   if (grid) *grid = g;
   if (!launch || a.count == 0) return cudaSuccess;
   // less than one wave: fewer warps per block so the batch spreads over
-  // every SM instead of filling a few; more than one: the warp count that
-  // wastes the least of the last turn
-  if (cfg.warps_per_cta == 0) {
+  // every SM instead of filling a few
+  if (cfg.warps_per_cta == 0 && a.count < (int64_t)g * nw) {
     const int64_t sms = g / c;
-    int want = nw;
-    if (a.count < (int64_t)g * nw) {
-      want = (int)((a.count + sms - 1) / sms);
-      want = std::max(2, (want + 1) & ~1);
-    } else {
-      want = balanced_warps(a.count, 1, nw, g, 2);
-    }
+    const int want = std::max(2, ((int)((a.count + sms - 1) / sms) + 1) & ~1);
     if (want < nw) {
       LaunchCfg sc;
       sc.warps_per_cta = want;
@@ -127,15 +120,10 @@ static cudaError_t fused_level(const DecArgs& a, cudaStream_t st, const LaunchCf
     return cudaGetLastError();
   }
   // less than one wave: fewer warps per block so the batch spreads over
-  // every SM instead of filling a few; more than one: the warp count that
-  // wastes the least of the last turn
-  if (cfg.warps_per_cta == 0) {
+  // every SM instead of filling a few
+  if (cfg.warps_per_cta == 0 && a.count < (int64_t)g * nw * G) {
     const int64_t sms = g / c;
-    int want = nw;
-    if (a.count < (int64_t)g * nw * G)
-      want = std::max(1, (int)((a.count + sms * G - 1) / (sms * G)));
-    else
-      want = balanced_warps(a.count, G, nw, g, 1);
+    const int want = std::max(1, (int)((a.count + sms * G - 1) / (sms * G)));
     if (want < nw) {
       LaunchCfg sc;
       sc.warps_per_cta = want;
@@ -222,18 +210,11 @@ static cudaError_t items_team_level(const MixedArgs& a, int grid, cudaStream_t s
   if (ctas) *ctas = c;
   if (full_grid) *full_grid = g;
   if (!launch || a.count == 0) return cudaSuccess;
-  // a full grid: for less than one wave fewer warps per block so the items
-  // spread over every SM, for more the warp count that wastes the least of
-  // the last turn
-  if (grid <= 0 && tc.warps_per_cta == 0) {
+  // a full grid for less than one wave: fewer warps per block so the items
+  // spread over every SM
+  if (grid <= 0 && tc.warps_per_cta == 0 && a.count < (int64_t)g * nw) {
     const int64_t sms = g / c;
-    int small = nw;
-    if (a.count < (int64_t)g * nw) {
-      small = (int)((a.count + sms - 1) / sms);
-      small = std::max(2, (small + 1) & ~1);
-    } else {
-      small = balanced_warps(a.count, 1, nw, g, 2);
-    }
+    const int small = std::max(2, ((int)((a.count + sms - 1) / sms) + 1) & ~1);
     if (small < nw) {
       LaunchCfg sc;
       sc.warps_per_cta = small;
@@ -263,16 +244,11 @@ static cudaError_t items_level(const MixedArgs& a, int grid, cudaStream_t st, co
   if (full_grid) *full_grid = g;
   if (!launch || a.count == 0) return cudaSuccess;
   constexpr int G = FusedGroup<LEVEL>::G;
-  // a full grid: for less than one wave fewer warps per block so the items
-  // spread over every SM, for more the warp count that wastes the least of
-  // the last turn
-  if (grid <= 0 && cfg.warps_per_cta == 0) {
+  // a full grid for less than one wave: fewer warps per block so the items
+  // spread over every SM
+  if (grid <= 0 && cfg.warps_per_cta == 0 && a.count < (int64_t)g * nw * G) {
     const int64_t sms = g / c;
-    int small = nw;
-    if (a.count < (int64_t)g * nw * G)
-      small = std::max(1, (int)((a.count + sms * G - 1) / (sms * G)));
-    else
-      small = balanced_warps(a.count, G, nw, g, 1);
+    const int small = std::max(1, (int)((a.count + sms * G - 1) / (sms * G)));
     if (small < nw) {
       LaunchCfg sc;
       sc.warps_per_cta = small;

@@ -420,30 +420,6 @@ static inline int device_props(int* sms, int* smem_optin) {
   return dev;
 }
 
-// Warps per block for a persistent launch of `count` items over `blocks`
-// blocks (blocks per SM x SMs) whose warps take `per_warp` items per turn:
-// the grid's last turn runs only partly full, and the batch takes
-// ceil(count / (blocks w per_warp)) turns of a time that grows with the
-// warps w sharing each SM, so among w in [0.6 nw_max, nw_max] (multiples of
-// `step`) the one with the fewest turns x warps wins, the larger on a tie.
-// (HQC-1, 65,536 items, G = 2: 32 warps need 6.74 turns, so the seventh
-// runs 74 % full; 27 warps need 7.98.)
-inline int balanced_warps(int64_t count, int per_warp, int nw_max, int64_t blocks, int step) {
-  int best = nw_max;
-  int64_t best_cost = -1;
-  const int lo = std::max(step, (nw_max * 3 + 4) / 5);
-  for (int w = nw_max; w >= lo; w -= step) {
-    const int64_t per_turn = blocks * w * per_warp;
-    const int64_t turns = (count + per_turn - 1) / per_turn;
-    const int64_t cost = turns * w;
-    if (best_cost < 0 || cost < best_cost) {
-      best_cost = cost;
-      best = w;
-    }
-  }
-  return best;
-}
-
 // per_warp: shared bytes per warp (for teams: per team / 2); teams: the
 // warp count must be even and at most 30 (15 named barriers).
 template <class KernelT>
