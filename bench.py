@@ -67,6 +67,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU-baseline duration")
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="trace length per offered load (serving)")
+    ap.add_argument("--mixed-plan", default="auto",
+                    help="mixed workload: 'auto' tunes the plan; FORM[:V1,V3,V5[:G1,G3,G5]] builds that configuration "
+                         "(form 1-4, per-level variants by name, blocks per level)")
     ap.add_argument("--configs", choices=["auto", "all", "none"], default="auto",
                     help="also measure every other benchmark configuration (auto: with the default workload at N=1)")
     return ap.parse_args()
@@ -681,7 +684,13 @@ def bench_mixed(ctx, full):
     torch.cuda.synchronize()
 
     t0 = time.perf_counter()
-    plan = hqc.hqc_plan_create_mixed(items_d, arena, keys3, m_out, autotune=True, stream=stream)
+    if args.mixed_plan == "auto":
+        plan = hqc.hqc_plan_create_mixed(items_d, arena, keys3, m_out, autotune=True, stream=stream)
+    else:
+        f = args.mixed_plan.split(":")
+        plan = hqc.hqc_plan_create_mixed(items_d, arena, keys3, m_out, stream=stream, form=int(f[0]),
+                                         variants=f[1].split(",") if len(f) > 1 else None,
+                                         grids=[int(x) for x in f[2].split(",")] if len(f) > 2 else None)
     torch.cuda.synchronize()
     tune_s = time.perf_counter() - t0
     info = plan.info()
