@@ -70,6 +70,8 @@ def parse_args():
     ap.add_argument("--mixed-plan", default="auto",
                     help="mixed workload: 'auto' tunes the plan; FORM[:V1,V3,V5[:G1,G3,G5]] builds that configuration "
                          "(form 1-4, per-level variants by name, blocks per level)")
+    ap.add_argument("--key-offset", type=int, default=0,
+                    help="draw the seeded keys from this key index on (another key set, same recipe)")
     ap.add_argument("--configs", choices=["auto", "all", "none"], default="auto",
                     help="also measure every other benchmark configuration (auto: with the default workload at N=1)")
     return ap.parse_args()
@@ -162,12 +164,15 @@ class Clocks:
 # workload construction (on the device, with the library's own keygen and
 # encryption kernels; randomness from the seeded generator)
 # ---------------------------------------------------------------------------
+KEY_OFFSET = 0  # --key-offset: the seeded key set starts at this key index
+
+
 def make_workload(hqc, level, count, nkeys, rank, device):
     import torch
     import synth
     P = hqc.hqc_get_params(level)
     S = synth.Shape.of(P)
-    h, x, y = synth.keys(S, nkeys, first=rank * nkeys)
+    h, x, y = synth.keys(S, nkeys, first=KEY_OFFSET + rank * nkeys)
     m, r1, r2, e = synth.ciphertext_randomness(S, count, first=rank * count)
     kidx = synth.key_assignment(count, nkeys, tag=100 + level)
     dev = lambda a, dt=None: torch.from_numpy(np.ascontiguousarray(a if dt is None else a.view(dt))).to(device)
@@ -1163,6 +1168,7 @@ def run_ours(args):
         line = bench_single(ctx, args.workload, full=True)
     want_configs = args.configs == "all" or (args.configs == "auto" and args.workload == "hqc1-bulk"
                                               and ctx.dist.world == 1)
+    line["profiles"] = profile_freshness()
     if want_configs:
         line["configs"] = run_sub_configs(ctx)
         line["configs_all_correct"] = all(c.get("correct") is True for c in line["configs"].values())
@@ -1170,6 +1176,22 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     ctx.dist.close()
     return 0
+
+
+def profile_freshness():
+    """For each committed ncu summary that records the kernel-source digest
+    it was captured at: whether that digest is today's (its counters still
+    describe the kernels), else 'stale'."""
+    import glob
+    import re
+    from paper_2512_12904_gb300 import _build
+    now = _build.kernel_digest()
+    out = {}
+    for f in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        m = re.search(r"digest at capture: `([0-9a-f]+)`", open(f).read())
+        if m:
+            out[os.path.basename(f)] = "current" if m.group(1) == now else "stale"
+    return out
 
 
 def traffic_from_profile(level):
@@ -1188,7 +1210,9 @@ def traffic_from_profile(level):
 
 
 def main():
+    global KEY_OFFSET
     args = parse_args()
+    KEY_OFFSET = args.key_offset
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
