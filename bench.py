@@ -66,7 +66,7 @@ def parse_args():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="hqc1-bulk")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU-baseline duration")
-    ap.add_argument("--serve-seconds", type=float, default=1.0, help="trace length per offered load (serving)")
+    ap.add_argument("--serve-seconds", type=float, default=2.0, help="trace length per offered load (serving): at most 30 s with --workload serving, 2 s inside the default line")
     ap.add_argument("--mixed-plan", default="auto",
                     help="mixed workload: 'auto' tunes the plan; FORM[:V1,V3,V5[:G1,G3,G5]] builds that configuration "
                          "(form 1-4, per-level variants by name, blocks per level)")
@@ -874,50 +874,56 @@ def bench_serving(ctx, full):
     moff = np.array(moff, np.int64)
     want = np.concatenate(want)
     keys3 = [per[l][1] for l in (1, 3, 5)]
-    # warm-up: one short run
-    hqc.hqc_serve_run(keys3, levels, key, woff, words, moff, synth.burst_trace(1e5, 0.05, tag=300))
+    serve_kw = dict(streams=4, max_batch=16384, budget_bytes=256 << 20, max_queue=1 << 22)
     points = []
-    duration = max(0.2, min(2.0, args.serve_seconds))
+    # the default bench line runs 2 s per offered load so that every
+    # configuration fits its minute; `--workload serving --serve-seconds 30`
+    # runs the full 30 s points (3e8 requests at 1e7 req/s: about 6 GB of
+    # host-side arrival, status and latency arrays)
+    duration = max(0.2, min(30.0 if full else 2.0, args.serve_seconds))
+    warm_s = 0.25
     for load in SERVE_LOADS:
         arr = synth.burst_trace(load, duration, tag=301 + int(np.log10(load)))
         # clocks are read just before and just after each point: an NVML
         # query while the loop runs holds the driver long enough to show in
-        # the tail latencies
+        # the tail latencies, so the read comes before the point's warm-up
         clk_before = clocks_now(dist.local)
-        st, lat, m_out, stats = hqc.hqc_serve_run(keys3, levels, key, woff, words, moff, arr, streams=4,
-                                                  max_batch=16384, budget_bytes=256 << 20, max_queue=1 << 22)
+        # warm-up at the point's own load (its own trace), not measured
+        hqc.hqc_serve_run(keys3, levels, key, woff, words, moff,
+                          synth.burst_trace(load, warm_s, tag=300 + int(np.log10(load))), **serve_kw)
+        st, lat, m_out, stats = hqc.hqc_serve_run(keys3, levels, key, woff, words, moff, arr, **serve_kw)
         clk_after = clocks_now(dist.local)
         ok = st == 0
         good = True
         idx = np.nonzero(ok)[0]
         # every completed ring entry must hold its message (later writers repeat it)
-        done_entries = np.unique(idx % period)
+        done_entries = np.nonzero(np.bincount(idx % period, minlength=period))[0]
         for j in done_entries[:: max(1, len(done_entries) // 2000)]:
             good &= bool((m_out[moff[j]:moff[j + 1]] == want[moff[j]:moff[j + 1]]).all())
         l_us = lat[ok] / 1e3
+        pct = [float(x) for x in np.percentile(l_us, [50, 99, 99.9])] if l_us.size else [None] * 3
         points.append({
             "offered_req_per_s": load, "requests": int(len(arr)), "completed": int(stats["completed"]),
             "rejected": int(stats["rejected_queue"] + stats["rejected_size"] + stats["rejected_invalid"]),
             "sustained_dec_per_s": stats["completed"] / (stats["wall_ns"] * 1e-9) if stats["wall_ns"] else None,
-            "p50_us": float(np.percentile(l_us, 50)) if l_us.size else None,
-            "p99_us": float(np.percentile(l_us, 99)) if l_us.size else None,
-            "p999_us": float(np.percentile(l_us, 99.9)) if l_us.size else None,
+            "p50_us": pct[0], "p99_us": pct[1], "p999_us": pct[2],
             "batches": int(stats["batches"]), "mean_batch": stats["mean_batch"], "correct": good,
             "transfer": "in place (kernels read the pinned host ring)" if stats["in_place"] else "copy engines",
             "clocks": {"before": clk_before, "after": clk_after}})
     top = points[-1]
     line = {
         "metric": METRIC, "value": top["sustained_dec_per_s"], "unit": UNIT, "n_gpus": dist.world,
-        "steps": len(points), "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+        "steps": len(points), "warmup": len(points), "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": WORKLOADS["serving"][3], "duration_s_per_point": duration, "ring_requests": period,
+        "config": {"workload": WORKLOADS["serving"][3], "duration_s_per_point": duration,
+                   "warmup_s_per_point": warm_s, "ring_requests": period,
                    "streams": 4, "max_batch": 16384, "budget_bytes": 256 << 20},
         "latency_us": {"p50": top["p50_us"], "p99": top["p99_us"], "p99.9": top["p999_us"]},
         "points": points,
         "correct": all(p["correct"] for p in points),
         "e2e": {"value": top["sustained_dec_per_s"], "unit": UNIT,
                 "h2d_bytes_per_step": int(woff[-1] * 8), "d2h_bytes_per_step": int(moff[-1]),
-                "api": "hqc_serve_run: ciphertexts copied from a pinned host ring per batch, m copied back"},
+                "api": "hqc_serve_run: " + top["transfer"] + "; m returned to host memory per batch"},
         "gpu_launches": int(sum(p["batches"] for p in points)),
         "clocks": top["clocks"]["after"],
     }
