@@ -182,8 +182,12 @@ __device__ __forceinline__ void load_supports(uint32_t* sup, const uint32_t* __r
 // secret positions.  (Lanes working on different entries at once, e.g. to
 // share out a few leftover words, would collide in banks depending on the
 // positions, so the strips cover the product with odd WPT and no tail.)
+// PREFETCH (validated supports only): the next pair of entries is read one
+// pass ahead, so a pass's window loads need not wait for its entries.
+// Worth it where a scheduler holds one or two warps (the latency teams);
+// elsewhere other warps hide that wait and the registers are scarcer.
 // ---------------------------------------------------------------------------
-template <int WPT, int W, bool MASKED>
+template <int WPT, int W, bool MASKED, bool PREFETCH = false>
 __device__ __forceinline__ void rot_xor_product(const uint32_t* u2, const uint32_t* sup, int w0,
                                                 uint32_t (&acc)[WPT]) {
 #pragma unroll
@@ -206,9 +210,19 @@ __device__ __forceinline__ void rot_xor_product(const uint32_t* u2, const uint32
   } else {
     // validated supports: two entries per pass so each accumulator update
     // is a single three-input XOR
+    uint4 en = *reinterpret_cast<const uint4*>(sup);
 #pragma unroll 1
     for (int t = 0; t + 1 < W; t += 2) {
-      const uint4 e = *reinterpret_cast<const uint4*>(sup + 2 * t);
+      uint4 e;
+      if constexpr (PREFETCH) {
+        // the last pass re-reads the last pair (an even index keeps the
+        // 16-byte load aligned and inside the W entries)
+        constexpr int LASTPAIR = (W - 2) & ~1;
+        e = en;
+        en = *reinterpret_cast<const uint4*>(sup + 2 * (t + 2 < LASTPAIR ? t + 2 : LASTPAIR));
+      } else {
+        e = *reinterpret_cast<const uint4*>(sup + 2 * t);
+      }
       const uint32_t* a0 = reinterpret_cast<const uint32_t*>(base + e.x);
       const uint32_t* a1 = reinterpret_cast<const uint32_t*>(base + e.z);
       uint32_t lo0 = a0[0], lo1 = a1[0];
@@ -963,7 +977,7 @@ __device__ __forceinline__ void product_rm_team(uint32_t* ws, int tid, const Tea
   load_supports<LV::n, LV::w, 32 * T>(sup, yrow, tid);
   build_doubled<LV::n, LV::W_u_pitch, TT::U2W, 32 * T>(u2, urow, tid, sync);
   uint32_t acc[WPT];
-  rot_xor_product<WPT, LV::w, MASKED>(u2, sup, tid * WPT, acc);
+  rot_xor_product<WPT, LV::w, MASKED, (T >= 4)>(u2, sup, tid * WPT, acc);
   const uint32_t* v32 = reinterpret_cast<const uint32_t*>(vrow);
 #pragma unroll
   for (int k = 0; k < WPT; k++) {
