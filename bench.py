@@ -448,6 +448,8 @@ def warm(fn, n, stream):
 
 def decrypt_kernel_name(level, count):
     """The kernel hqc_decrypt_batch_keyed runs for this batch (default shape)."""
+    if count <= 8:
+        return "k_decrypt_latency_cluster<%d,keyed,4,4>" % level
     if count <= 512:
         return "k_decrypt_latency<%d,keyed,4>" % level
     return ("k_decrypt_team<%d,keyed>" if level == 5 else "k_decrypt_fused<%d,keyed>") % level

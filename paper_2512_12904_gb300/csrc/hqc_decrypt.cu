@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <type_traits>
 
 #include "hqc_kernels.cuh"
@@ -55,6 +56,35 @@ static cudaError_t launch_latency(const DecArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// The cluster latency form (C blocks on C SMs per ciphertext) for batches
+// of at most max_count: a lone ciphertext finishes sooner when its product
+// and RM blocks are spread over four SMs' shared-memory bandwidth.
+template <int LEVEL> struct ClusterLatency {
+  static constexpr int C = 4;
+  static constexpr int64_t max_count = 8;
+};
+
+template <int LEVEL, bool KEYED>
+static cudaError_t launch_latency_cluster(const DecArgs& a, cudaStream_t st) {
+  constexpr int C = ClusterLatency<LEVEL>::C, T = LAT_TEAM;
+  constexpr size_t sm = GF_TABLE_BYTES + (size_t)ClusterShare<Level<LEVEL>, C, T>::WORDS * 4;
+  // above the default 48 KB: raise the kernel's limit once per device
+  static std::atomic<uint64_t> attr_done{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = 1ull << (dev & 63);
+  if (!(attr_done.load() & bit)) {
+    e = cudaFuncSetAttribute(k_decrypt_latency_cluster<LEVEL, KEYED, C, T>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    attr_done.fetch_or(bit);
+  }
+  const int64_t clusters = std::min<int64_t>(a.count, MAX_LATENCY_GRID / C);
+  k_decrypt_latency_cluster<LEVEL, KEYED, C, T><<<(unsigned)(clusters * C), 32 * T, sm, st>>>(a);
+  return cudaGetLastError();
+}
+
 template <int LEVEL, bool KEYED>
 static cudaError_t team_level(const DecArgs& a, cudaStream_t st, const LaunchCfg& cfg, bool launch, int* warps,
                               int* ctas, int* grid) {
@@ -93,7 +123,8 @@ static cudaError_t fused_level(const DecArgs& a, cudaStream_t st, const LaunchCf
   // a small batch with the default shape: a team of warps per ciphertext
   if (launch && a.count > 0 && cfg.warps_per_cta == 0 && cfg.ctas_per_sm == 0 &&
       a.count <= FusedLatencyMax<LEVEL>::count)
-    return launch_latency<LEVEL, KEYED>(a, st);
+    return a.count <= ClusterLatency<LEVEL>::max_count ? launch_latency_cluster<LEVEL, KEYED>(a, st)
+                                                       : launch_latency<LEVEL, KEYED>(a, st);
   if (UseTeam<LEVEL>::value) return team_level<LEVEL, KEYED>(a, st, cfg, launch, warps, ctas, grid);
   int nw = 0, c = 0, g = 0;
   size_t sm = 0;

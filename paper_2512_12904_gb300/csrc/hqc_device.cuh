@@ -45,7 +45,7 @@ __device__ __forceinline__ uint32_t gf_xtime(uint32_t a) {
 // The two tables packed as the 32-bit words one lane's column holds:
 // exp4[q] = exp[4q .. 4q+3] as bytes, log2[p] = log[2p], log[2p+1] as
 // halfwords.  Computed at compile time (GF(2^8) mod x^8+x^4+x^3+x^2+1,
-// alpha = x) into constant memory; a block copies each word into all 32
+// alpha = x) into global memory; a block copies each word into all 32
 // lane columns.
 struct GfPacked {
   uint32_t exp4[128];
@@ -68,17 +68,24 @@ struct GfPacked {
     for (int p = 0; p < 128; p++) log2[p] = lg[2 * p] | lg[2 * p + 1] << 16;
   }
 };
-static __constant__ GfPacked c_gf_packed = GfPacked();
+static __device__ const GfPacked g_gf_packed = GfPacked();
 
 // Fill both tables; called by every thread of the block, then
 // __syncthreads.  Word w of either table belongs to lane w mod 32 and holds
-// packed word w / 32 (a warp reads one constant word: a broadcast).
+// packed word w / 32, so each 128-byte row is one packed word 32 times.
+// Thread q of the first 256 reads packed word q (exp rows, then log rows)
+// with its own load -- all rows arrive after one memory round trip -- and
+// writes the row as eight 16-byte stores, in an order rotated by the
+// thread so the eight threads of a store phase hit eight different banks.
 __device__ inline void gf_tables_init(uint8_t* smem, int tid, int nthreads) {
-  uint32_t* ex32 = reinterpret_cast<uint32_t*>(smem);
-  uint32_t* lg32 = reinterpret_cast<uint32_t*>(smem + GF_EXP_BYTES);
-  for (int w = tid; w < 128 * 32; w += nthreads) {
-    ex32[w] = c_gf_packed.exp4[w >> 5];
-    lg32[w] = c_gf_packed.log2[w >> 5];
+  const uint32_t* packed = reinterpret_cast<const uint32_t*>(&g_gf_packed);
+  uint4* rows = reinterpret_cast<uint4*>(smem);  // 128 exp rows, then 128 log rows
+  static_assert(GF_EXP_BYTES == 128 * 128 && sizeof(GfPacked) == 256 * 4, "table layout");
+  for (int q = tid; q < 256; q += nthreads) {
+    const uint32_t w = __ldg(packed + q);
+    const uint4 v = make_uint4(w, w, w, w);
+#pragma unroll
+    for (int j = 0; j < 8; j++) rows[8 * q + ((j + q) & 7)] = v;
   }
 }
 

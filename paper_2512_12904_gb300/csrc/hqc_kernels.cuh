@@ -234,6 +234,111 @@ __global__ void __launch_bounds__(32 * T, 4) k_decrypt_latency(DecArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Cluster latency form: the C blocks of a thread-block cluster decode ONE
+// ciphertext together.  With four warps on one SM, the product of one
+// HQC-5 ciphertext needs 131 x 16 x 4 shared-memory wavefronts, about 4 us
+// of that SM's shared-memory bandwidth alone; split over C SMs it takes a
+// C-th of that.  Block c of the cluster owns RM blocks [b0(c), b0(c + 1)):
+// it builds the whole doubled operand, computes the product words of those
+// blocks (strips of WPT words over its 32 T lanes, starting at its first
+// word), XORs v, decodes its RM blocks in one pass of lane pairs, and
+// stores the bytes into block 0's shared memory (distributed shared
+// memory).  After a cluster barrier, block 0's team runs the RS stage.
+// Only block 0 fills the GF tables.  Every block of a cluster takes the
+// same items in the same order and meets the same two barriers per item
+// (hardware barriers, no spin): A (block 0 has finished reading the
+// previous item's bytes, and every block is running before the first
+// remote store) and B (every byte is in block 0's memory).
+// ---------------------------------------------------------------------------
+template <class LV, int C, int T>
+struct ClusterShare {
+  static constexpr int NW = LV::n2 / 32;     // words per RM block
+  static constexpr int MAXB = cdiv(LV::n1, C);  // most RM blocks per block
+  static constexpr int WPT = odd_at_least(cdiv(MAXB * NW, 32 * T));
+  __host__ __device__ static constexpr int b0(int c) { return c * LV::n1 / C; }
+  // product reads reach word w0 + WPT + (n >> 5) for the last strip
+  static constexpr int U2W =
+      round_up(cmax(cdiv(2 * LV::n, 32), b0(C - 1) * NW + 32 * T * WPT + (LV::n >> 5) + 1), 4);
+  static constexpr int RB = cdiv(LV::n1, 4) * 4;
+  static constexpr int WORDS = round_up(U2W + LV::WP + RB / 4, 4);
+  static_assert(LV::n2 % 32 == 0 && MAXB <= 16 * T, "one pass of lane pairs covers a block's RM share");
+  static_assert(rs_team_scratch<T>() <= U2W && U2W % 4 == 0 && LV::WP % 4 == 0, "RS scratch fits; alignment");
+};
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+// one byte into the same shared-memory offset of block `rank` of the cluster
+__device__ __forceinline__ void st_cluster_u8(const uint8_t* local, uint32_t rank, uint32_t v) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(local);
+  uint32_t ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+  asm volatile("st.shared::cluster.u8 [%0], %1;" ::"r"(ra), "r"(v) : "memory");
+}
+
+template <int LEVEL, bool KEYED, int C, int T>
+__global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(32 * T, 1) k_decrypt_latency_cluster(DecArgs a) {
+  using LV = Level<LEVEL>;
+  using CS = ClusterShare<LV, C, T>;
+  extern __shared__ __align__(16) uint8_t smem[];
+  const uint32_t rank = cluster_ctarank();
+  if (rank == 0) gf_tables_init(smem, threadIdx.x, blockDim.x);
+  __syncthreads();
+  const int tid = threadIdx.x, lane = tid & 31, wt = tid >> 5;
+  const GF gf(smem, lane);
+  uint32_t* ws = reinterpret_cast<uint32_t*>(smem + GF_TABLE_BYTES);
+  uint32_t* u2 = ws;
+  uint32_t* sup = ws + CS::U2W;
+  uint8_t* rbuf = reinterpret_cast<uint8_t*>(sup + LV::WP);
+  const TeamSync sync{1u, 32u * T};
+  const int b0 = CS::b0((int)rank), b1 = CS::b0((int)rank + 1);
+  const int w_lo = b0 * CS::NW, w_hi = b1 * CS::NW;
+  const int w0 = w_lo + tid * CS::WPT;
+  const int64_t nclusters = gridDim.x / C;
+  for (int64_t it = blockIdx.x / C; it < a.count; it += nclusters) {
+    cluster_arrive();  // A
+    bool ok = true;
+    const uint32_t* y;
+    if (KEYED) {
+      // an index outside [0, nkeys) decodes key 0's supports and stores nothing
+      const uint32_t ki = (uint32_t)__ldg(a.key_idx + it);
+      ok = ki < (uint64_t)a.nkeys;
+      y = a.y + (ok ? (int64_t)ki : 0) * LV::w;
+    } else {
+      y = a.y + it * LV::w;
+    }
+    load_supports<LV::n, LV::w, 32 * T>(sup, y, tid);
+    build_doubled<LV::n, LV::W_u_pitch, CS::U2W, 32 * T>(u2, a.u + it * LV::W_u_pitch, tid, sync);
+    uint32_t acc[CS::WPT];
+    rot_xor_product<CS::WPT, LV::w, !KEYED, true>(u2, sup, w0, acc);
+    const uint32_t* v32 = reinterpret_cast<const uint32_t*>(a.v + it * LV::W_v);
+#pragma unroll
+    for (int k = 0; k < CS::WPT; k++)
+      if (w0 + k < w_hi) acc[k] ^= __ldcs(v32 + w0 + k);
+    sync();
+#pragma unroll
+    for (int k = 0; k < CS::WPT; k++)
+      if (w0 + k < w_hi) u2[w0 + k] = acc[k];
+    sync();
+    const int j = b0 + (tid >> 1);
+    const int jj = j < b1 ? j : b1 - 1;
+    const uint32_t byte = rm_decode_pair<LV::mult>(u2 + jj * CS::NW, tid & 1);
+    cluster_wait();  // A
+    if (j < b1 && (tid & 1) == 0) st_cluster_u8(rbuf + j, 0u, byte);
+    cluster_arrive();  // B
+    cluster_wait();
+    if (rank == 0) {
+      rs_decode_team<LV, T>(gf, ws, rbuf, wt, lane, sync, ok, a.m + it * LV::k);
+      sync();  // the RS scratch lives in u2: the next item rebuilds it
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Items of one level taken from a mixed list
 // ---------------------------------------------------------------------------
 // Whether item `it` of a one-level list names valid rows, key and m bytes.

@@ -149,6 +149,33 @@ def test_latency_form_at_its_limit_and_past_it(hqc, level):
     keys.free()
 
 
+@pytest.mark.parametrize("level", LEVELS)
+def test_cluster_latency_form(hqc, level):
+    """Batches of at most 8 run the cluster form (four blocks per ciphertext
+    sharing the product and the RM blocks, block 0 decoding RS): literal
+    adversarial rows (beyond-delta v, all-zero and all-one u, garbage
+    padding, repeated and out-of-range supports) in batches of 1, 5 and 8,
+    and keyed honest batches of 1, 8 (with an out-of-range key index,
+    skipped) and 9 (the one-block team form), all against the oracle."""
+    P, au, av, ay = adversarial(level, tag=40 + level)
+    want = oracle_dumps(level, au, av, ay)["m"]
+    for lo, hi in ((0, 1), (1, 6), (6, 14)):
+        got = host(hqc.hqc_decrypt_batch(level, u64(au[lo:hi]), u64(av[lo:hi]), i32(ay[lo:hi])))
+        assert (got == want[lo:hi]).all(), (lo, hi)
+    wl = honest(level, 3, 9, first_ct=16000, tag=27)
+    keys = hqc.Keyset(level, wl.y)
+    kidx = wl.key_idx.astype(np.int32).copy()
+    kidx[4] = 3  # == nkeys: skipped
+    want_k = wl.m.copy()
+    want_k[4] = 0xA5
+    for cnt in (1, 8, 9):
+        out = torch.full((cnt, wl.P.k), 0xA5, dtype=torch.uint8, device="cuda")
+        got = host(hqc.hqc_decrypt_batch_keyed(level, u64(wl.u[:cnt]), u64(wl.v[:cnt]), keys, dev(kidx[:cnt]),
+                                               m_out=out))
+        assert (got == want_k[:cnt]).all(), cnt
+    keys.free()
+
+
 BAD_KEY_ROWS = (3, 40, 41, 69)
 
 
