@@ -128,6 +128,27 @@ int hqc_decrypt_batch_staged(int level, int64_t count, const uint64_t* u, const 
                              const hqc_keyset_t* keys, const int32_t* key_idx, void* workspace,
                              size_t workspace_bytes, uint8_t* m_out, void* stream);
 
+/* S5-S7 alone: decode the n1 duplicated RM(1,7) blocks of each of count
+ * received words w [count][W_v] (device, 64-bit words, 16-byte aligned;
+ * block j of word i is bits [j n2, (j + 1) n2) of row i) into r_out
+ * [count][n1] bytes (device): byte = a* + 128 [F(a*) < 0] with F the
+ * Walsh-Hadamard transform of the copy counts and a* = argmax |F|, ties
+ * to the smaller a (Sec. II-A; the decoder inside every decryption form).
+ * use_tensor_cores = 0 runs the register butterflies of the per-stage
+ * form; 1 runs the same transform as one dense product on the tensor
+ * cores (tcgen05, fp16 operands, fp32 accumulators in tensor memory, exact
+ * for these small integers), a measured alternative.  Both give identical
+ * bytes.  Asynchronous on stream; HQC_EINVAL on a bad level, count < 0 or a
+ * NULL or misaligned pointer with count > 0. */
+int hqc_rm_decode_batch(int level, int64_t count, const uint64_t* w, uint8_t* r_out, int use_tensor_cores,
+                        void* stream);
+/* Timed-out waits of the tensor-core RM form since the last call
+ * (synchronises the current device; reads and clears a device counter).
+ * Each wait for the tensor core is bounded: a timeout stops that block,
+ * leaves its remaining bytes unwritten and is counted here.  0 in normal
+ * operation. */
+int hqc_rm_tc_timeouts(int* out);
+
 /* Same per-stage decryption, for callers that cannot allocate device memory
  * at all (a framework that owns every device byte through its own
  * allocator, a latency-critical path where cudaMalloc could block or fail

@@ -23,7 +23,7 @@ __all__ = [
     "hqc_keys_register", "hqc_decrypt_batch_keyed", "hqc_staged_workspace_bytes",
     "hqc_decrypt_batch_staged", "hqc_decrypt_batch_staged_noalloc", "hqc_decrypt_debug", "hqc_mixed_workspace_bytes",
     "hqc_decrypt_mixed", "hqc_set_launch_config", "hqc_get_launch_shape", "hqc_keygen_batch",
-    "hqc_encrypt_batch", "hqc_count_bad_key_idx", "LEVELS", "Plan", "PLAN_VARIANTS", "PLAN_FORMS", "hqc_plan_create_keyed", "hqc_plan_create_mixed", "hqc_serve_run",
+    "hqc_encrypt_batch", "hqc_count_bad_key_idx", "hqc_rm_decode_batch", "hqc_rm_tc_timeouts", "LEVELS", "Plan", "PLAN_VARIANTS", "PLAN_FORMS", "hqc_plan_create_keyed", "hqc_plan_create_mixed", "hqc_serve_run",
     "SERVE_STATUS", "hqc_decrypt_host_keyed", "hqc_host_workspace_bytes", "hqc_shake256_batch",
     "hqc_kem_keygen", "hqc_kem_workspace_bytes", "hqc_kem_encaps", "hqc_kem_decaps",
     "hqc_kem_host_workspace_bytes", "hqc_kem_decaps_host", "hqc_mixed_host_workspace_bytes",
@@ -110,6 +110,8 @@ def load(build_if_missing: bool = True):
             "hqc_kem_decaps_host": (i32, [i32, i64, P, P, P, P, P, P, P, P, P, P, i64, P, sz, P]),
             "hqc_keygen_batch": (i32, [i32, i64, P, P, P, P, P]),
             "hqc_count_bad_key_idx": (i32, [i64, P, i64, P, P]),
+            "hqc_rm_decode_batch": (i32, [i32, i64, P, P, i32, P]),
+            "hqc_rm_tc_timeouts": (i32, [P]),
             "hqc_plan_describe": (i32, [P, P, sz]),
             "hqc_plan_create_keyed_fixed": (i32, [i32, i64, P, P, P, P, P, i32, P, P, P]),
             "hqc_plan_create_mixed_fixed": (i32, [i64, P, P, i64, P, P, i64, i32, P, P, P, P, P]),
@@ -268,6 +270,28 @@ def hqc_count_bad_key_idx(key_idx, nkeys: int, stream=None) -> int:
     if stream is not None:
         stream.synchronize()
     return int(out.item()) & 0xFFFFFFFF
+
+
+def hqc_rm_decode_batch(level, w, r_out=None, tensor_cores=False, stream=None):
+    """S5-S7 alone: the n1 RM bytes of each received word of w (int64
+    [count, W_v], device), by the register butterflies or, with
+    tensor_cores, by the tensor-core product (hqc_rm_decode_batch)."""
+    torch = _torch()
+    P = hqc_get_params(level)
+    cnt = w.shape[0]
+    if r_out is None:
+        r_out = torch.zeros((cnt, P.n1), dtype=torch.uint8, device=w.device)
+    _check(load().hqc_rm_decode_batch(level, cnt, _dev_ptr(w, torch.int64, (cnt, P.W_v), "w"),
+                                      _dev_ptr(r_out, torch.uint8, (cnt, P.n1), "r_out"), 1 if tensor_cores else 0,
+                                      _stream(stream)))
+    return r_out
+
+
+def hqc_rm_tc_timeouts() -> int:
+    """Timed-out tensor-core waits since the last call (0 normally)."""
+    out = ctypes.c_int(0)
+    _check(load().hqc_rm_tc_timeouts(ctypes.byref(out)))
+    return out.value
 
 
 def hqc_staged_workspace_bytes(level: int, count: int) -> int:

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libhqc_gb300.so")
 PEAKS_LIB = os.path.join(BUILD, "libhqc_peaks.so")
-SOURCES = ["hqc_decrypt.cu", "hqc_stage.cu", "hqc_tune.cu", "hqc_encrypt.cu", "hqc_abi.cu", "hqc_noalloc.cu", "hqc_plan.cu", "hqc_serve.cu", "hqc_host.cu", "hqc_kem.cu"]
+SOURCES = ["hqc_decrypt.cu", "hqc_stage.cu", "hqc_tune.cu", "hqc_encrypt.cu", "hqc_abi.cu", "hqc_noalloc.cu", "hqc_plan.cu", "hqc_serve.cu", "hqc_host.cu", "hqc_kem.cu", "hqc_rm_tc.cu"]
 PEAKS_SOURCES = ["hqc_peaks.cu"]
 HEADERS = ["hqc_params.cuh", "hqc_device.cuh", "hqc_kernels.cuh", "hqc_internal.h", "hqc_keccak.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

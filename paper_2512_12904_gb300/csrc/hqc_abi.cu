@@ -214,6 +214,29 @@ int hqc_count_bad_key_idx(int64_t count, const int32_t* key_idx, int64_t nkeys, 
   return launch_result(cudaGetLastError(), "count launch");
 }
 
+int hqc_rm_decode_batch(int level, int64_t count, const uint64_t* w, uint8_t* r_out, int use_tensor_cores,
+                        void* stream) {
+  g_err.clear();
+  hqc_params_t p{};
+  if (!params_of(level, &p)) return fail(HQC_EINVAL, "level must be 1, 3 or 5");
+  if (count < 0) return fail(HQC_EINVAL, "count must be >= 0");
+  if (count == 0) return HQC_OK;
+  if (!w || !aligned(w, 16)) return fail(HQC_EINVAL, "w must be a non-NULL 16-byte aligned device pointer");
+  if (!r_out) return fail(HQC_EINVAL, "r_out must be a non-NULL device pointer");
+  return launch_result(hqc::launch_rm_decode(level, count, w, r_out, use_tensor_cores != 0, (cudaStream_t)stream),
+                       "RM decode launch");
+}
+
+int hqc_rm_tc_timeouts(int* out) {
+  g_err.clear();
+  if (!out) return fail(HQC_EINVAL, "out must be a non-NULL host pointer");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "synchronising the device");
+  e = hqc::rm_tc_take_timeouts(out);
+  if (e != cudaSuccess) return cuda_fail(e, "reading the timeout counter");
+  return HQC_OK;
+}
+
 size_t hqc_staged_workspace_bytes(int level, int64_t count) {
   hqc_params_t p{};
   if (!params_of(level, &p) || count <= 0) return 0;

@@ -72,6 +72,12 @@ void set_last_error(const char* msg);  // message returned by hqc_last_error() o
 cudaError_t launch_fused(int level, bool keyed, const DecArgs& a, cudaStream_t st, const LaunchCfg& cfg);
 cudaError_t launch_staged(int level, bool keyed, const DecArgs& a, uint64_t* w_ws, uint8_t* r_ws, cudaStream_t st);
 cudaError_t launch_debug(int level, const DecArgs& a, const DebugArgs& d, cudaStream_t st);
+// S5-S7 alone on [count][W_v] words: the register butterflies (k_stage_rm)
+// or the tensor-core product (hqc_rm_tc.cu); and the tensor-core form's
+// count of timed-out waits since the last call (read and cleared).
+cudaError_t launch_rm_decode(int level, int64_t count, const uint64_t* w, uint8_t* r, bool tensor_cores,
+                             cudaStream_t st);
+cudaError_t rm_tc_take_timeouts(int* out);
 cudaError_t launch_mixed(const MixedArgs& a, cudaStream_t st, const LaunchCfg& cfg);
 // Latency form of the mixed kernel: a team of warps per item, one item per
 // team at a time, for batches of at most MIXED_LATENCY_MAX items.
