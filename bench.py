@@ -550,6 +550,10 @@ def bench_single(ctx, wl_name, full):
     if full:
         line["e2e"] = e2e_single(ctx, level, count, P, keys, u_d, v_d, k_d, m_ref, stream)
         line["correct"] = line["correct"] and line["e2e"].pop("correct")
+    if full and count > 512:
+        line["rm_stage"] = rm_stage_forms(ctx, level, count, stream)
+        line["correct"] = (line["correct"] and line["rm_stage"]["equal"]
+                           and line["rm_stage"]["tensor_core_timeouts"] == 0)
     if count <= 512:
         line["one_ciphertext_us"] = one_ciphertext_latency(ctx, stream)
         line["correct"] = line["correct"] and all(x["correct"] for x in line["one_ciphertext_us"].values())
@@ -582,6 +586,30 @@ def one_ciphertext_latency(ctx, stream, reps=200):
                            "kernel": decrypt_kernel_name(level, 1)}
         keys.free()
     return out
+
+
+def rm_stage_forms(ctx, level, count, stream, reps=10):
+    """S5-S7 alone on count received words (seeded random bits; the decoders'
+    work does not depend on the bits): the register butterflies of the
+    per-stage form against the tensor-core product (tcgen05), median device
+    time of `reps` launches each, and whether their bytes agree."""
+    import torch
+    import synth
+    hqc = ctx.hqc
+    P = hqc.hqc_get_params(level)
+    w = torch.from_numpy(synth.words(count * P.W_v, tag=990 + level).view(np.int64).reshape(count, P.W_v)).to(
+        ctx.device)
+    out, times = {}, {}
+    for tc in (False, True):
+        r = torch.zeros((count, P.n1), dtype=torch.uint8, device=ctx.device)
+        fn = lambda: hqc.hqc_rm_decode_batch(level, w, r_out=r, tensor_cores=tc, stream=stream)
+        warm(fn, 3, stream)
+        _, per, _ = timed_steps(fn, reps, stream, ctx.dist)
+        out[tc], times[tc] = r, 1e3 * pct(per, 50)
+    return {"rm_blocks": count * P.n1, "butterflies_us": times[False], "tensor_cores_us": times[True],
+            "equal": bool(torch.equal(out[False], out[True])), "tensor_core_timeouts": hqc.hqc_rm_tc_timeouts(),
+            "what": "hqc_rm_decode_batch: k_stage_rm (register butterflies) vs k_rm_tc (tcgen05.mma kind::f16, "
+                    "fp32 accumulators in tensor memory); median device time per launch"}
 
 
 def e2e_single(ctx, level, count, P, keys, u_d, v_d, k_d, m_ref, stream):
