@@ -231,3 +231,20 @@ def test_serving_rejects_rings_whose_offsets_decrease_without_a_gpu():
     assert call(np.array([0, 555, 1109], np.int64), np.array([0, 16, 32], np.int64), transfer=2) == -1
     assert b"even word offsets" in lib.hqc_last_error()
     assert call(np.array([0, 554, 1108], np.int64), np.array([0, 16, 32], np.int64), transfer=3) == -1
+
+
+def test_rm_decode_batch_argument_checks():
+    """hqc_rm_decode_batch rejects a bad level, a negative count and a NULL
+    or misaligned w before touching the device; an empty batch is a no-op;
+    hqc_rm_tc_timeouts rejects a NULL output."""
+    lib = hqc.load()
+    buf = ctypes.create_string_buffer(64)
+    p16 = ctypes.c_void_p((ctypes.addressof(buf) + 15) & ~15)
+    odd = ctypes.c_void_p(p16.value + 8)
+    assert lib.hqc_rm_decode_batch(2, 1, p16, p16, 0, None) == hqc.HQC_EINVAL
+    assert lib.hqc_rm_decode_batch(1, -1, p16, p16, 1, None) == hqc.HQC_EINVAL
+    assert lib.hqc_rm_decode_batch(3, 1, None, p16, 1, None) == hqc.HQC_EINVAL
+    assert lib.hqc_rm_decode_batch(5, 1, odd, p16, 0, None) == hqc.HQC_EINVAL
+    assert lib.hqc_rm_decode_batch(1, 1, p16, None, 1, None) == hqc.HQC_EINVAL
+    assert lib.hqc_rm_decode_batch(1, 0, None, None, 1, None) == hqc.HQC_OK
+    assert lib.hqc_rm_tc_timeouts(None) == hqc.HQC_EINVAL
