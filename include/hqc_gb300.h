@@ -292,6 +292,17 @@ typedef struct hqc_debug_dump_s {
 int hqc_decrypt_debug(int level, int64_t count, const uint64_t* u, const uint64_t* v, const uint32_t* y,
                       const hqc_debug_dump_t* dump, uint8_t* m_out, void* stream);
 
+/* The latency forms' own intermediates: decrypt with literal supports
+ * through form 0 (a block of four warps per ciphertext, k_decrypt_latency)
+ * or form 1 (a cluster of four blocks per ciphertext,
+ * k_decrypt_latency_cluster), whatever the count, and write each
+ * ciphertext's RM bytes (dump->r), syndromes (dump->S) and Lambda
+ * (dump->lam) as the block that ran RS holds them.  dump points to HOST
+ * memory holding device pointers; r, S and lam must be non-NULL, the other
+ * fields are ignored.  HQC_EINVAL on a bad form or pointer. */
+int hqc_decrypt_debug_team(int level, int form, int64_t count, const uint64_t* u, const uint64_t* v, const uint32_t* y,
+                           const hqc_debug_dump_t* dump, uint8_t* m_out, void* stream);
+
 /* Mixed-level batch in one persistent launch.  items: device array of
  * `count` work items; u and v rows are read from `arena` (device, 64-bit
  * words) at the given word offsets (u_off even), m is written to

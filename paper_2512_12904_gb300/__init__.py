@@ -23,7 +23,7 @@ __all__ = [
     "hqc_keys_register", "hqc_decrypt_batch_keyed", "hqc_staged_workspace_bytes",
     "hqc_decrypt_batch_staged", "hqc_decrypt_batch_staged_noalloc", "hqc_decrypt_debug", "hqc_mixed_workspace_bytes",
     "hqc_decrypt_mixed", "hqc_set_launch_config", "hqc_get_launch_shape", "hqc_keygen_batch",
-    "hqc_encrypt_batch", "hqc_count_bad_key_idx", "hqc_rm_decode_batch", "hqc_rm_tc_timeouts", "LEVELS", "Plan", "PLAN_VARIANTS", "PLAN_FORMS", "hqc_plan_create_keyed", "hqc_plan_create_mixed", "hqc_serve_run",
+    "hqc_encrypt_batch", "hqc_count_bad_key_idx", "hqc_rm_decode_batch", "hqc_rm_tc_timeouts", "hqc_decrypt_debug_team", "LEVELS", "Plan", "PLAN_VARIANTS", "PLAN_FORMS", "hqc_plan_create_keyed", "hqc_plan_create_mixed", "hqc_serve_run",
     "SERVE_STATUS", "hqc_decrypt_host_keyed", "hqc_host_workspace_bytes", "hqc_shake256_batch",
     "hqc_kem_keygen", "hqc_kem_workspace_bytes", "hqc_kem_encaps", "hqc_kem_decaps",
     "hqc_kem_host_workspace_bytes", "hqc_kem_decaps_host", "hqc_mixed_host_workspace_bytes",
@@ -112,6 +112,7 @@ def load(build_if_missing: bool = True):
             "hqc_count_bad_key_idx": (i32, [i64, P, i64, P, P]),
             "hqc_rm_decode_batch": (i32, [i32, i64, P, P, i32, P]),
             "hqc_rm_tc_timeouts": (i32, [P]),
+            "hqc_decrypt_debug_team": (i32, [i32, i32, i64, P, P, P, P, P, P]),
             "hqc_plan_describe": (i32, [P, P, sz]),
             "hqc_plan_create_keyed_fixed": (i32, [i32, i64, P, P, P, P, P, i32, P, P, P]),
             "hqc_plan_create_mixed_fixed": (i32, [i64, P, P, i64, P, P, i64, i32, P, P, P, P, P]),
@@ -382,6 +383,29 @@ def hqc_decrypt_debug(level, u, v, y, stream=None):
                                     _dev_ptr(v, torch.int64, (cnt, P.W_v), "v"),
                                     _dev_ptr(y, torch.int32, (cnt, P.w), "y"), ctypes.byref(d),
                                     _dev_ptr(out["m"], torch.uint8, (cnt, P.k), "m"), _stream(stream)))
+    return out
+
+
+def hqc_decrypt_debug_team(level, u, v, y, form=0, stream=None):
+    """The latency forms' intermediates (form 0: four-warp team per
+    ciphertext, 1: cluster of four blocks): r, S, lam and m per ciphertext."""
+    torch = _torch()
+    P = hqc_get_params(level)
+    u, v = _as_u64(u), _as_u64(v)
+    y = y.view(torch.int32) if y.dtype == torch.uint32 else y
+    cnt = u.shape[0]
+    dev = u.device
+    nr = 2 * P.delta
+    out = dict(r=torch.zeros((cnt, P.n1), dtype=torch.uint8, device=dev),
+               S=torch.zeros((cnt, nr), dtype=torch.uint8, device=dev),
+               lam=torch.zeros((cnt, nr + 1), dtype=torch.uint8, device=dev),
+               m=torch.zeros((cnt, P.k), dtype=torch.uint8, device=dev))
+    ptrs = {f: ctypes.c_void_p(out[f].data_ptr()) if f in out else ctypes.c_void_p(0) for f, _ in _Dump._fields_}
+    d = _Dump(*[ptrs[f] for f, _ in _Dump._fields_])
+    _check(load().hqc_decrypt_debug_team(level, int(form), cnt, _dev_ptr(u, torch.int64, (cnt, P.W_u_pitch), "u"),
+                                         _dev_ptr(v, torch.int64, (cnt, P.W_v), "v"),
+                                         _dev_ptr(y, torch.int32, (cnt, P.w), "y"), ctypes.byref(d),
+                                         _dev_ptr(out["m"], torch.uint8, (cnt, P.k), "m"), _stream(stream)))
     return out
 
 

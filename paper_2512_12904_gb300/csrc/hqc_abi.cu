@@ -294,6 +294,25 @@ int hqc_decrypt_debug(int level, int64_t count, const uint64_t* u, const uint64_
   return launch_result(hqc::launch_debug(level, a, d, (cudaStream_t)stream), "debug decrypt launch");
 }
 
+int hqc_decrypt_debug_team(int level, int form, int64_t count, const uint64_t* u, const uint64_t* v, const uint32_t* y,
+                           const hqc_debug_dump_t* dump, uint8_t* m_out, void* stream) {
+  hqc_params_t p{};
+  int rc = check_common(level, count, u, v, m_out, &p);
+  if (rc != HQC_OK) return rc;
+  if (form != 0 && form != 1) return fail(HQC_EINVAL, "form must be 0 (four-warp team) or 1 (cluster)");
+  if (count == 0) return HQC_OK;
+  if (!y || !dump) return fail(HQC_EINVAL, "y and dump must be non-NULL");
+  if (!dump->r || !dump->S || !dump->lam) return fail(HQC_EINVAL, "dump->r, dump->S and dump->lam must be non-NULL");
+  hqc::DecArgs a;
+  a.count = count;
+  a.u = u;
+  a.v = v;
+  a.y = y;
+  a.m = m_out;
+  hqc::DebugArgs d{nullptr, nullptr, dump->r, dump->S, dump->lam, nullptr, nullptr, nullptr, nullptr, nullptr};
+  return launch_result(hqc::launch_debug_team(level, form, a, d, (cudaStream_t)stream), "debug latency launch");
+}
+
 size_t hqc_mixed_workspace_bytes(void) { return 256; }
 
 int hqc_decrypt_mixed(int64_t count, const hqc_item_t* items, const uint64_t* arena, int64_t arena_words,

@@ -853,6 +853,11 @@ __device__ __forceinline__ uint32_t rs_bm_lookahead(const GF& gf, const uint8_t*
 template <int T>
 __host__ __device__ constexpr int rs_team_scratch() { return 176 + 40 * T + 256; }
 
+// Where rs_decode_team keeps log S (indices [-64, 64), log-zero below 0)
+// and log Lambda in its scratch; the debug path reads them back from there.
+__device__ __forceinline__ uint16_t* rs_team_logS(uint32_t* rs) { return reinterpret_cast<uint16_t*>(rs + 48) + 64; }
+__device__ __forceinline__ uint16_t* rs_team_logLam(uint32_t* rs) { return reinterpret_cast<uint16_t*>(rs + 112); }
+
 template <class LV, int T>
 __device__ __forceinline__ void rs_decode_team(const GF& gf, uint32_t* rs, const uint8_t* r, int wt, int lane,
                                                const TeamSync& sync, bool active, uint8_t* __restrict__ m_out) {
@@ -860,8 +865,8 @@ __device__ __forceinline__ void rs_decode_team(const GF& gf, uint32_t* rs, const
   static_assert(n1 <= 96 && CAP <= 64 && k <= 32, "RS scratch sizes");
   const int tid = wt * 32 + lane;
   uint16_t* logr = reinterpret_cast<uint16_t*>(rs);
-  uint16_t* logS = reinterpret_cast<uint16_t*>(rs + 48) + 64;
-  uint16_t* logLam = reinterpret_cast<uint16_t*>(rs + 112);
+  uint16_t* logS = rs_team_logS(rs);
+  uint16_t* logLam = rs_team_logLam(rs);
   uint16_t* logOm = reinterpret_cast<uint16_t*>(rs + 144);
   uint8_t* partS = reinterpret_cast<uint8_t*>(rs + 176);           // [T][64] partial syndromes
   uint8_t* partC = reinterpret_cast<uint8_t*>(rs + 176 + 16 * T);  // [T][3][32] partial Chien sums
@@ -981,6 +986,8 @@ struct Team {
   static constexpr int U2W = round_up(cmax(cdiv(2 * LV::n, 32), 32 * T * WPT2 + (LV::n >> 5) + 1), 4);
   static constexpr int RB = cdiv(LV::n1, 4) * 4;  // bytes per stored RM word
   static constexpr int WORDS = round_up(U2W + LV::WP + NI * (RB / 4), 4);  // shared words per team
+  // the RM bytes of the team's NI ciphertexts, RB bytes each, behind u2 and the supports
+  __device__ static uint8_t* rbuf(uint32_t* ws) { return reinterpret_cast<uint8_t*>(ws + U2W + LV::WP); }
   static_assert(NI >= 1 && NI <= T, "one RS word per warp at most");
   static_assert(NI * RS_SCRATCH <= U2W && rs_team_scratch<T>() <= U2W, "the RS scratches fit in u2");
   static_assert(U2W % 4 == 0 && LV::WP % 4 == 0 && WORDS % 4 == 0, "16-byte alignment");
@@ -1023,7 +1030,7 @@ __device__ __forceinline__ void decrypt_team(const GF& gf, uint32_t* ws, int wt,
                                              const Rows& rows) {
   using TT = Team<LV, T, NI>;
   const int tid = (wt << 5) | lane;
-  uint8_t* rbuf = reinterpret_cast<uint8_t*>(ws + TT::U2W + LV::WP);
+  uint8_t* rbuf = TT::rbuf(ws);
   const uint64_t* u;
   const uint64_t* v;
   const uint32_t* y;

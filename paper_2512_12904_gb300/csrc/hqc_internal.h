@@ -72,6 +72,9 @@ void set_last_error(const char* msg);  // message returned by hqc_last_error() o
 cudaError_t launch_fused(int level, bool keyed, const DecArgs& a, cudaStream_t st, const LaunchCfg& cfg);
 cudaError_t launch_staged(int level, bool keyed, const DecArgs& a, uint64_t* w_ws, uint8_t* r_ws, cudaStream_t st);
 cudaError_t launch_debug(int level, const DecArgs& a, const DebugArgs& d, cudaStream_t st);
+// The latency forms (form 0: a four-warp team per item, 1: a cluster of four
+// blocks) with literal supports, dumping each item's r, S and lam to d.
+cudaError_t launch_debug_team(int level, int form, const DecArgs& a, const DebugArgs& d, cudaStream_t st);
 // S5-S7 alone on [count][W_v] words: the register butterflies (k_stage_rm)
 // or the tensor-core product (hqc_rm_tc.cu); and the tensor-core form's
 // count of timed-out waits since the last call (read and cleared).

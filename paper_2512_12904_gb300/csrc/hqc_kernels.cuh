@@ -202,10 +202,12 @@ __global__ void __launch_bounds__(32 * T, 4) k_decrypt_mixed_team(MixedArgs a) {
 
 // The same latency form for a batch of one level (literal or keyed
 // supports): block b decodes ciphertexts b, b + grid, ... with its team.
-template <int LEVEL, bool KEYED, int T>
-__global__ void __launch_bounds__(32 * T, 4) k_decrypt_latency(DecArgs a) {
+// after(it, ws) runs once per item, after its decryption, on the whole
+// block: the kernel passes a no-op; the debug path reads the team's RM
+// bytes and RS intermediates back from shared memory there.
+template <int LEVEL, bool KEYED, int T, class After>
+__device__ __forceinline__ void latency_items(const DecArgs& a, uint8_t* smem, const After& after) {
   using LV = Level<LEVEL>;
-  extern __shared__ __align__(16) uint8_t smem[];
   gf_tables_init(smem, threadIdx.x, blockDim.x);
   __syncthreads();
   const int lane = threadIdx.x & 31, wt = threadIdx.x >> 5;
@@ -230,7 +232,14 @@ __global__ void __launch_bounds__(32 * T, 4) k_decrypt_latency(DecArgs a) {
       return ok;
     };
     decrypt_team<LV, !KEYED, T, 1>(gf, ws, wt, lane, sync, rows);
+    after(it, ws);
   }
+}
+
+template <int LEVEL, bool KEYED, int T>
+__global__ void __launch_bounds__(32 * T, 4) k_decrypt_latency(DecArgs a) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  latency_items<LEVEL, KEYED, T>(a, smem, [](int64_t, uint32_t*) {});
 }
 
 // ---------------------------------------------------------------------------
@@ -280,11 +289,12 @@ __device__ __forceinline__ void st_cluster_u8(const uint8_t* local, uint32_t ran
   asm volatile("st.shared::cluster.u8 [%0], %1;" ::"r"(ra), "r"(v) : "memory");
 }
 
-template <int LEVEL, bool KEYED, int C, int T>
-__global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(32 * T, 1) k_decrypt_latency_cluster(DecArgs a) {
+// after(it, ws, rbuf) runs on block 0 once per item, after RS, as in
+// latency_items.
+template <int LEVEL, bool KEYED, int C, int T, class After>
+__device__ __forceinline__ void cluster_items(const DecArgs& a, uint8_t* smem, const After& after) {
   using LV = Level<LEVEL>;
   using CS = ClusterShare<LV, C, T>;
-  extern __shared__ __align__(16) uint8_t smem[];
   const uint32_t rank = cluster_ctarank();
   if (rank == 0) gf_tables_init(smem, threadIdx.x, blockDim.x);
   __syncthreads();
@@ -334,8 +344,15 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(32 * T, 1) k_decrypt
     if (rank == 0) {
       rs_decode_team<LV, T>(gf, ws, rbuf, wt, lane, sync, ok, a.m + it * LV::k);
       sync();  // the RS scratch lives in u2: the next item rebuilds it
+      after(it, ws, rbuf);
     }
   }
+}
+
+template <int LEVEL, bool KEYED, int C, int T>
+__global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(32 * T, 1) k_decrypt_latency_cluster(DecArgs a) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  cluster_items<LEVEL, KEYED, C, T>(a, smem, [](int64_t, uint32_t*, const uint8_t*) {});
 }
 
 // ---------------------------------------------------------------------------

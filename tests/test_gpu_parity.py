@@ -75,6 +75,27 @@ def test_debug_path_every_intermediate(hqc, level):
     assert (host(got["m"])[-20:] == wl.m).all()
 
 
+@pytest.mark.parametrize("level", LEVELS)
+@pytest.mark.parametrize("form", (0, 1))
+def test_latency_forms_every_rs_intermediate(hqc, level, form):
+    """The latency forms' own intermediates (not only m): form 0 (four-warp
+    team per ciphertext) and form 1 (cluster of four blocks, whose RM bytes
+    reach block 0 through distributed shared memory) dump each ciphertext's
+    RM bytes, syndromes and Lambda as the block that ran RS holds them; all
+    equal the oracle's, on adversarial and honest ciphertexts."""
+    P, u, v, y = adversarial(level, tag=70 + level)
+    wl = honest(level, 3, 11, first_ct=22000, tag=31)
+    u = np.concatenate([u, wl.u]); v = np.concatenate([v, wl.v]); y = np.concatenate([y, wl.y_rows])
+    want = oracle_dumps(level, u, v, y)
+    got = hqc.hqc_decrypt_debug_team(level, u64(u), u64(v), i32(y), form=form)
+    torch.cuda.synchronize()
+    for k in ("r", "S", "lam", "m"):
+        g = host(got[k])
+        bad = np.argwhere(g != want[k])
+        assert bad.size == 0, (k, bad[:5])
+    assert (host(got["m"])[-11:] == wl.m).all()
+
+
 # launch shapes of the single-level path: the default picks the latency form
 # (a four-warp team per ciphertext) for batches of at most 512; an explicit
 # shape runs the persistent fused kernel
