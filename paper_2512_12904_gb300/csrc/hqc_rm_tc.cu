@@ -166,18 +166,28 @@ __global__ void __launch_bounds__(128, 1) k_rm_tc(int64_t count, const uint64_t*
   const int64_t ntiles = (total + RMTC_ROWS - 1) / RMTC_ROWS;
   uint32_t parity = 0;
   bool ok = true;
-  for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-    // A: row tid = RM block g (the tail repeats the last block, not stored)
+  // the words of this thread's RM block of a tile (row tid; the tail of the
+  // last tile repeats the last block, and its byte is not stored)
+  uint32_t words[MULT][4];
+  auto fetch = [&](int64_t tile) {
     const int64_t g = tile * RMTC_ROWS + tid;
     const int64_t gg = g < total ? g : total - 1;
     const int64_t it = gg / LV::n1;
     const int j = (int)(gg - it * LV::n1);
     const uint32_t* blk = reinterpret_cast<const uint32_t*>(w + it * LV::W_v) + j * NW;
 #pragma unroll
+    for (int c = 0; c < MULT; c++)
+#pragma unroll
+      for (int q = 0; q < 4; q++) words[c][q] = __ldg(blk + 4 * c + q);
+  };
+  if (blockIdx.x < ntiles) fetch(blockIdx.x);
+  for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    const int64_t g = tile * RMTC_ROWS + tid;
+#pragma unroll
     for (int q = 0; q < 4; q++) {
       uint32_t b[MULT];
 #pragma unroll
-      for (int c = 0; c < MULT; c++) b[c] = __ldg(blk + 4 * c + q);
+      for (int c = 0; c < MULT; c++) b[c] = words[c][q];
       uint32_t pk[16];
       count_pairs<MULT>(b, pk);
 #pragma unroll
@@ -185,6 +195,8 @@ __global__ void __launch_bounds__(128, 1) k_rm_tc(int64_t count, const uint64_t*
         *reinterpret_cast<uint4*>(sa + tile_off(tid, 32 * q + 8 * u)) =
             make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]);
     }
+    // the next tile's words load while this tile's product and argmax run
+    if (tile + gridDim.x < ntiles) fetch(tile + gridDim.x);
     // generic-proxy stores -> visible to the tensor core's reads
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
@@ -219,10 +231,18 @@ __global__ void __launch_bounds__(128, 1) k_rm_tc(int64_t count, const uint64_t*
         for (int jj = 0; jj < 32; jj++) {
           const int a = c0 + jj;
           const float d = __uint_as_float(v[jj]);
-          // |F| / 2 and [F < 0]: F = -2 D for a > 0, 2 (H0 - D) for a = 0
-          const float half = a == 0 ? H0 - d : d;  // |F| / 2 = |half|, F < 0 iff (a ? half > 0 : half < 0)
-          const float neg = a == 0 ? (half < 0.f ? 1.f : 0.f) : (half > 0.f ? 1.f : 0.f);
-          best = fmaxf(best, fmaf(fabsf(half), 256.f, (float)(254 - 2 * a) + neg));
+          if (a == 0) {
+            // F = 2 (H0 - D): |F| / 2 = |H0 - D|, F < 0 iff H0 < D
+            const float half = H0 - d;
+            best = fmaxf(best, fmaf(fabsf(half), 256.f, 254.f + (half < 0.f ? 1.f : 0.f)));
+          } else {
+            // F = -2 D: the key is D 256 + (254 - 2a) + 1 when D > 0 (F < 0)
+            // and -D 256 + (254 - 2a) when D < 0, the larger of the two;
+            // D = 0 gives 255 - 2a, below column 0's key whenever every F
+            // is 0, so its low bit never decides
+            const float c = (float)(254 - 2 * a);
+            best = fmaxf(best, fmaxf(fmaf(d, 256.f, c + 1.f), fmaf(d, -256.f, c)));
+          }
         }
       }
       const int kb = (int)best;
