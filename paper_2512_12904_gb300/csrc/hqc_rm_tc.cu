@@ -19,11 +19,14 @@
 // Tensor-core details.  Both operands are K-major in the canonical layout
 // without swizzle: core matrices of 8 rows x 16 bytes, K-adjacent ones 128
 // bytes apart (the descriptor's leading offset), 8-row groups 2048 bytes
-// apart (its stride offset).  One thread issues the eight K = 16 steps and
-// commits them to an mbarrier; the four warps then read their 32 TMEM
-// lanes (rows) with tcgen05.ld.  Every wait on the mbarrier is bounded:
-// on a timeout the kernel records it in a device flag, stops, frees its
-// tensor memory and returns.
+// apart (its stride offset).  A block holds four groups of four warps that
+// share the H tile (160 KB of shared memory, all 512 tensor-memory columns:
+// one block per SM, 16 warps).  In each group one thread issues the eight
+// K = 16 steps and commits them to the group's mbarrier; the group's four
+// warps then read their 32 TMEM lanes (rows) with tcgen05.ld.  Each thread
+// loads its block's words for the group's next tile one turn ahead.
+// Every wait on an mbarrier is bounded: on a timeout the kernel records it
+// in a device flag, stops, frees its tensor memory and returns.
 #include <cuda_runtime.h>
 
 #include "hqc_kernels.cuh"
@@ -34,8 +37,9 @@ namespace {
 
 constexpr int RMTC_ROWS = 128;                    // RM blocks per tile (MMA M)
 constexpr int RMTC_TILE_BYTES = 128 * 128 * 2;    // one fp16 operand tile
-constexpr int RMTC_SMEM = 2 * RMTC_TILE_BYTES + 64;
-constexpr uint32_t RMTC_TMEM_COLS = 128;          // fp32 accumulators, one column per a
+constexpr int RMTC_GROUPS = 4;                    // four-warp groups per block, one tile each
+constexpr int RMTC_SMEM = (RMTC_GROUPS + 1) * RMTC_TILE_BYTES + 64;  // A per group, H, mbarriers, TMEM address
+constexpr uint32_t RMTC_TMEM_COLS = 128 * RMTC_GROUPS;  // one 128-column fp32 accumulator per group
 constexpr int RMTC_MAX_SPIN = 1 << 22;
 
 __device__ int g_rm_tc_timeouts = 0;
@@ -60,6 +64,20 @@ constexpr uint32_t RMTC_IDESC = (1u << 4) | ((128u >> 3) << 17) | ((128u >> 4) <
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// barrier of the 128 threads of group g (named barrier 1 + g); the AND of p
+__device__ __forceinline__ void group_sync(int g) {
+  asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory");
+}
+__device__ __forceinline__ bool group_and(int g, bool p) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred a, b;\n\tsetp.ne.u32 a, %2, 0;\n\tbar.red.and.pred b, %1, 128, a;\n\tselp.u32 %0, 1, 0, b;\n\t}"
+      : "=r"(r)
+      : "r"(1 + g), "r"((uint32_t)p)
+      : "memory");
+  return r != 0;
+}
 
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity) {
   uint32_t done = 0;
@@ -126,34 +144,38 @@ __device__ __forceinline__ void count_pairs(const uint32_t (&b)[MULT], uint32_t 
 }
 
 template <int LEVEL>
-__global__ void __launch_bounds__(128, 1) k_rm_tc(int64_t count, const uint64_t* __restrict__ w,
-                                                 uint8_t* __restrict__ r_out) {
+__global__ void __launch_bounds__(128 * RMTC_GROUPS, 1) k_rm_tc(int64_t count, const uint64_t* __restrict__ w,
+                                                               uint8_t* __restrict__ r_out) {
   using LV = Level<LEVEL>;
   constexpr int MULT = LV::mult, NW = LV::n2 / 32;
   static_assert(LV::n2 == 128 * MULT, "one RM block is MULT copies of 128 bits");
   extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t* sa = smem;
-  uint8_t* sh = smem + RMTC_TILE_BYTES;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * RMTC_TILE_BYTES);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + 2 * RMTC_TILE_BYTES + 8);
-  const int tid = threadIdx.x, warp = tid >> 5;
-  // B: row n of H, (-1)^popcount(n & k) as fp16
-  for (int k8 = 0; k8 < 16; k8++) {
+  // four groups of four warps share H; group g owns A tile g, mbarrier g
+  // and accumulator columns [128 g, 128 g + 128)
+  uint8_t* sh = smem + RMTC_GROUPS * RMTC_TILE_BYTES;
+  uint64_t* mbars = reinterpret_cast<uint64_t*>(smem + (RMTC_GROUPS + 1) * RMTC_TILE_BYTES);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + (RMTC_GROUPS + 1) * RMTC_TILE_BYTES + 8 * RMTC_GROUPS);
+  const int grp = threadIdx.x >> 7, tid = threadIdx.x & 127, warp = tid >> 5;
+  uint8_t* sa = smem + grp * RMTC_TILE_BYTES;
+  uint64_t* mbar = mbars + grp;
+  // B: row n of H, (-1)^popcount(n & k) as fp16 (rows split over the groups)
+  for (int r = threadIdx.x; r < 128 * 16; r += blockDim.x) {
+    const int n = r >> 4, k8 = r & 15;
     uint32_t p[4];
 #pragma unroll
     for (int q = 0; q < 4; q++) {
       const int k0 = 8 * k8 + 2 * q;
-      const uint32_t lo = (__popc(tid & k0) & 1) ? 0xBC00u : 0x3C00u;
-      const uint32_t hi = (__popc(tid & (k0 + 1)) & 1) ? 0xBC00u : 0x3C00u;
+      const uint32_t lo = (__popc(n & k0) & 1) ? 0xBC00u : 0x3C00u;
+      const uint32_t hi = (__popc(n & (k0 + 1)) & 1) ? 0xBC00u : 0x3C00u;
       p[q] = lo | (hi << 16);
     }
-    *reinterpret_cast<uint4*>(sh + tile_off(tid, 8 * k8)) = make_uint4(p[0], p[1], p[2], p[3]);
+    *reinterpret_cast<uint4*>(sh + tile_off(n, 8 * k8)) = make_uint4(p[0], p[1], p[2], p[3]);
   }
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+  if (threadIdx.x < RMTC_GROUPS) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbars + threadIdx.x)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
+  if (threadIdx.x < 32) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
                  "r"(RMTC_TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -161,9 +183,10 @@ __global__ void __launch_bounds__(128, 1) k_rm_tc(int64_t count, const uint64_t*
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = *tslot;
+  const uint32_t tmem = *tslot + 128u * grp;
   const int64_t total = count * LV::n1;
   const int64_t ntiles = (total + RMTC_ROWS - 1) / RMTC_ROWS;
+  const int64_t first = (int64_t)blockIdx.x * RMTC_GROUPS + grp, stride = (int64_t)gridDim.x * RMTC_GROUPS;
   uint32_t parity = 0;
   bool ok = true;
   // the words of this thread's RM block of a tile (row tid; the tail of the
@@ -180,8 +203,8 @@ __global__ void __launch_bounds__(128, 1) k_rm_tc(int64_t count, const uint64_t*
 #pragma unroll
       for (int q = 0; q < 4; q++) words[c][q] = __ldg(blk + 4 * c + q);
   };
-  if (blockIdx.x < ntiles) fetch(blockIdx.x);
-  for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+  if (first < ntiles) fetch(first);
+  for (int64_t tile = first; tile < ntiles && ok; tile += stride) {
     const int64_t g = tile * RMTC_ROWS + tid;
 #pragma unroll
     for (int q = 0; q < 4; q++) {
@@ -196,11 +219,11 @@ __global__ void __launch_bounds__(128, 1) k_rm_tc(int64_t count, const uint64_t*
             make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]);
     }
     // the next tile's words load while this tile's product and argmax run
-    if (tile + gridDim.x < ntiles) fetch(tile + gridDim.x);
+    if (tile + stride < ntiles) fetch(tile + stride);
     // generic-proxy stores -> visible to the tensor core's reads
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
-    __syncthreads();
+    group_sync(grp);
     tc_fence_after();
     if (tid == 0) {
 #pragma unroll
@@ -218,7 +241,7 @@ __global__ void __launch_bounds__(128, 1) k_rm_tc(int64_t count, const uint64_t*
     }
     const bool done = mbar_wait_bounded(smem_u32(mbar), parity);
     parity ^= 1u;
-    ok = __syncthreads_and(done) != 0;
+    ok = group_and(grp, done);
     tc_fence_after();
     if (ok) {
       constexpr float H0 = (float)(MULT * 64 + 65536);
@@ -250,12 +273,14 @@ __global__ void __launch_bounds__(128, 1) k_rm_tc(int64_t count, const uint64_t*
       if (g < total) r_out[g] = (uint8_t)byte;
     }
     tc_fence_before();
-    __syncthreads();
+    group_sync(grp);
   }
   if (!ok && tid == 0) atomicAdd(&g_rm_tc_timeouts, 1);
+  tc_fence_before();
+  __syncthreads();
   tc_fence_after();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(RMTC_TMEM_COLS));
+  if (threadIdx.x < 32)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tslot), "r"(RMTC_TMEM_COLS));
 }
 
 template <int LEVEL>
@@ -267,9 +292,9 @@ cudaError_t rm_tc_level(int64_t count, const uint64_t* w, uint8_t* r, cudaStream
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   const int64_t tiles = (count * Level<LEVEL>::n1 + RMTC_ROWS - 1) / RMTC_ROWS;
-  // at most three blocks of 64 KB fit an SM: 3 x 128 tensor-memory columns
-  const int64_t grid = std::min<int64_t>(tiles, 3 * (int64_t)sms);
-  k_rm_tc<LEVEL><<<(unsigned)grid, 128, RMTC_SMEM, st>>>(count, w, r);
+  // one 160 KB block of four groups per SM, holding all 512 tensor-memory columns
+  const int64_t grid = std::min<int64_t>((tiles + RMTC_GROUPS - 1) / RMTC_GROUPS, (int64_t)sms);
+  k_rm_tc<LEVEL><<<(unsigned)grid, 128 * RMTC_GROUPS, RMTC_SMEM, st>>>(count, w, r);
   return cudaGetLastError();
 }
 
