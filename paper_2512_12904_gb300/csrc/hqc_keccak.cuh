@@ -130,4 +130,97 @@ __device__ __forceinline__ void shake256_absorb(uint64_t (&a)[25], int len, Word
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same permutation on a lane pair: lane h (= lane & 1) of the pair holds
+// the h-th 32-bit half of each of the 25 lanes (h = 0: bits 0..31), so a
+// batch of messages keeps twice as many warps busy for the same ALU work.
+// A 64-bit rotation by r needs the partner's half of the lane, one shuffle:
+//   r in [1, 31]:  mine' = funnel_l(other, mine, r)   (both halves alike)
+//   r in [33, 63]: mine' = funnel_l(mine, other, r - 32)
+// Every lane of the warp must take part (the shuffles name all 32 lanes).
+// ---------------------------------------------------------------------------
+template <int R>
+__device__ __forceinline__ uint32_t rotl64_half(uint32_t mine, uint32_t other) {
+  constexpr int r = R & 63;
+  if constexpr (r == 0) {
+    return mine;
+  } else if constexpr (r < 32) {
+    return __funnelshift_l(other, mine, r);
+  } else if constexpr (r == 32) {
+    return other;
+  } else {
+    return __funnelshift_l(mine, other, r - 32);
+  }
+}
+
+__device__ __forceinline__ void keccak_round_pair(uint32_t (&a)[25], uint32_t rc_half) {
+  uint32_t C[5], Cp[5];
+#pragma unroll
+  for (int x = 0; x < 5; x++) C[x] = a[x] ^ a[x + 5] ^ a[x + 10] ^ a[x + 15] ^ a[x + 20];
+#pragma unroll
+  for (int x = 0; x < 5; x++) Cp[x] = __shfl_xor_sync(0xFFFFFFFFu, C[x], 1);
+#pragma unroll
+  for (int x = 0; x < 5; x++) {
+    const uint32_t D = C[(x + 4) % 5] ^ rotl64_half<1>(C[(x + 1) % 5], Cp[(x + 1) % 5]);
+#pragma unroll
+    for (int y = 0; y < 5; y++) a[x + 5 * y] ^= D;
+  }
+  uint32_t p[25];
+#pragma unroll
+  for (int i = 0; i < 25; i++) p[i] = keccak_rho(i) % 64 == 0 ? 0u : __shfl_xor_sync(0xFFFFFFFFu, a[i], 1);
+  uint32_t b[25];
+#define HQC_RHO_PI_H(x, y) \
+  b[(y) + 5 * ((2 * (x) + 3 * (y)) % 5)] = rotl64_half<keccak_rho((x) + 5 * (y))>(a[(x) + 5 * (y)], p[(x) + 5 * (y)]);
+#define HQC_RHO_PI_H_ROW(y) HQC_RHO_PI_H(0, y) HQC_RHO_PI_H(1, y) HQC_RHO_PI_H(2, y) HQC_RHO_PI_H(3, y) HQC_RHO_PI_H(4, y)
+  HQC_RHO_PI_H_ROW(0) HQC_RHO_PI_H_ROW(1) HQC_RHO_PI_H_ROW(2) HQC_RHO_PI_H_ROW(3) HQC_RHO_PI_H_ROW(4)
+#undef HQC_RHO_PI_H_ROW
+#undef HQC_RHO_PI_H
+#pragma unroll
+  for (int y = 0; y < 5; y++)
+#pragma unroll
+    for (int x = 0; x < 5; x++) a[x + 5 * y] = b[x + 5 * y] ^ (~b[(x + 1) % 5 + 5 * y] & b[(x + 2) % 5 + 5 * y]);
+  a[0] ^= rc_half;
+}
+
+__device__ __forceinline__ void keccak_f1600_pair(uint32_t (&a)[25], uint32_t h) {
+#pragma unroll 2
+  for (int ir = 0; ir < 24; ir++) {
+    const uint64_t rc = c_keccak_rc[ir];
+    keccak_round_pair(a, h ? (uint32_t)(rc >> 32) : (uint32_t)rc);
+  }
+}
+
+// shake256_absorb on a lane pair: word(q) returns the whole 64-bit word
+// (both lanes of the pair read the same address) and each lane keeps its
+// half.
+template <class WordFn>
+__device__ __forceinline__ void shake256_absorb_pair(uint32_t (&a)[25], int len, uint32_t h, WordFn word) {
+#pragma unroll
+  for (int i = 0; i < 25; i++) a[i] = 0;
+  const int nblocks = len / SHAKE256_RATE + 1;
+  const int qpad = len >> 3;
+  auto fetch = [&](int blk, uint32_t (&wh)[SHAKE256_RATE_WORDS]) {
+#pragma unroll
+    for (int i = 0; i < SHAKE256_RATE_WORDS; i++) {
+      const int q = blk * SHAKE256_RATE_WORDS + i;
+      const uint64_t wv = q < qpad || (q == qpad && (len & 7)) ? word(q) : 0ull;
+      wh[i] = h ? (uint32_t)(wv >> 32) : (uint32_t)wv;
+    }
+  };
+  uint32_t wh[SHAKE256_RATE_WORDS];
+  fetch(0, wh);
+  for (int blk = 0; blk < nblocks; blk++) {
+#pragma unroll
+    for (int i = 0; i < SHAKE256_RATE_WORDS; i++) {
+      const int q = blk * SHAKE256_RATE_WORDS + i;
+      uint64_t pad = 0;
+      if (q == qpad) pad ^= 0x1Full << (8 * (len & 7));
+      if (i == SHAKE256_RATE_WORDS - 1 && blk == nblocks - 1) pad ^= 0x80ull << 56;
+      a[i] ^= wh[i] ^ (h ? (uint32_t)(pad >> 32) : (uint32_t)pad);
+    }
+    if (blk + 1 < nblocks) fetch(blk + 1, wh);
+    keccak_f1600_pair(a, h);
+  }
+}
+
 }  // namespace hqc

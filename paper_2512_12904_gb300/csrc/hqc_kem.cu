@@ -6,7 +6,7 @@
 //   k_kem_seed_keys   h, x, y of a key pair from its two 32-byte seeds
 //   k_kem_derive      theta = G(m, salt), then r1, r2, e from the theta
 //                     stream through the constant-weight sampler
-//   k_kem_K           K = SHAKE256(x || U || V || salt || 4), x = m, or
+//   k_kem_K2          K = SHAKE256(x || U || V || salt || 4), x = m, or
 //                     sigma where the re-encryption did not match
 //
 // Encapsulation = derive, encrypt, K.  Decapsulation = the fused decryption,
@@ -33,7 +33,7 @@
 namespace hqc {
 
 constexpr int KEM_THREADS = 128;
-constexpr int KEM_K_THREADS = 64;  // 1,024 blocks for 65,536 items: even spread over 152 SMs
+constexpr int KEM_K2_THREADS = 128;  // 64 lane pairs per block: 1,024 blocks for 65,536 items
 constexpr int KEM_SALT = 16;
 constexpr int KEM_SEED = 32;
 constexpr int KEM_KBYTES = 32;
@@ -219,14 +219,24 @@ __global__ void __launch_bounds__(KEM_THREADS) k_kem_derive(int64_t count, const
 // shifted by r = (k + ceil(n/8)) mod 8 bytes over T = [last u word,
 // v[0..W_v), salt, 0x04]: word P1 + i = (T[i+1] << 8r) | (T[i] >> (64 - 8r)).
 // The previous T word is carried, so each message word costs one load.
+// K = SHAKE256(x || U || V || salt || 4) with each message on a lane pair
+// (keccak_f1600_pair): lane h of the pair keeps the h-th 32-bit half of
+// every state lane, so 65,536 messages fill 4,096 warps instead of 2,048
+// (one thread per message measured 0.7 % slower on HQC-1 decapsulation:
+// the pair's 29 shuffles per round cost most of what the warps gain).  x is
+// m, or sigma where the re-encryption did not match, chosen by mask.  The
+// message is a byte-shifted stream over the u and v words with the
+// previous word carried, one load per message word.  Lanes past the batch, and
+// items with a key index outside [0, nkeys), hash the last item's (or key
+// 0's) data and store nothing: every lane takes part in the shuffles.
 template <int LEVEL>
-__global__ void __launch_bounds__(KEM_K_THREADS) k_kem_K(int64_t count, const uint8_t* __restrict__ m,
-                                                        const uint32_t* __restrict__ ok,
-                                                        const uint8_t* __restrict__ sigma,
-                                                        const int32_t* __restrict__ key_idx, int64_t nkeys,
-                                                        const uint64_t* __restrict__ u,
-                                                        const uint64_t* __restrict__ v,
-                                                        const uint8_t* __restrict__ salt, uint8_t* __restrict__ K) {
+__global__ void __launch_bounds__(KEM_K2_THREADS) k_kem_K2(int64_t count, const uint8_t* __restrict__ m,
+                                                          const uint32_t* __restrict__ ok,
+                                                          const uint8_t* __restrict__ sigma,
+                                                          const int32_t* __restrict__ key_idx, int64_t nkeys,
+                                                          const uint64_t* __restrict__ u,
+                                                          const uint64_t* __restrict__ v,
+                                                          const uint8_t* __restrict__ salt, uint8_t* __restrict__ K) {
   using LV = Level<LEVEL>;
   constexpr int KW = LV::k / 8;
   constexpr int UB = cdiv(LV::n, 8), VB = LV::n1 * LV::n2 / 8;
@@ -235,16 +245,18 @@ __global__ void __launch_bounds__(KEM_K_THREADS) k_kem_K(int64_t count, const ui
   constexpr int P1 = OFF_V / 8, R8 = 8 * (OFF_V % 8);
   constexpr int NT = LV::W_v + 4;  // T[1..NT): v words, two salt words, the domain byte
   static_assert(P1 == KW + LV::W_u - 1 && R8 > 0, "U ends inside its last word");
-  const int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (it >= count) return;
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t h = (uint32_t)(gt & 1);
+  const bool in = (gt >> 1) < count;
+  const int64_t it = in ? (gt >> 1) : count - 1;
   const uint32_t ki = (uint32_t)__ldg(key_idx + it);
-  if (ki >= (uint64_t)nkeys) return;  // skipped item: K untouched (the index is public)
+  const bool store = in && ki < (uint64_t)nkeys;  // a skipped item: K untouched (the index is public)
   const uint64_t* mrow = reinterpret_cast<const uint64_t*>(m + it * LV::k);
   uint64_t keep = ~0ull;
   const uint64_t* grow = mrow;
   if (ok) {
     keep = 0ull - (uint64_t)(__ldg(ok + it) != 0u);
-    grow = reinterpret_cast<const uint64_t*>(sigma + (int64_t)ki * LV::k);
+    grow = reinterpret_cast<const uint64_t*>(sigma + (int64_t)(ki < (uint64_t)nkeys ? ki : 0u) * LV::k);
   }
   const uint64_t* urow = u + it * LV::W_u_pitch;
   const uint64_t* vrow = v + it * LV::W_v;
@@ -255,8 +267,8 @@ __global__ void __launch_bounds__(KEM_K_THREADS) k_kem_K(int64_t count, const ui
   auto tword = [&](int i) {  // T[i], i >= 1
     return i <= LV::W_v ? __ldg(vrow + i - 1) : i <= LV::W_v + 2 ? __ldg(srow + i - 1 - LV::W_v) : 0x04ull;
   };
-  uint64_t a[25];
-  shake256_absorb(a, LEN, [&](int q) {
+  uint32_t a[25];
+  shake256_absorb_pair(a, LEN, h, [&](int q) {
     uint64_t w;
     if (q < KW) {
       w = (__ldg(mrow + q) & keep) | (__ldg(grow + q) & ~keep);
@@ -270,9 +282,11 @@ __global__ void __launch_bounds__(KEM_K_THREADS) k_kem_K(int64_t count, const ui
     }
     return w;
   });
-  uint64_t* krow = reinterpret_cast<uint64_t*>(K + it * KEM_KBYTES);
+  if (store) {
+    uint32_t* krow = reinterpret_cast<uint32_t*>(K + it * KEM_KBYTES);
 #pragma unroll
-  for (int i = 0; i < KEM_KBYTES / 8; i++) krow[i] = a[i];
+    for (int i = 0; i < KEM_KBYTES / 8; i++) krow[2 * i + h] = a[i];
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -339,11 +353,12 @@ cudaError_t launch_kem_K(int level, int64_t count, const uint8_t* m, const uint3
                          const int32_t* key_idx, int64_t nkeys, const uint64_t* u, const uint64_t* v,
                          const uint8_t* salt, uint8_t* K, cudaStream_t st) {
   if (count == 0) return cudaSuccess;
-  const unsigned kb = (unsigned)((count + KEM_K_THREADS - 1) / KEM_K_THREADS);
+  // one message per lane pair
+  const unsigned kb = (unsigned)((2 * count + KEM_K2_THREADS - 1) / KEM_K2_THREADS);
   switch (level) {
-    case 1: k_kem_K<1><<<kb, KEM_K_THREADS, 0, st>>>(count, m, ok, sigma, key_idx, nkeys, u, v, salt, K); break;
-    case 3: k_kem_K<3><<<kb, KEM_K_THREADS, 0, st>>>(count, m, ok, sigma, key_idx, nkeys, u, v, salt, K); break;
-    case 5: k_kem_K<5><<<kb, KEM_K_THREADS, 0, st>>>(count, m, ok, sigma, key_idx, nkeys, u, v, salt, K); break;
+    case 1: k_kem_K2<1><<<kb, KEM_K2_THREADS, 0, st>>>(count, m, ok, sigma, key_idx, nkeys, u, v, salt, K); break;
+    case 3: k_kem_K2<3><<<kb, KEM_K2_THREADS, 0, st>>>(count, m, ok, sigma, key_idx, nkeys, u, v, salt, K); break;
+    case 5: k_kem_K2<5><<<kb, KEM_K2_THREADS, 0, st>>>(count, m, ok, sigma, key_idx, nkeys, u, v, salt, K); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
