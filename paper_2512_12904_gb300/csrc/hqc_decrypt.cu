@@ -129,7 +129,7 @@ static cudaError_t fused_level(const DecArgs& a, cudaStream_t st, const LaunchCf
   int nw = 0, c = 0, g = 0;
   size_t sm = 0;
   cudaError_t e = shape_for(k_decrypt_fused<LEVEL, KEYED>, FusedBound<LEVEL>::threads,
-                            (size_t)fused_words<LEVEL>() * 4, cfg, &nw, &c, &g, &sm);
+                            (size_t)fused_words<LEVEL>() * 4, cfg, &nw, &c, &g, &sm, false, fused_fixed_bytes<LEVEL>());
   if (e != cudaSuccess) return e;
   if (warps) *warps = nw;
   if (ctas) *ctas = c;
@@ -143,7 +143,8 @@ static cudaError_t fused_level(const DecArgs& a, cudaStream_t st, const LaunchCf
     LaunchCfg sc;
     sc.warps_per_cta = (int)((a.count + sms - 1) / sms);
     e = shape_for(k_decrypt_fused<LEVEL, KEYED, 1>, FusedBound<LEVEL>::threads,
-                  (size_t)fused_warp_words<Level<LEVEL>, 1>() * 4, sc, &nw, &c, &g, &sm);
+                  (size_t)fused_warp_words<Level<LEVEL>, 1>() * 4, sc, &nw, &c, &g, &sm, false,
+                  fused_fixed_bytes<LEVEL>());
     if (e != cudaSuccess) return e;
     const int64_t need1 = (a.count + nw - 1) / nw;
     if (need1 < g) g = (int)need1;
@@ -160,7 +161,7 @@ static cudaError_t fused_level(const DecArgs& a, cudaStream_t st, const LaunchCf
       sc.warps_per_cta = want;
       sc.ctas_per_sm = cfg.ctas_per_sm;
       e = shape_for(k_decrypt_fused<LEVEL, KEYED>, FusedBound<LEVEL>::threads, (size_t)fused_words<LEVEL>() * 4, sc,
-                    &nw, &c, &g, &sm);
+                    &nw, &c, &g, &sm, false, fused_fixed_bytes<LEVEL>());
       if (e != cudaSuccess) return e;
     }
   }
@@ -268,7 +269,7 @@ static cudaError_t items_level(const MixedArgs& a, int grid, cudaStream_t st, co
   int nw = 0, c = 0, g = 0;
   size_t sm = 0;
   cudaError_t e = shape_for(k_decrypt_items<LEVEL>, FusedBound<LEVEL>::threads, (size_t)fused_words<LEVEL>() * 4,
-                            cfg, &nw, &c, &g, &sm);
+                            cfg, &nw, &c, &g, &sm, false, fused_fixed_bytes<LEVEL>());
   if (e != cudaSuccess) return e;
   if (warps) *warps = nw;
   if (ctas) *ctas = c;
@@ -284,7 +285,7 @@ static cudaError_t items_level(const MixedArgs& a, int grid, cudaStream_t st, co
       LaunchCfg sc;
       sc.warps_per_cta = small;
       e = shape_for(k_decrypt_items<LEVEL>, FusedBound<LEVEL>::threads, (size_t)fused_words<LEVEL>() * 4, sc, &nw, &c,
-                    &g, &sm);
+                    &g, &sm, false, fused_fixed_bytes<LEVEL>());
       if (e != cudaSuccess) return e;
     }
   }

@@ -262,11 +262,19 @@ __device__ __forceinline__ void rot_xor_product(const uint32_t* u2, const uint32
 //   F(a) = sum_i s_i (-1)^{popcount(a & i)}, 7 butterfly stages (S6)
 //   byte = a* + 128 [F(a*) < 0], a* = argmax |F|, ties -> smallest a (S7)
 // Lane hb (= lane & 1) of the pair holds the 64 elements with index bit 6
-// equal to hb, as 32 registers of two 16-bit halves biased by 640 (|F| <=
-// 640, and F is even: a sum of 128 odd s_i).  Register r = 16 tt + q holds
-// indices q | tt << 5 | hb << 6 (low half) and the same | 16 (high half).
-// Stages on index bits 0-3 and 5 are packed adds inside a lane, bit 6 is
-// one shuffle with the partner lane, bit 4 (the halves) is the last stage.
+// equal to hb, as 32 registers of two 16-bit halves.  Register r = 16 tt +
+// q holds indices q | tt << 5 | hb << 6 (low half) and the same | 16 (high
+// half).  Stages on index bits 0-3 and 5 are packed adds inside a lane.
+// For mult 3 a register there is the integer 65536 hi + lo of its two
+// signed halves, which sums and differences keep exact (a negative low half
+// borrows from the high half, and is lent back when the bias is added), so
+// a butterfly is a plain add and a plain subtract; bit 6, one shuffle with
+// the partner lane, adds the bias 640 to both halves.  For mult 5 every
+// stage keeps both halves biased by 640 (a butterfly adds or subtracts the
+// bias too), which measured 0.6-0.8 % faster there, against 3.6 % slower
+// for mult 3.  Either way, after bit 6 each half is F + 640 as an unsigned
+// 16-bit value (|F| <= 640, and F is even: a sum of 128 odd s_i); bit 4
+// (the halves) is the last stage.
 // The argmax runs on 16-bit keys (F + 640) / 2 * 64 + (63 - r6) -- score,
 // then smaller index -- with packed unsigned max, once for +F (b = 0) and
 // once for -F (b = 1); the half bit and b stay implicit in where the key
@@ -287,7 +295,9 @@ template <int MULT>
 __device__ __forceinline__ uint32_t rm_decode_pair(const uint32_t* blk, uint32_t hb) {
   constexpr uint32_t BIAS = 640u;
   constexpr uint32_t BP = BIAS * 0x10001u;
-  constexpr uint32_t K = (BIAS + MULT) * 0x10001u;
+  constexpr bool SIGNED = MULT == 3;  // unbiased in-lane stages
+  constexpr uint32_t K = (SIGNED ? MULT : BIAS + MULT) * 0x10001u;  // K - 2 c = s_i (+ bias) in both halves
+  constexpr uint32_t SB = SIGNED ? 0u : BP;
   constexpr uint32_t KN = 2u * BP * 32u;  // (1280 per half) * 32
   uint32_t p0[2], p1[2], p2[2];
   {
@@ -349,15 +359,16 @@ __device__ __forceinline__ uint32_t rm_decode_pair(const uint32_t* blk, uint32_t
     for (int r = 0; r < 32; r++) {
       if (!(r & (1 << b))) {
         const uint32_t X = R[r], Y = R[r | (1 << b)];
-        R[r] = X + Y - BP;
-        R[r | (1 << b)] = X - Y + BP;
+        R[r] = X + Y - SB;
+        R[r | (1 << b)] = X - Y + SB;
       }
     }
   }
   // index bit 6: lane 0 keeps x + y, lane 1 keeps y - x (x = own value,
-  // y = partner's): own * (+-1) + y + (-+bias), one multiply-add
+  // y = partner's), both biased: own * (+-1) + (y + cst), one multiply-add
+  // (cst adds the bias for unbiased inputs, corrects it for biased ones)
   const uint32_t sgn = hb ? 0xFFFFFFFFu : 1u;
-  const uint32_t cst = hb ? BP : (0u - BP);
+  const uint32_t cst = SIGNED ? BP : hb ? BP : (0u - BP);
 #pragma unroll
   for (int r = 0; r < 32; r++) {
     const uint32_t Y = __shfl_xor_sync(FULL_MASK, R[r], 1);
@@ -443,6 +454,77 @@ struct RSDebugRow {
 // words: log r (96 halfwords), log S behind 64 halfwords of log-zero padding
 // (128), log Lambda and log Omega (64 halfwords each)
 constexpr int RS_SCRATCH = 176;
+
+// ---------------------------------------------------------------------------
+// Syndromes by Horner's rule on per-lane multiply tables (the table-driven
+// syndromes of Sec. III-D, in a GPU layout).  For one received word
+//   S_i = sum_j r_j alpha^{i j}
+//       = (...((r_{n1-1}) alpha^i + r_{n1-2}) alpha^i + ...) alpha^i + r_0,
+// so lane L, which owns S_{L+1}, only ever multiplies by alpha^{L+1}: a
+// 256-entry table of its own, in its own bank.  An element x travels as
+// its byte offset in the table block,
+//   o_L(x) = spread(x) | 4 L,  spread(x) = ((x >> 1) << 7) | ((x & 1) << 1)
+// (entry x of lane L is halfword x & 1 of word 32 (x >> 1) + L).  spread
+// is linear over GF(2) and leaves bits 2..6 free for 4 L, so
+//   o_L(x alpha^{L+1} + r) = T_L[o_L(x)] ^ spread(r),
+// with T_L[o_L(x)] = o_L(x alpha^{L+1}) stored in the table: a Horner step
+// is one shared load and one XOR, with no exponent arithmetic.  Every
+// offset stays inside the 16 KB block (spread(255) | 124 + 2 < 16384)
+// whatever the bytes, and a warp's 32 loads hit 32 banks.
+// ---------------------------------------------------------------------------
+constexpr int SYN_TABLE_BYTES = 256 * 32 * 2;
+
+__host__ __device__ constexpr uint32_t syn_spread(uint32_t x) { return ((x >> 1) << 7) | ((x & 1u) << 1); }
+__host__ __device__ constexpr uint32_t syn_unspread(uint32_t o) { return ((o >> 6) & 0xFEu) | ((o >> 1) & 1u); }
+static_assert(syn_unspread(syn_spread(0xA5u) | 4u * 31u) == 0xA5u && syn_spread(255u) + 4u * 31u + 2u <= 16384u,
+              "syndrome table offsets");
+
+// Fill a block's syndrome table: column L multiplies by alpha^{L+1}.  Reads
+// the packed GF tables from global memory, so it needs no barrier after the
+// shared GF tables and can share theirs.
+__device__ inline void syn_table_init(uint8_t* tab, int tid, int nthreads) {
+  const uint32_t* packed = reinterpret_cast<const uint32_t*>(&g_gf_packed);
+  for (int e = tid; e < 32 * 256; e += nthreads) {
+    const uint32_t L = (uint32_t)e & 31u, x = (uint32_t)e >> 5;
+    const uint32_t lg = (__ldg(packed + 128 + (x >> 1)) >> (16 * (x & 1u))) & 0xFFFFu;
+    const uint32_t ex = lg + L + 1u;  // <= 254 + 32: inside the doubled exp table
+    const uint32_t y = x == 0 ? 0u : (__ldg(packed + (ex >> 2)) >> (8 * (ex & 3u))) & 0xFFu;
+    *reinterpret_cast<uint16_t*>(tab + (syn_spread(x) | 4u * L)) = (uint16_t)(syn_spread(y) | 4u * L);
+  }
+}
+
+// S_1..S_{2 delta} of a warp's G received words (lane L computes S_{L+1}
+// of each: G Horner chains side by side), stored as logs where
+// rs_decode_seg<..., HAVE_S = true> expects them.  rs: the words' scratch
+// areas (RS_SCRATCH words apart); r: their RM bytes (RB bytes apart).  The
+// spread bytes go where rs_decode_seg would keep log r.  Lanes past
+// 2 delta run the chains and store nothing.
+template <class LV, int G>
+__device__ __forceinline__ void rs_syndromes_horner(const GF& gf, const uint8_t* syn, uint32_t* rs,
+                                                    const uint8_t* r, int RB, int lane) {
+  constexpr int n1 = LV::n1, NR = LV::NR;
+  static_assert(NR <= 32 && n1 <= 96, "one syndrome per lane; spread bytes fit the log r area");
+#pragma unroll
+  for (int g = 0; g < G; g++)
+    for (int j = lane; j < n1; j += 32)
+      reinterpret_cast<uint16_t*>(rs + g * RS_SCRATCH)[j] = (uint16_t)syn_spread(r[g * RB + j]);
+  __syncwarp();
+  uint32_t o[G];
+#pragma unroll
+  for (int g = 0; g < G; g++) o[g] = (4u * (uint32_t)lane) ^ reinterpret_cast<const uint16_t*>(rs + g * RS_SCRATCH)[n1 - 1];
+#pragma unroll
+  for (int j = n1 - 2; j >= 0; j--) {
+#pragma unroll
+    for (int g = 0; g < G; g++)
+      o[g] = (uint32_t)*reinterpret_cast<const uint16_t*>(syn + o[g]) ^
+             reinterpret_cast<const uint16_t*>(rs + g * RS_SCRATCH)[j];
+  }
+  if (lane < NR) {
+#pragma unroll
+    for (int g = 0; g < G; g++)
+      (reinterpret_cast<uint16_t*>(rs + g * RS_SCRATCH + 48) + 64)[lane] = (uint16_t)gf.log(syn_unspread(o[g]));
+  }
+}
 
 // Berlekamp-Massey (S8) on SEG lanes: exactly 2 delta iterations over the
 // syndromes logS (log form, with log-zero padding below index 0); writes the
@@ -542,11 +624,13 @@ __device__ __forceinline__ uint32_t rs_bm(const GF& gf, const uint16_t* logS, ui
   return L;
 }
 
-template <class LV, int SEG, bool ALL_POS>
+// HAVE_S: the syndromes' logs are already in rs (rs_syndromes_horner).
+template <class LV, int SEG, bool ALL_POS, bool HAVE_S = false>
 __device__ __forceinline__ void rs_decode_seg(const GF& gf, uint32_t* rs, const uint8_t* r, int lane, bool active,
                                               uint8_t* __restrict__ m_out, const RSDebugRow* dbg) {
   constexpr int n1 = LV::n1, k = LV::k, NR = LV::NR, CAP = LV::CAP, delta = LV::delta;
   static_assert(n1 <= 96 && CAP <= 64, "RS scratch sizes");
+  static_assert(!(HAVE_S && ALL_POS), "the debug path computes its own syndromes");
   const int sl = lane % SEG;
   uint16_t* logr = reinterpret_cast<uint16_t*>(rs);
   // logS[i] for i in [-64, 64): negative indices read log 0, so terms of
@@ -555,14 +639,15 @@ __device__ __forceinline__ void rs_decode_seg(const GF& gf, uint32_t* rs, const 
   uint16_t* logLam = reinterpret_cast<uint16_t*>(rs + 112);
   uint16_t* logOm = reinterpret_cast<uint16_t*>(rs + 144);
 
-  for (int j = sl; j < n1; j += SEG) logr[j] = (uint16_t)gf.log(r[j]);
+  if constexpr (!HAVE_S)
+    for (int j = sl; j < n1; j += SEG) logr[j] = (uint16_t)gf.log(r[j]);
   for (int j = sl; j < 64; j += SEG) logS[j - 64] = (uint16_t)GF_LOG_ZERO;
   __syncwarp();
 
   // syndromes: lane owns i = sl + 1 + SEG s; each log r_j is loaded once
   // for all of the lane's syndromes
   constexpr int NS = cdiv(NR, SEG);
-  {
+  if constexpr (!HAVE_S) {
     uint32_t acc[NS], e[NS];
 #pragma unroll
     for (int s = 0; s < NS; s++) acc[s] = e[s] = 0;
@@ -700,8 +785,11 @@ __host__ __device__ constexpr int fused_warp_words() {
 // for each in turn, then Reed-Solomon for all G side by side on 32 / G
 // lanes each.  rows(g, u, v, y, m) fills ciphertext g's rows and returns
 // false for a slot past the end of the batch (skipped, nothing stored).
-template <class LV, int G, bool MASKED, class Rows>
-__device__ __forceinline__ void decrypt_group(const GF& gf, uint32_t* ws, int lane, const Rows& rows) {
+// HORNER: the syndromes come from the block's syndrome table syn (Horner
+// chains on all 32 lanes) instead of SEG lanes' exponent sums.
+template <class LV, int G, bool MASKED, bool HORNER = false, class Rows>
+__device__ __forceinline__ void decrypt_group(const GF& gf, uint32_t* ws, int lane, const Rows& rows,
+                                              const uint8_t* syn = nullptr) {
   constexpr int RB = cdiv(LV::n1, 4) * 4;  // bytes per stored RM word
   static_assert(G * RS_SCRATCH <= LV::U2W, "RS scratch of G words fits in u2");
   static_assert(fused_warp_words<LV, G>() % 4 == 0 && LV::U2W % 4 == 0 && LV::WP % 4 == 0, "16-byte alignment");
@@ -716,7 +804,8 @@ __device__ __forceinline__ void decrypt_group(const GF& gf, uint32_t* ws, int la
   constexpr int SEG = 32 / G;
   const int seg = lane / SEG;
   const bool act = rows(seg, u, v, y, m);
-  rs_decode_seg<LV, SEG, false>(gf, ws + seg * RS_SCRATCH, rbuf + seg * RB, lane, act, m, nullptr);
+  if constexpr (HORNER) rs_syndromes_horner<LV, G>(gf, syn, ws, rbuf, RB, lane);
+  rs_decode_seg<LV, SEG, false, HORNER>(gf, ws + seg * RS_SCRATCH, rbuf + seg * RB, lane, act, m, nullptr);
   __syncwarp();
 }
 

@@ -43,6 +43,19 @@ template <> struct FusedGroup<1> { static constexpr int G = 2; };
 template <int LEVEL>
 __host__ __device__ constexpr int fused_words() { return fused_warp_words<Level<LEVEL>, FusedGroup<LEVEL>::G>(); }
 
+// Levels whose fused kernels compute the syndromes by Horner's rule on the
+// block's syndrome table (rs_syndromes_horner): 16 KB more shared memory
+// per block.  HQC-1 has the room (its warps are capped by the 1,024-thread
+// block, not by shared memory); HQC-3 would lose two of its 20 warps, and
+// HQC-5's 58 syndromes need two table columns per lane.
+template <int LEVEL> struct FusedSyn { static constexpr bool on = LEVEL == 1; };
+
+// Shared bytes of a fused block before the warps' slices.
+template <int LEVEL>
+__host__ __device__ constexpr int fused_fixed_bytes() {
+  return GF_TABLE_BYTES + (FusedSyn<LEVEL>::on ? SYN_TABLE_BYTES : 0);
+}
+
 // ---------------------------------------------------------------------------
 // Fused persistent kernel, one level.  Warp w takes groups of G consecutive
 // ciphertexts w, w + (all warps), ...
@@ -50,12 +63,14 @@ __host__ __device__ constexpr int fused_words() { return fused_warp_words<Level<
 template <int LEVEL, bool KEYED, int G = FusedGroup<LEVEL>::G>
 __global__ void __launch_bounds__(FusedBound<LEVEL>::threads, 1) k_decrypt_fused(DecArgs a) {
   using LV = Level<LEVEL>;
+  constexpr bool SYN = FusedSyn<LEVEL>::on;
   extern __shared__ __align__(16) uint8_t smem[];
   gf_tables_init(smem, threadIdx.x, blockDim.x);
+  if constexpr (SYN) syn_table_init(smem + GF_TABLE_BYTES, threadIdx.x, blockDim.x);
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const GF gf(smem, lane);
-  uint32_t* ws = reinterpret_cast<uint32_t*>(smem + GF_TABLE_BYTES) + warp * fused_warp_words<LV, G>();
+  uint32_t* ws = reinterpret_cast<uint32_t*>(smem + fused_fixed_bytes<LEVEL>()) + warp * fused_warp_words<LV, G>();
   const int64_t ngroups = (a.count + G - 1) / G;
   for (int64_t q = (int64_t)blockIdx.x * nw + warp; q < ngroups; q += (int64_t)gridDim.x * nw) {
     auto rows = [&](int g, const uint64_t*& u, const uint64_t*& v, const uint32_t*& y, uint8_t*& m) {
@@ -76,7 +91,7 @@ __global__ void __launch_bounds__(FusedBound<LEVEL>::threads, 1) k_decrypt_fused
       m = a.m + it * LV::k;
       return ok;
     };
-    decrypt_group<LV, G, !KEYED>(gf, ws, lane, rows);
+    decrypt_group<LV, G, !KEYED, SYN>(gf, ws, lane, rows, smem + GF_TABLE_BYTES);
   }
 }
 
@@ -378,20 +393,21 @@ __device__ __forceinline__ bool item_rows(const MixedArgs& a, int64_t it, const 
 
 // The items of ONE level by single warps, G per warp per turn: block `blk`
 // of `nblk`, warp `warp` of `nw` (the shared memory after the GF tables is
-// nw slices of fused_warp_words<LV, G>).
-template <int LEVEL, int G>
+// nw slices of fused_warp_words<LV, G>, after the syndrome table if SYN).
+template <int LEVEL, int G, bool SYN = false>
 __device__ __forceinline__ void items_solo(const MixedArgs& a, uint8_t* smem, int64_t blk, int64_t nblk, int warp,
                                            int nw) {
   using LV = Level<LEVEL>;
   const int lane = threadIdx.x & 31;
   const GF gf(smem, lane);
-  uint32_t* ws = reinterpret_cast<uint32_t*>(smem + GF_TABLE_BYTES) + warp * fused_warp_words<LV, G>();
+  uint32_t* ws = reinterpret_cast<uint32_t*>(smem + GF_TABLE_BYTES + (SYN ? SYN_TABLE_BYTES : 0)) +
+                 warp * fused_warp_words<LV, G>();
   const int64_t ngroups = (a.count + G - 1) / G;
   for (int64_t q = blk * nw + warp; q < ngroups; q += nblk * nw) {
     auto rows = [&](int g, const uint64_t*& u, const uint64_t*& v, const uint32_t*& y, uint8_t*& m) {
       return item_rows<LEVEL>(a, q * G + g, u, v, y, m);
     };
-    decrypt_group<LV, G, false>(gf, ws, lane, rows);
+    decrypt_group<LV, G, false, SYN>(gf, ws, lane, rows, smem + GF_TABLE_BYTES);
   }
 }
 
@@ -421,10 +437,12 @@ __device__ __forceinline__ void items_team(const MixedArgs& a, uint8_t* smem, in
 // these per level side by side in a CUDA graph.
 template <int LEVEL, int G = FusedGroup<LEVEL>::G>
 __global__ void __launch_bounds__(FusedBound<LEVEL>::threads, 1) k_decrypt_items(MixedArgs a) {
+  constexpr bool SYN = FusedSyn<LEVEL>::on;
   extern __shared__ __align__(16) uint8_t smem[];
   gf_tables_init(smem, threadIdx.x, blockDim.x);
+  if constexpr (SYN) syn_table_init(smem + GF_TABLE_BYTES, threadIdx.x, blockDim.x);
   __syncthreads();
-  items_solo<LEVEL, G>(a, smem, blockIdx.x, gridDim.x, threadIdx.x >> 5, blockDim.x >> 5);
+  items_solo<LEVEL, G, SYN>(a, smem, blockIdx.x, gridDim.x, threadIdx.x >> 5, blockDim.x >> 5);
 }
 
 template <int LEVEL>
@@ -527,7 +545,7 @@ __global__ void __launch_bounds__(STAGE_THREADS) k_stage_rs(int64_t count, const
 // ---------------------------------------------------------------------------
 template <int LEVEL>
 [[maybe_unused]] static size_t fused_smem(int warps) {
-  return (size_t)GF_TABLE_BYTES + (size_t)warps * fused_words<LEVEL>() * 4;
+  return (size_t)fused_fixed_bytes<LEVEL>() + (size_t)warps * fused_words<LEVEL>() * 4;
 }
 
 [[maybe_unused]] static std::mutex g_shape_mu;
@@ -543,21 +561,24 @@ static inline int device_props(int* sms, int* smem_optin) {
 }
 
 // per_warp: shared bytes per warp (for teams: per team / 2); teams: the
-// warp count must be even and at most 30 (15 named barriers).
+// warp count must be even and at most 30 (15 named barriers); fixed: the
+// block's bytes before the warps' slices (the GF tables, and for some
+// kernels the syndrome table).
 template <class KernelT>
 static cudaError_t shape_for(KernelT kern, int max_threads, size_t per_warp, const LaunchCfg& cfg, int* warps,
-                             int* ctas, int* grid, size_t* smem_bytes, bool teams = false) {
+                             int* ctas, int* grid, size_t* smem_bytes, bool teams = false,
+                             size_t fixed = GF_TABLE_BYTES) {
   int sms = 0, optin = 0;
   const int dev = device_props(&sms, &optin);
   int nw = cfg.warps_per_cta;
   if (nw <= 0) {
-    nw = (int)((optin - GF_TABLE_BYTES) / per_warp);
+    nw = (int)((optin - fixed) / per_warp);
     if (nw > max_threads / 32) nw = max_threads / 32;
     if (teams) nw = std::min(nw & ~1, 30);
   }
   if (nw < 1 || (teams && (nw & 1))) return cudaErrorInvalidValue;
   if (nw > max_threads / 32 || (teams && nw > 30)) return cudaErrorInvalidValue;
-  const size_t sm = GF_TABLE_BYTES + (size_t)nw * per_warp;
+  const size_t sm = fixed + (size_t)nw * per_warp;
   if (sm > (size_t)optin) return cudaErrorInvalidValue;
   // the shared-memory attribute only grows, and occupancies are looked up
   // once per (kernel, device, warps, bytes): repeated launches of small

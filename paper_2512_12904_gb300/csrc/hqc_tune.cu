@@ -26,7 +26,8 @@ cudaError_t solo_keyed(const DecArgs& a, cudaStream_t st, const LaunchCfg& cfg, 
   int nw = 0, cc = 0, gg = 0;
   size_t sm = 0;
   cudaError_t e = shape_for(k_decrypt_fused<LEVEL, true, G>, FusedBound<LEVEL>::threads,
-                            (size_t)fused_warp_words<Level<LEVEL>, G>() * 4, cfg, &nw, &cc, &gg, &sm);
+                            (size_t)fused_warp_words<Level<LEVEL>, G>() * 4, cfg, &nw, &cc, &gg, &sm, false,
+                            fused_fixed_bytes<LEVEL>());
   if (e != cudaSuccess) return e;
   if (w) *w = nw;
   if (c) *c = cc;
@@ -62,7 +63,8 @@ cudaError_t solo_items(const MixedArgs& a, int grid, cudaStream_t st, const Laun
   int nw = 0, cc = 0, gg = 0;
   size_t sm = 0;
   cudaError_t e = shape_for(k_decrypt_items<LEVEL, G>, FusedBound<LEVEL>::threads,
-                            (size_t)fused_warp_words<Level<LEVEL>, G>() * 4, cfg, &nw, &cc, &gg, &sm);
+                            (size_t)fused_warp_words<Level<LEVEL>, G>() * 4, cfg, &nw, &cc, &gg, &sm, false,
+                            fused_fixed_bytes<LEVEL>());
   if (e != cudaSuccess) return e;
   if (w) *w = nw;
   if (c) *c = cc;
