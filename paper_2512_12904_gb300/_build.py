@@ -19,7 +19,7 @@ LIB = os.path.join(BUILD, "libhqc_gb300.so")
 PEAKS_LIB = os.path.join(BUILD, "libhqc_peaks.so")
 SOURCES = ["hqc_decrypt.cu", "hqc_stage.cu", "hqc_tune.cu", "hqc_encrypt.cu", "hqc_abi.cu", "hqc_noalloc.cu", "hqc_plan.cu", "hqc_serve.cu", "hqc_host.cu", "hqc_kem.cu", "hqc_rm_tc.cu"]
 PEAKS_SOURCES = ["hqc_peaks.cu"]
-HEADERS = ["hqc_params.cuh", "hqc_device.cuh", "hqc_kernels.cuh", "hqc_internal.h", "hqc_keccak.cuh"]
+HEADERS = ["hqc_params.cuh", "hqc_device.cuh", "hqc_kernels.cuh", "hqc_internal.h", "hqc_keccak.cuh", "hqc_kem_k.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]
 

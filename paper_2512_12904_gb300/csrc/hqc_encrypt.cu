@@ -4,6 +4,7 @@
 // per item; used to build synthetic ciphertexts on the device.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <utility>
 
 #include "hqc_device.cuh"
@@ -244,12 +245,62 @@ __device__ __forceinline__ void enc_rm_encode(uint32_t* u2, int tid) {
   }
 }
 
+// One item by one warp (its key index already checked): u = r1 + h r2 and
+// v = first n1 n2 bits of mG + s r2 + e in the warp's shared slice u2 /
+// sup.  CMP: instead of storing (u, v), compare them with (u_in, v_in) on
+// the n and n1 n2 bits (padding of u_in ignored); returns true, on every
+// lane, when they match (the re-encryption check of decapsulation).
+// VALID: the supports are known to hold distinct positions < n (drawn by
+// the sampler), so the product takes the unmasked two-entries-per-pass
+// path.
+template <class LV, bool CMP, bool VALID>
+__device__ __forceinline__ bool encrypt_item(const uint8_t* smem, uint32_t* u2, uint32_t* sup, int lane, int64_t it,
+                                             int64_t key, const uint64_t* __restrict__ h,
+                                             const uint64_t* __restrict__ s, const uint8_t* __restrict__ m,
+                                             const uint32_t* __restrict__ r1, const uint32_t* __restrict__ r2,
+                                             const uint32_t* __restrict__ e, uint64_t* __restrict__ u,
+                                             uint64_t* __restrict__ v, const uint64_t* __restrict__ u_in,
+                                             const uint64_t* __restrict__ v_in) {
+  // u = r1 + h * r2
+  full_product_to_smem<LV, LV::wr, !VALID>(u2, sup, h + key * LV::W_u_pitch, r2 + it * LV::wr, lane);
+  xor_support_bits<LV::wr, LV::n>(u2, r1 + it * LV::wr, lane);
+  uint32_t diff = 0;
+  if constexpr (CMP) {
+    constexpr int R = LV::n & 31;
+    const uint32_t* ui = reinterpret_cast<const uint32_t*>(u_in + it * LV::W_u_pitch);
+    for (int i = lane; i < LV::N32; i += 32) {
+      uint32_t x = __ldg(ui + i);
+      if (R && i == LV::N32 - 1) x &= (1u << R) - 1u;
+      diff |= x ^ u2[i];
+    }
+  } else {
+    store_row<LV::W_u_pitch, LV::N32>(u + it * LV::W_u_pitch, u2, lane);
+  }
+  __syncwarp();
+
+  // s * r2, truncated to n1*n2 bits, plus e
+  build_doubled<LV::n, LV::W_u_pitch, LV::U2W_FULL>(u2, s + key * LV::W_u_pitch, lane);
+  truncated_product_to_smem<LV, LV::wr, !VALID>(u2, sup, lane);
+  xor_support_bits<LV::we, LV::n1 * LV::n2>(u2, e + it * LV::we, lane);
+
+  enc_rs_encode<LV>(m + it * LV::k, smem, lane, reinterpret_cast<uint8_t*>(u2 + LV::W_v32));
+  __syncwarp();
+  enc_rm_encode<LV, 32>(u2, lane);
+  __syncwarp();
+  bool same = false;
+  if constexpr (CMP) {
+    const uint32_t* vi = reinterpret_cast<const uint32_t*>(v_in + it * LV::W_v);
+    for (int i = lane; i < LV::W_v32; i += 32) diff |= __ldg(vi + i) ^ u2[i];
+    same = !__any_sync(FULL_MASK, diff != 0u);
+  } else {
+    store_row<LV::W_v, LV::W_v32>(v + it * LV::W_v, u2, lane);
+  }
+  __syncwarp();
+  return same;
+}
+
 // Persistent: each warp encrypts items it, it + (warps in the grid), ...
-// CMP: instead of storing (u, v), compare them with (u_in, v_in) on the n
-// and n1 n2 bits (padding of u_in ignored) and store ok[item] = 1 on a match
-// (the re-encryption check of decapsulation).  VALID: the supports are known
-// to hold distinct positions < n (drawn by the sampler), so the product
-// takes the unmasked two-entries-per-pass path.
+// (encrypt_item); with CMP it stores ok[item] = 1 on a match, 0 otherwise.
 template <int LEVEL, bool CMP, bool VALID>
 __global__ void __launch_bounds__(EncBound<LEVEL>::threads, 1) k_encrypt(int64_t count, const uint64_t* __restrict__ h,
                                                         const uint64_t* __restrict__ s, int64_t nkeys,
@@ -260,7 +311,6 @@ __global__ void __launch_bounds__(EncBound<LEVEL>::threads, 1) k_encrypt(int64_t
                                                         const uint64_t* __restrict__ u_in,
                                                         const uint64_t* __restrict__ v_in, uint32_t* __restrict__ ok) {
   using LV = Level<LEVEL>;
-  constexpr int k = LV::k;
   constexpr int WARP_W = LV::U2W_FULL + LV::WP_R;
   extern __shared__ __align__(16) uint8_t smem[];
   enc_tab_init<LV>(smem, threadIdx.x, blockDim.x);
@@ -271,44 +321,9 @@ __global__ void __launch_bounds__(EncBound<LEVEL>::threads, 1) k_encrypt(int64_t
   for (int64_t it = (int64_t)blockIdx.x * nw + warp; it < count; it += (int64_t)gridDim.x * nw) {
     const uint32_t ki = (uint32_t)key_idx[it];
     if (ki >= (uint64_t)nkeys) continue;  // skipped item: outputs untouched (the index is public)
-    const int64_t key = (int64_t)ki;
-
-    // u = r1 + h * r2
-    full_product_to_smem<LV, LV::wr, !VALID>(u2, sup, h + key * LV::W_u_pitch,
-                                                                        r2 + it * LV::wr, lane);
-    xor_support_bits<LV::wr, LV::n>(u2, r1 + it * LV::wr, lane);
-    uint32_t diff = 0;
-    if constexpr (CMP) {
-      constexpr int R = LV::n & 31;
-      const uint32_t* ui = reinterpret_cast<const uint32_t*>(u_in + it * LV::W_u_pitch);
-      for (int i = lane; i < LV::N32; i += 32) {
-        uint32_t x = __ldg(ui + i);
-        if (R && i == LV::N32 - 1) x &= (1u << R) - 1u;
-        diff |= x ^ u2[i];
-      }
-    } else {
-      store_row<LV::W_u_pitch, LV::N32>(u + it * LV::W_u_pitch, u2, lane);
-    }
-    __syncwarp();
-
-    // s * r2, truncated to n1*n2 bits, plus e
-    build_doubled<LV::n, LV::W_u_pitch, LV::U2W_FULL>(u2, s + key * LV::W_u_pitch, lane);
-    truncated_product_to_smem<LV, LV::wr, !VALID>(u2, sup, lane);
-    xor_support_bits<LV::we, LV::n1 * LV::n2>(u2, e + it * LV::we, lane);
-
-    enc_rs_encode<LV>(m + it * k, smem, lane, reinterpret_cast<uint8_t*>(u2 + LV::W_v32));
-    __syncwarp();
-    enc_rm_encode<LV, 32>(u2, lane);
-    __syncwarp();
-    if constexpr (CMP) {
-      const uint32_t* vi = reinterpret_cast<const uint32_t*>(v_in + it * LV::W_v);
-      for (int i = lane; i < LV::W_v32; i += 32) diff |= __ldg(vi + i) ^ u2[i];
-      const bool differs = __any_sync(FULL_MASK, diff != 0u);
-      if (lane == 0) ok[it] = differs ? 0u : 1u;
-    } else {
-      store_row<LV::W_v, LV::W_v32>(v + it * LV::W_v, u2, lane);
-    }
-    __syncwarp();
+    const bool same =
+        encrypt_item<LV, CMP, VALID>(smem, u2, sup, lane, it, (int64_t)ki, h, s, m, r1, r2, e, u, v, u_in, v_in);
+    if (CMP && lane == 0) ok[it] = same ? 1u : 0u;
   }
 }
 

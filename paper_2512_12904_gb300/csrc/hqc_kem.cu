@@ -29,14 +29,13 @@
 #include "hqc_device.cuh"
 #include "hqc_internal.h"
 #include "hqc_keccak.cuh"
+#include "hqc_kem_k.cuh"
 
 namespace hqc {
 
 constexpr int KEM_THREADS = 128;
 constexpr int KEM_K2_THREADS = 128;  // 64 lane pairs per block: 1,024 blocks for 65,536 items
-constexpr int KEM_SALT = 16;
 constexpr int KEM_SEED = 32;
-constexpr int KEM_KBYTES = 32;
 
 // ---------------------------------------------------------------------------
 // Batched SHAKE256 of fixed-length rows (msg [count][len] -> out
@@ -212,23 +211,14 @@ __global__ void __launch_bounds__(KEM_THREADS) k_kem_derive(int64_t count, const
   draw_support<LV::n, LV::we>(st, pos, e + it * LV::we);
 }
 
-// K = SHAKE256(x || U || V || salt || 0x04)[0:32]; x = m where ok (or no
-// flags given), sigma of the item's key otherwise, chosen by mask.
-// Message words: x (k/8 words), then the u words up to the one that holds
-// the last byte of U (bits >= n cleared), then, from word P1 on, a stream
-// shifted by r = (k + ceil(n/8)) mod 8 bytes over T = [last u word,
-// v[0..W_v), salt, 0x04]: word P1 + i = (T[i+1] << 8r) | (T[i] >> (64 - 8r)).
-// The previous T word is carried, so each message word costs one load.
-// K = SHAKE256(x || U || V || salt || 4) with each message on a lane pair
-// (keccak_f1600_pair): lane h of the pair keeps the h-th 32-bit half of
-// every state lane, so 65,536 messages fill 4,096 warps instead of 2,048
-// (one thread per message measured 0.7 % slower on HQC-1 decapsulation:
-// the pair's 29 shuffles per round cost most of what the warps gain).  x is
-// m, or sigma where the re-encryption did not match, chosen by mask.  The
-// message is a byte-shifted stream over the u and v words with the
-// previous word carried, one load per message word.  Lanes past the batch, and
-// items with a key index outside [0, nkeys), hash the last item's (or key
-// 0's) data and store nothing: every lane takes part in the shuffles.
+// K on lane pairs (kem_K_pair): lane h of the pair keeps the h-th 32-bit
+// half of every state lane, so 65,536 messages fill 4,096 warps instead of
+// 2,048 (one thread per message measured 0.7 % slower on HQC-1
+// decapsulation: the pair's 29 shuffles per round cost most of what the
+// warps gain).  x is m, or sigma where the re-encryption did not match
+// (ok given and 0), chosen by mask.  Lanes past the batch, and items with a
+// key index outside [0, nkeys), hash the last item's (or key 0's) data and
+// store nothing: every lane takes part in the shuffles.
 template <int LEVEL>
 __global__ void __launch_bounds__(KEM_K2_THREADS) k_kem_K2(int64_t count, const uint8_t* __restrict__ m,
                                                           const uint32_t* __restrict__ ok,
@@ -238,13 +228,6 @@ __global__ void __launch_bounds__(KEM_K2_THREADS) k_kem_K2(int64_t count, const 
                                                           const uint64_t* __restrict__ v,
                                                           const uint8_t* __restrict__ salt, uint8_t* __restrict__ K) {
   using LV = Level<LEVEL>;
-  constexpr int KW = LV::k / 8;
-  constexpr int UB = cdiv(LV::n, 8), VB = LV::n1 * LV::n2 / 8;
-  constexpr int OFF_V = LV::k + UB;
-  constexpr int LEN = OFF_V + VB + KEM_SALT + 1;
-  constexpr int P1 = OFF_V / 8, R8 = 8 * (OFF_V % 8);
-  constexpr int NT = LV::W_v + 4;  // T[1..NT): v words, two salt words, the domain byte
-  static_assert(P1 == KW + LV::W_u - 1 && R8 > 0, "U ends inside its last word");
   const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t h = (uint32_t)(gt & 1);
   const bool in = (gt >> 1) < count;
@@ -258,30 +241,9 @@ __global__ void __launch_bounds__(KEM_K2_THREADS) k_kem_K2(int64_t count, const 
     keep = 0ull - (uint64_t)(__ldg(ok + it) != 0u);
     grow = reinterpret_cast<const uint64_t*>(sigma + (int64_t)(ki < (uint64_t)nkeys ? ki : 0u) * LV::k);
   }
-  const uint64_t* urow = u + it * LV::W_u_pitch;
-  const uint64_t* vrow = v + it * LV::W_v;
-  const uint64_t* srow = reinterpret_cast<const uint64_t*>(salt + it * KEM_SALT);
-  constexpr uint64_t UMASK = (LV::n & 63) ? (1ull << (LV::n & 63)) - 1ull : ~0ull;
-  // T[0] = last u word placed so that T[0] >> (64 - 8r) is its U bytes
-  uint64_t prev = (__ldg(urow + LV::W_u - 1) & UMASK) << (64 - R8);
-  auto tword = [&](int i) {  // T[i], i >= 1
-    return i <= LV::W_v ? __ldg(vrow + i - 1) : i <= LV::W_v + 2 ? __ldg(srow + i - 1 - LV::W_v) : 0x04ull;
-  };
   uint32_t a[25];
-  shake256_absorb_pair(a, LEN, h, [&](int q) {
-    uint64_t w;
-    if (q < KW) {
-      w = (__ldg(mrow + q) & keep) | (__ldg(grow + q) & ~keep);
-    } else if (q < P1) {
-      w = __ldg(urow + q - KW);
-    } else {
-      const int i = q - P1 + 1;
-      const uint64_t cur = i < NT ? tword(i) : 0ull;
-      w = (cur << R8) | (prev >> (64 - R8));
-      prev = cur;
-    }
-    return w;
-  });
+  kem_K_pair<LV>(h, keep, mrow, grow, u + it * LV::W_u_pitch, v + it * LV::W_v,
+                 reinterpret_cast<const uint64_t*>(salt + it * KEM_SALT), a);
   if (store) {
     uint32_t* krow = reinterpret_cast<uint32_t*>(K + it * KEM_KBYTES);
 #pragma unroll
@@ -507,10 +469,9 @@ int hqc_kem_decaps(int level, int64_t count, const hqc_keyset_t* keys, const uin
   a.m = w.m;
   int rc = kcuda(hqc::launch_fused(level, true, a, st, hqc::level_cfg(level)), "decrypt launch");
   if (rc == HQC_OK) rc = kcuda(hqc::launch_kem_derive(level, count, w.m, salt, w.r1, w.r2, w.e, st), "derive launch");
-  if (rc == HQC_OK)
-    rc = kcuda(hqc::launch_encrypt_compare(level, count, h, s, keys->nkeys, key_idx, w.m, w.r1, w.r2, w.e, u, v, ok,
-                                           st),
-               "re-encrypt launch");
+  if (rc != HQC_OK) return rc;
+  rc = kcuda(hqc::launch_encrypt_compare(level, count, h, s, keys->nkeys, key_idx, w.m, w.r1, w.r2, w.e, u, v, ok, st),
+             "re-encrypt launch");
   if (rc == HQC_OK)
     rc = kcuda(hqc::launch_kem_K(level, count, w.m, ok, sigma, key_idx, keys->nkeys, u, v, salt, K_out, st),
                "K launch");

@@ -209,3 +209,49 @@ def test_kem_skips_bad_key_index(hqc, level):
     assert (K_h[good] == oK[good]).all() and (ok_h[good] == 1).all()
     assert (K_h[bad_rows] == 0).all() and (ok_h[bad_rows] == 0).all()
     keys.free()
+
+
+def test_decaps_ragged_counts_tampered_and_skipped(hqc):
+    """HQC-1 decapsulation at counts below, at and above one block's warp
+    count, a ragged count over every SM and a batch of 240,011 items (more
+    than three waves of the persistent kernels), with every 97th item
+    tampered and every 389th skipped: every accepted K equals the
+    encapsulated one, tampered items are rejected with K(sigma, c) equal to
+    the oracle's on a sample, and skipped items keep their rows."""
+    level = 1
+    P = oracle.params(level)
+    nkeys = 64
+    sk, pk = _keys(level, nkeys, tag=1200)
+    h, x, y, s = hqc.hqc_kem_keygen(level, cu8(sk), cu8(pk))
+    sigma = cu8(rows(nkeys, P.k, 1201))
+    keys = hqc.Keyset(level, y.cpu().numpy().view(np.uint32))
+    hh, ss, yy, sg = host_u64(h), host_u64(s), y.cpu().numpy().view(np.uint32), sigma.cpu().numpy()
+    for count in (1, 23, 24, 25, 3647, 240011):
+        kidx = cu32(synth.key_assignment(count, nkeys, tag=1202 + count))
+        m = cu8(rows(count, P.k, 1203 + count))
+        salt = cu8(rows(count, 16, 1204 + count))
+        u, v, K = hqc.hqc_kem_encaps(level, h, s, kidx, m, salt)
+        # every 97th item tampered (a v bit: rejected), every 389th skipped
+        vt = v.clone()
+        vt[0::97, 3] ^= 1 << 11
+        kt = kidx.clone()
+        kt[5::389] = nkeys + 3
+        K0 = torch.full((count, 32), 0x5A, dtype=torch.uint8, device="cuda")
+        ok0 = torch.full((count,), 7, dtype=torch.int32, device="cuda")
+        Kd, ok = hqc.hqc_kem_decaps(level, keys, h, s, sigma, kt, u, vt, salt, K_out=K0, ok_out=ok0)
+        okh, Kdh, Kh = ok.cpu().numpy(), Kd.cpu().numpy(), K.cpu().numpy()
+        tam = np.zeros(count, bool)
+        tam[0::97] = True
+        skip = np.zeros(count, bool)
+        skip[5::389] = True
+        acc = ~tam & ~skip
+        assert (okh[acc] == 1).all() and (Kdh[acc] == Kh[acc]).all(), count
+        assert (okh[tam & ~skip] == 0).all() and not (Kdh[tam & ~skip] == Kh[tam & ~skip]).all(axis=1).any(), count
+        assert (okh[skip] == 7).all() and (Kdh[skip] == 0x5A).all(), count
+        idx = np.unique(np.r_[np.flatnonzero(tam & ~skip)[:3], np.flatnonzero(acc)[-2:], [count - 1]])
+        idx = idx[~skip[idx]]
+        ti = torch.from_numpy(idx).cuda()
+        oK, ook = oracle.kem_decaps(level, hh, ss, yy, sg, kt[ti].cpu().numpy(), host_u64(u[ti]), host_u64(vt[ti]),
+                                    salt[ti].cpu().numpy())
+        assert (Kdh[idx] == oK).all() and (okh[idx] == ook).all(), count
+    keys.free()
