@@ -269,10 +269,13 @@ __device__ __forceinline__ void rot_xor_product(const uint32_t* u2, const uint32
 // signed halves, which sums and differences keep exact (a negative low half
 // borrows from the high half, and is lent back when the bias is added), so
 // a butterfly is a plain add and a plain subtract; bit 6, one shuffle with
-// the partner lane, adds the bias 640 to both halves.  For mult 5 every
-// stage keeps both halves biased by 640 (a butterfly adds or subtracts the
-// bias too), which measured 0.6-0.8 % faster there, against 3.6 % slower
-// for mult 3.  Either way, after bit 6 each half is F + 640 as an unsigned
+// the partner lane, adds the bias 640 to both halves.  With SIGNED false
+// every stage keeps both halves biased by 640 (a butterfly adds or
+// subtracts the bias too).  Measured: the signed form is 3.6 % faster in
+// the HQC-1 fused kernel (it removes a spill at 64 registers), the biased
+// one 0.6-0.8 % faster for mult 5, and in the stand-alone RM stage kernel
+// (48 against 54 registers, so more warps per SM) 8 % faster for mult 3
+// too.  Either way, after bit 6 each half is F + 640 as an unsigned
 // 16-bit value (|F| <= 640, and F is even: a sum of 128 odd s_i); bit 4
 // (the halves) is the last stage.
 // The argmax runs on 16-bit keys (F + 640) / 2 * 64 + (63 - r6) -- score,
@@ -291,11 +294,10 @@ __device__ __forceinline__ uint32_t vmax3_u16x2(uint32_t a, uint32_t b, uint32_t
   return __vimax3_u16x2(a, b, c);
 }
 
-template <int MULT>
+template <int MULT, bool SIGNED = MULT == 3>
 __device__ __forceinline__ uint32_t rm_decode_pair(const uint32_t* blk, uint32_t hb) {
   constexpr uint32_t BIAS = 640u;
   constexpr uint32_t BP = BIAS * 0x10001u;
-  constexpr bool SIGNED = MULT == 3;  // unbiased in-lane stages
   constexpr uint32_t K = (SIGNED ? MULT : BIAS + MULT) * 0x10001u;  // K - 2 c = s_i (+ bias) in both halves
   constexpr uint32_t SB = SIGNED ? 0u : BP;
   constexpr uint32_t KN = 2u * BP * 32u;  // (1280 per half) * 32

@@ -504,7 +504,7 @@ __global__ void __launch_bounds__(STAGE_THREADS) k_stage_rm(int64_t count, const
   const int64_t it = gg / LV::n1;
   const int j = (int)(gg - it * LV::n1);
   const uint32_t* blk = reinterpret_cast<const uint32_t*>(w + it * LV::W_v) + j * (LV::n2 / 32);
-  const uint32_t byte = rm_decode_pair<LV::mult>(blk, threadIdx.x & 1);
+  const uint32_t byte = rm_decode_pair<LV::mult, false>(blk, threadIdx.x & 1);
   if (g < total && (threadIdx.x & 1) == 0) r_out[it * LV::n1 + j] = (uint8_t)byte;
 }
 
