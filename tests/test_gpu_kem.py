@@ -148,7 +148,8 @@ def test_kem_full_size_roundtrip_sampled(hqc, level, count, nkeys):
 @pytest.mark.parametrize("level", LEVELS)
 def test_decaps_from_host_buffers_matches_device_path(hqc, level):
     """Chunked host-buffer decapsulation (ragged last chunk, one-item chunks,
-    one chunk larger than the batch) against the oracle, with rejections."""
+    one chunk larger than the batch, and the library's own choice with
+    chunk = 0) against the oracle, with rejections."""
     P, h, y, s, sigma, kidx, m, salt = _kem_setup(hqc, level, 3, 70, tag=1000 + 10 * level)
     u, v, K = oracle.kem_encaps(level, h, s, kidx, m, salt)
     v[::4, 2] ^= np.uint64(1 << 3)  # a quarter rejected
@@ -159,8 +160,8 @@ def test_decaps_from_host_buffers_matches_device_path(hqc, level):
     v_h = torch.from_numpy(v.view(np.int64).copy()).pin_memory()
     k_h = torch.from_numpy(kidx.astype(np.int32)).pin_memory()
     s_h = torch.from_numpy(salt.copy()).pin_memory()
-    for chunk in (1, 16, 32, 100):
-        ws = torch.empty(hqc.hqc_kem_host_workspace_bytes(level, chunk), dtype=torch.uint8, device="cuda")
+    for chunk in (1, 16, 32, 100, 0):
+        ws = torch.empty(hqc.hqc_kem_host_workspace_bytes(level, chunk or 100), dtype=torch.uint8, device="cuda")
         K_h, ok_h = hqc.hqc_kem_decaps_host(level, keys, hd, sd, sig, k_h, u_h, v_h, s_h, chunk=chunk, workspace=ws)
         torch.cuda.current_stream().synchronize()
         assert (K_h.numpy() == oK).all(), chunk
