@@ -292,12 +292,15 @@ typedef struct hqc_debug_dump_s {
 int hqc_decrypt_debug(int level, int64_t count, const uint64_t* u, const uint64_t* v, const uint32_t* y,
                       const hqc_debug_dump_t* dump, uint8_t* m_out, void* stream);
 
-/* The latency forms' own intermediates: decrypt with literal supports
- * through form 0 (a block of four warps per ciphertext, k_decrypt_latency)
- * or form 1 (a cluster of four blocks per ciphertext,
- * k_decrypt_latency_cluster), whatever the count, and write each
- * ciphertext's RM bytes (dump->r), syndromes (dump->S) and Lambda
- * (dump->lam) as the block that ran RS holds them.  dump points to HOST
+/* The fused kernels' own intermediates: decrypt with literal supports
+ * through form 0 (a block of four warps per ciphertext, k_decrypt_latency),
+ * form 1 (a cluster of four blocks per ciphertext,
+ * k_decrypt_latency_cluster) or form 2 (the per-turn code of the persistent
+ * throughput kernels: k_decrypt_fused's solo warps with G words per turn,
+ * HQC-1's Horner syndromes included, or k_decrypt_team's two-warp teams for
+ * HQC-5), whatever the count, and write each ciphertext's RM bytes
+ * (dump->r), syndromes (dump->S) and Lambda (dump->lam) as the warps that
+ * ran RS hold them.  dump points to HOST
  * memory holding device pointers; r, S and lam must be non-NULL, the other
  * fields are ignored.  HQC_EINVAL on a bad form or pointer. */
 int hqc_decrypt_debug_team(int level, int form, int64_t count, const uint64_t* u, const uint64_t* v, const uint32_t* y,

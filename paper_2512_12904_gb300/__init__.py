@@ -387,8 +387,9 @@ def hqc_decrypt_debug(level, u, v, y, stream=None):
 
 
 def hqc_decrypt_debug_team(level, u, v, y, form=0, stream=None):
-    """The latency forms' intermediates (form 0: four-warp team per
-    ciphertext, 1: cluster of four blocks): r, S, lam and m per ciphertext."""
+    """The fused kernels' own intermediates (form 0: four-warp team per
+    ciphertext, 1: cluster of four blocks, 2: the persistent throughput
+    kernels' per-turn code): r, S, lam and m per ciphertext."""
     torch = _torch()
     P = hqc_get_params(level)
     u, v = _as_u64(u), _as_u64(v)

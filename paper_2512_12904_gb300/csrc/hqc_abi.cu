@@ -299,7 +299,8 @@ int hqc_decrypt_debug_team(int level, int form, int64_t count, const uint64_t* u
   hqc_params_t p{};
   int rc = check_common(level, count, u, v, m_out, &p);
   if (rc != HQC_OK) return rc;
-  if (form != 0 && form != 1) return fail(HQC_EINVAL, "form must be 0 (four-warp team) or 1 (cluster)");
+  if (form < 0 || form > 2)
+    return fail(HQC_EINVAL, "form must be 0 (four-warp team), 1 (cluster) or 2 (throughput kernels)");
   if (count == 0) return HQC_OK;
   if (!y || !dump) return fail(HQC_EINVAL, "y and dump must be non-NULL");
   if (!dump->r || !dump->S || !dump->lam) return fail(HQC_EINVAL, "dump->r, dump->S and dump->lam must be non-NULL");
@@ -310,7 +311,7 @@ int hqc_decrypt_debug_team(int level, int form, int64_t count, const uint64_t* u
   a.y = y;
   a.m = m_out;
   hqc::DebugArgs d{nullptr, nullptr, dump->r, dump->S, dump->lam, nullptr, nullptr, nullptr, nullptr, nullptr};
-  return launch_result(hqc::launch_debug_team(level, form, a, d, (cudaStream_t)stream), "debug latency launch");
+  return launch_result(hqc::launch_debug_team(level, form, a, d, (cudaStream_t)stream), "debug team launch");
 }
 
 size_t hqc_mixed_workspace_bytes(void) { return 256; }

@@ -76,13 +76,16 @@ def test_debug_path_every_intermediate(hqc, level):
 
 
 @pytest.mark.parametrize("level", LEVELS)
-@pytest.mark.parametrize("form", (0, 1))
+@pytest.mark.parametrize("form", (0, 1, 2))
 def test_latency_forms_every_rs_intermediate(hqc, level, form):
-    """The latency forms' own intermediates (not only m): form 0 (four-warp
-    team per ciphertext) and form 1 (cluster of four blocks, whose RM bytes
-    reach block 0 through distributed shared memory) dump each ciphertext's
-    RM bytes, syndromes and Lambda as the block that ran RS holds them; all
-    equal the oracle's, on adversarial and honest ciphertexts."""
+    """The fused kernels' own intermediates (not only m): form 0 (four-warp
+    team per ciphertext), form 1 (cluster of four blocks, whose RM bytes
+    reach block 0 through distributed shared memory) and form 2 (the
+    persistent throughput kernels' per-turn code: HQC-1's two words per warp
+    with Horner syndromes, HQC-3's one, HQC-5's two-warp teams) dump each
+    ciphertext's RM bytes, syndromes and Lambda as the warps that ran RS
+    hold them; all equal the oracle's, on adversarial and honest
+    ciphertexts."""
     P, u, v, y = adversarial(level, tag=70 + level)
     wl = honest(level, 3, 11, first_ct=22000, tag=31)
     u = np.concatenate([u, wl.u]); v = np.concatenate([v, wl.v]); y = np.concatenate([y, wl.y_rows])
@@ -94,6 +97,29 @@ def test_latency_forms_every_rs_intermediate(hqc, level, form):
         bad = np.argwhere(g != want[k])
         assert bad.size == 0, (k, bad[:5])
     assert (host(got["m"])[-11:] == wl.m).all()
+
+
+def test_throughput_turns_every_rs_intermediate(hqc):
+    """Form 2 over 519 HQC-1 ciphertexts: 64 blocks of four warps take two
+    words per warp per turn, so some warps run a second turn (reusing their
+    shared memory and the block's syndrome table) and the last group holds
+    one word.  Every ninth v is replaced by random words (far beyond delta
+    errors).  RM bytes, syndromes, Lambda and m all equal the oracle's."""
+    level, count = 1, 519
+    P = oracle.params(level)
+    wl = honest(level, 4, count, first_ct=31000, tag=33)
+    v = wl.v.copy()
+    v[::9] = synth.words(v[::9].size, tag=34).reshape(v[::9].shape)
+    want = oracle_dumps(level, wl.u, v, wl.y_rows)
+    got = hqc.hqc_decrypt_debug_team(level, u64(wl.u), u64(v), i32(wl.y_rows), form=2)
+    torch.cuda.synchronize()
+    for k in ("r", "S", "lam", "m"):
+        g = host(got[k])
+        bad = np.argwhere(g != want[k])
+        assert bad.size == 0, (k, bad[:5])
+    ok = np.ones(count, bool)
+    ok[::9] = False
+    assert (host(got["m"])[ok] == wl.m[ok]).all()
 
 
 # launch shapes of the single-level path: the default picks the latency form
