@@ -248,3 +248,16 @@ def test_rm_decode_batch_argument_checks():
     assert lib.hqc_rm_decode_batch(1, 1, p16, None, 1, None) == hqc.HQC_EINVAL
     assert lib.hqc_rm_decode_batch(1, 0, None, None, 1, None) == hqc.HQC_OK
     assert lib.hqc_rm_tc_timeouts(None) == hqc.HQC_EINVAL
+
+
+def test_debug_team_argument_checks():
+    """hqc_decrypt_debug_team accepts forms 0, 1 and 2 only and checks y and
+    the dump before touching the device; an empty batch is a no-op."""
+    lib = hqc.load()
+    buf = ctypes.create_string_buffer(64)
+    p16 = ctypes.c_void_p((ctypes.addressof(buf) + 15) & ~15)
+    for form in (-1, 3):
+        assert lib.hqc_decrypt_debug_team(1, form, 1, p16, p16, p16, p16, p16, None) == hqc.HQC_EINVAL
+    assert lib.hqc_decrypt_debug_team(1, 2, 1, p16, p16, None, p16, p16, None) == hqc.HQC_EINVAL
+    assert lib.hqc_decrypt_debug_team(5, 2, 1, p16, p16, p16, None, p16, None) == hqc.HQC_EINVAL
+    assert lib.hqc_decrypt_debug_team(3, 2, 0, p16, p16, p16, p16, p16, None) == hqc.HQC_OK
